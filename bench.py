@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark of the CALU / CAQR hot path on GB300.
+
+One step = CALU (tournament pivoting over the reduction tree) + getrs, then
+CAQR (TSQR panels + tree update) + geqrs, of one n x n FP64 matrix already
+resident in HBM (n = 16384, b = 128, leaves of 256 rows).  The input is
+A = U diag(s) V^T with orthogonal U, V and log-spaced s (cond 1e6) and one
+right-hand side; every step restores A from a pristine device copy.
+
+Prints one JSON line: GFLOP/s over the standard flop counts (LU 2n^3/3,
+QR 4n^3/3, solves), the roofline of the dominant kernel measured live with
+CUDA events on its launch stream, the oracle timed on the host cores on a
+bounded sample, an end-to-end number through the public API with host
+buffers, the SM clocks sampled during the timed region and the number of
+library kernel launches.
+
+--impl reference runs the CPU oracle (plain C, FP64) on the host cores on a
+bounded sample of the same workload (the only other code path that may run
+the oracle).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CALU/CAQR GFLOP/s & % roofline (n=16384, FP64 vs mixed+IR); solves/s, p99 lat"
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # SMs x DFMA/clk/SM x flops/DFMA x max GHz = 1258.6
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--b", type=int, default=128)
+    p.add_argument("--leaf", type=int, default=256)
+    p.add_argument("--cond", type=float, default=1e6)
+    p.add_argument("--nrhs", type=int, default=1)
+    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--cpu-n", type=int, default=1024, help="oracle sample size")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def step_flops(n: int, nrhs: int) -> float:
+    lu = 2.0 * n ** 3 / 3.0
+    qr = 4.0 * n ** 3 / 3.0
+    getrs = 2.0 * n * n * nrhs
+    geqrs = 3.0 * n * n * nrhs
+    return lu + qr + getrs + geqrs
+
+
+TREE_LEVELS = [(4, 0), (0, 0)]  # binary merges: 4 leaves per cluster group, then the grid
+
+
+def workload_config(a, extra=None):
+    c = {
+        "workload": (f"CALU+getrs and CAQR+geqrs of one {a.n}x{a.n} FP64 matrix "
+                     f"(A = U diag(s) V^T, cond {a.cond:g}), b={a.b}, leaves of {a.leaf} rows, "
+                     f"binary reduction tree, {a.nrhs} RHS"),
+        "n": a.n, "b": a.b, "leaf_rows": a.leaf, "tree": "binary (fan-in 4 level, then all)",
+        "cond": a.cond, "nrhs": a.nrhs, "precision": "plain FP64",
+        "l2": "inputs (8 n^2 bytes) larger than the 129 MB L2",
+    }
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(a, n: int):
+    """CALU + getrs and CAQR + geqrs by the CPU oracle on an n x n matrix of
+    the same family; returns (seconds, flops)."""
+    import oracle
+    from paper_1303_5837_gb300 import inputs
+    A = inputs.conditioned(n, a.cond, 2026)
+    B = inputs.rhs(n, a.nrhs, 2027)
+    tree = oracle.make_tree(a.leaf, TREE_LEVELS)
+    oracle.build()
+    t0 = time.perf_counter()
+    LU, ipiv, _, _ = oracle.calu(A, a.b, tree)
+    oracle.getrs(LU, ipiv, B)
+    QR, T = oracle.caqr(A, a.b, tree)
+    oracle.geqrs(QR, T, a.b, tree, B)
+    return time.perf_counter() - t0, step_flops(n, a.nrhs)
+
+
+def cpu_baseline(a):
+    secs, fl = oracle_sample(a, a.cpu_n)
+    return {"value": fl / secs / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle CALU+getrs and CAQR+geqrs of one {a.cpu_n}x{a.cpu_n} matrix of the "
+                       f"same family (b={a.b}, leaves {a.leaf}), single-threaded C, {secs:.1f} s"),
+            "seconds": secs}
+
+
+def run_reference(a, rank: int, world: int):
+    if rank != 0:
+        return
+    times = []
+    for i in range(a.warmup + a.steps):
+        secs, fl = oracle_sample(a, a.cpu_n)
+        if i >= a.warmup:
+            times.append(secs)
+    t = sum(times)
+    value = fl * len(times) / t / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1e3 * t / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": workload_config(a, {"sample_n": a.cpu_n}),
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: oracle on one {a.cpu_n}x{a.cpu_n} matrix"},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def traffic_for(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if
+    the summary was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1303_5837_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    digest = h.hexdigest()[:16]
+    for ln in open(path):
+        p = ln.split()
+        if len(p) >= 3 and p[0] == kernel and p[1] == digest:
+            return float(p[2])
+    return None
+
+
+def run_ours(a, rank: int, world: int, local: int):
+    import torch
+    import paper_1303_5837_gb300 as ca
+    from paper_1303_5837_gb300 import inputs
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ca.load()
+    n, b, nrhs = a.n, a.b, a.nrhs
+    tree = ca.make_tree(a.leaf, TREE_LEVELS)
+
+    # ---- inputs (untimed): A = U diag(s) V^T, B = A x_true ------------------
+    A0 = conditioned_device(n, a.cond, 2026 + rank, dev)
+    x_true = torch.randn(n, nrhs, dtype=torch.float64, device=dev,
+                         generator=torch.Generator(device=dev).manual_seed(7 + rank))
+    B0 = ca.colmajor(A0 @ x_true)
+    A = torch.empty_like(A0)
+    X = torch.empty_like(B0)
+    ipiv = torch.empty(n, dtype=torch.int32, device=dev)
+    info = torch.zeros(2, dtype=torch.int32, device=dev)
+    lwork = ca.ca_calu_workspace(n, n, b, tree)
+    work = torch.empty((lwork + 7) // 8, dtype=torch.float64, device=dev)
+    qb, qw = ca.ca_caqr_workspace(n, n, b, tree)
+    qtree = torch.empty((qb + 7) // 8, dtype=torch.float64, device=dev)
+    qwork = torch.empty((max(qw, ca.ca_geqrs_workspace(n, n, nrhs, b, tree)) + 7) // 8,
+                        dtype=torch.float64, device=dev)
+
+    def factor_and_solve(src_A, src_B):
+        A.copy_(src_A)
+        X.copy_(src_B)
+        ca.calu_factor(A, b, tree, ipiv=ipiv, work=work, dev_info=info)
+        ca.calu_getrs(A, ipiv, X)
+        x_lu = X.clone() if check else None
+        A.copy_(src_A)
+        X.copy_(src_B)
+        ca.caqr_factor(A, b, tree, qtree=qtree, work=qwork, dev_info=info)
+        ca.caqr_geqrs(A, b, tree, qtree, X, work=qwork)
+        return x_lu
+
+    # ---- correctness of the timed configuration (untimed) -----------------
+    check = True
+    x_lu = factor_and_solve(A0, B0)
+    torch.cuda.synchronize()
+    err_lu = float(torch.linalg.norm(x_lu - x_true) / torch.linalg.norm(x_true))
+    err_qr = float(torch.linalg.norm(X - x_true) / torch.linalg.norm(x_true))
+    check = False
+
+    for _ in range(a.warmup):
+        factor_and_solve(A0, B0)
+    torch.cuda.synchronize()
+    barrier(world)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ca.ca_prof_enable(True, 12000 * max(1, a.steps))
+    launches0 = ca.ca_launch_count()
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(a.steps):
+        factor_and_solve(A0, B0)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = ca.ca_launch_count() - launches0
+    clocks = sampler.stop()
+    kernels = {}
+    for c, name in enumerate(ca.KERNEL_CLASSES):
+        cnt, kms, kfl, dropped = ca.ca_prof_read(c)
+        if cnt:
+            kernels[name] = {"launches": cnt, "ms": kms, "gflop": kfl / 1e9, "dropped": dropped}
+    ca.ca_prof_enable(False, 1)
+    ms_max = allreduce_max(ms, world)
+
+    flops = step_flops(n, nrhs)
+    value = world * flops * a.steps / (ms_max / 1e3) / 1e9
+    # dominant kernel by device time
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    dk = kernels[dom]
+    achieved = dk["gflop"] / (dk["ms"] / 1e3)
+    tot_kms = sum(v["ms"] for v in kernels.values())
+    for v in kernels.values():
+        v["share"] = v["ms"] / tot_kms
+
+    # ---- end to end through the public API with host buffers --------------
+    e2e = None
+    if a.e2e_steps > 0:
+        A_h = A0.cpu().pin_memory()
+        B_h = B0.cpu().pin_memory()
+        X_h = torch.empty(B0.shape, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            A.copy_(A_h, non_blocking=True)      # H2D: the matrix
+            X.copy_(B_h, non_blocking=True)      # H2D: the right-hand side
+            ca.calu_factor(A, b, tree, ipiv=ipiv, work=work, dev_info=info)
+            ca.calu_getrs(A, ipiv, X)
+            X_h.copy_(X, non_blocking=True)      # D2H: the LU solution
+            A.copy_(A_h, non_blocking=True)
+            X.copy_(B_h, non_blocking=True)
+            ca.caqr_factor(A, b, tree, qtree=qtree, work=qwork, dev_info=info)
+            ca.caqr_geqrs(A, b, tree, qtree, X, work=qwork)
+            X_h.copy_(X, non_blocking=True)      # D2H: the least-squares solution
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(st)
+        for _ in range(a.e2e_steps):
+            e2e_step()
+        f1.record(st)
+        torch.cuda.synchronize()
+        ems = allreduce_max(f0.elapsed_time(f1), world)
+        h2d = 2 * A0.numel() * 8 + 2 * B0.numel() * 8
+        d2h = 2 * B0.numel() * 8
+        e2e = {"value": world * flops * a.e2e_steps / (ems / 1e3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": ems / a.e2e_steps}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not a.no_cpu:
+        cpu = cpu_baseline(a)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(a, {"parallelism": f"replicas{world}" if world > 1 else "single"}),
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+                     "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+                     "traffic": traffic_for(dom),
+                     "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "kernels": kernels,
+        "check": {"x_rel_err_calu": err_lu, "x_rel_err_caqr": err_qr},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def conditioned_device(n, cond, seed, dev):
+    """A = U diag(s) V^T in FP64 on the device; U and V are Kronecker products
+    of two seeded Haar-orthogonal factors (exactly orthogonal up to rounding,
+    cheap to draw at n = 16384), s log-spaced from 1 to 1/cond."""
+    import torch
+    from paper_1303_5837_gb300 import inputs
+    n1 = 1 << (int(np.log2(n)) // 2)
+    if n1 * (n // n1) != n or n < 4096:
+        return torch.from_numpy(np.ascontiguousarray(inputs.conditioned(n, cond, seed).T)).to(dev).t()
+    n2 = n // n1
+    g = np.random.Generator(np.random.PCG64(seed))
+
+    def haar(k):
+        z = g.standard_normal((k, k))
+        q, r = np.linalg.qr(z)
+        return q * np.sign(np.diag(r))
+
+    U = torch.kron(torch.from_numpy(haar(n1)).to(dev), torch.from_numpy(haar(n2)).to(dev))
+    V = torch.kron(torch.from_numpy(haar(n1)).to(dev), torch.from_numpy(haar(n2)).to(dev))
+    s = torch.from_numpy(inputs.singular_values(n, cond)).to(dev)
+    perm = torch.from_numpy(g.permutation(n)).to(dev)
+    A = (U * s[perm]) @ V.t()
+    del U, V
+    return A.t().contiguous().t()
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    run_ours(a, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * ca_gb300.h -- C-ABI of the GB300 (sm_103a) communication-avoiding LU and QR
+ * library: tall-skinny panel factorization by reduction trees (TSLU
+ * tournament pivoting, TSQR) and the trailing updates that consume each
+ * panel (CALU, CAQR), plus the solves built on the factors.
+ *
+ * Method: Grigori, Jacquelin, Khabou, "Multilevel communication optimal LU
+ * and QR factorizations for hierarchical platforms" (INRIA RR-8270, 2013).
+ * Each entry point cites the passage that defines its operation.
+ *
+ * Common conventions
+ *   - Matrices are FP64, column-major, element (i, j) at A[i + j * lda],
+ *     lda >= max(1, m).  All matrix, vector and workspace pointers are DEVICE
+ *     pointers owned by the caller; the library never allocates, frees or
+ *     keeps them after the call returns.
+ *   - Every call only enqueues work on `stream` and returns without waiting.
+ *     The return value is the synchronous argument check: CA_OK (0), -i when
+ *     argument i (1-based) is invalid, or a CA_ERR_* code.  On a non-zero
+ *     return nothing has been enqueued and no memory has been touched.
+ *   - dev_info (device, 2 ints) is written asynchronously on `stream`:
+ *       dev_info[0]  LAPACK-style info: 0, or 1 + the first column whose U
+ *                    diagonal is exactly zero (LU; the factorization still
+ *                    completes, as in LAPACK getrf);
+ *       dev_info[1]  status bits: CA_STATUS_NONFINITE when a NaN or Inf was
+ *                    read from a panel.
+ *     Read it after synchronizing the stream.
+ *   - The reduction tree (ca_tree_t): the panel's rows are cut into leaves of
+ *     `leaf_rows` consecutive rows (the last leaf may be shorter).  Level l
+ *     groups consecutive nodes of the level below by fan_in[l]; inside a
+ *     group, style CA_TREE_BINARY merges neighbours two by two until one node
+ *     is left (an odd node is promoted unchanged) and CA_TREE_FLAT merges the
+ *     whole group in one step.  The last level always merges all remaining
+ *     nodes.  leaf_rows must be >= the panel width b.  (Sec. 3.1 and 3.2:
+ *     Pr subsets of the panel per level, log Pr pairwise reduction steps.)
+ *     The tree fixes the numerical result; where each node runs on the GPU
+ *     (one CTA, a thread-block cluster sharing its rows through distributed
+ *     shared memory, successive grid launches) is the library's choice.
+ */
+#ifndef CA_GB300_H
+#define CA_GB300_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CA_MAX_LEVELS 8
+#define CA_TREE_BINARY 0
+#define CA_TREE_FLAT 1
+
+typedef struct {
+  int leaf_rows;              /* rows per leaf, >= panel width               */
+  int nlevels;                /* 1 .. CA_MAX_LEVELS                          */
+  int fan_in[CA_MAX_LEVELS];  /* nodes per group at each level (>= 2 except  */
+                              /* the last level, whose value is ignored)     */
+  int style[CA_MAX_LEVELS];   /* CA_TREE_BINARY or CA_TREE_FLAT              */
+} ca_tree_t;
+
+/* return codes (negative small values -i name a bad argument i) */
+#define CA_OK 0
+#define CA_ERR_WORKSPACE -1001   /* workspace pointer null or too small      */
+#define CA_ERR_UNSUPPORTED -1002 /* valid shape this build cannot run        */
+#define CA_ERR_LAUNCH -1003      /* a kernel launch failed (CUDA error)      */
+#define CA_ERR_TREE -1004        /* malformed tree                           */
+
+#define CA_STATUS_NONFINITE 1
+
+/* Human-readable text for a return code (static storage). */
+const char *ca_strerror(int code);
+
+/* ------------------------------------------------------------------------ */
+/* Workspace queries (host only, no GPU work).                              */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of device workspace `work` needed by calu_factor / tslu for an
+ * m x n matrix with panel width b and this tree.  Also returns CA_OK or an
+ * argument error exactly as calu_factor would for the same shape. */
+int ca_calu_workspace(int m, int n, int b, const ca_tree_t *tree, size_t *work_bytes);
+
+/* Bytes of the CAQR reflector store `qtree` (the T factors of every tree
+ * node, see caqr_factor) and of the scratch workspace `work` for an m x n
+ * matrix (m >= n) with panel width b. */
+int ca_caqr_workspace(int m, int n, int b, const ca_tree_t *tree, size_t *qtree_bytes,
+                      size_t *work_bytes);
+
+/* Bytes of scratch workspace needed by caqr_geqrs. */
+int ca_geqrs_workspace(int m, int n, int nrhs, int b, const ca_tree_t *tree, size_t *work_bytes);
+
+/* ------------------------------------------------------------------------ */
+/* LU with tournament pivoting                                              */
+/* ------------------------------------------------------------------------ */
+
+/* calu_factor: P A = L U of the m x n matrix A (any m, n >= 0) by CALU, the
+ * one-level base case of 1D-ML-CALU (Algorithm "1D multilevel CALU", Sec. 3.2
+ * and the appendix): for each panel of bk = min(b, min(m,n) - kb) columns
+ *   1. tournament pivoting (TSLU) over the tree picks bk pivot rows
+ *      (leaves: GEPP on each leaf; merges: GEPP on the stacked candidate rows,
+ *      original values, children in order);
+ *   2. the rows are swapped at left and right of the panel (full width);
+ *   3. L21 = A21 U11^-1 and U12 = L11^-1 A12, with L11 U11 the root's factors;
+ *   4. A22 -= L21 U12 (Schur complement).
+ * Output in LAPACK getrf layout: unit L strictly below the diagonal, U on and
+ * above; ipiv[i] (1-based, device, min(m,n) ints) is the row swapped with
+ * row i, applied in order i = 0, 1, ....  Arguments: 1 m, 2 n, 3 A, 4 lda,
+ * 5 b (>= 1), 6 tree, 7 ipiv, 8 work, 9 lwork, 10 dev_info, 11 stream. */
+int calu_factor(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int *ipiv,
+                void *work, size_t lwork, int *dev_info, cudaStream_t stream);
+
+/* tslu: the panel factorization alone (TSLU, Sec. 3.2): calu_factor of an
+ * m x n tall-skinny matrix with a single panel of width n (n <= 256). */
+int tslu(int m, int n, double *A, int lda, const ca_tree_t *tree, int *ipiv, void *work,
+         size_t lwork, int *dev_info, cudaStream_t stream);
+
+/* calu_getrs: solve A X = B from calu_factor's output (n x n, PA = LU):
+ * apply the ipiv swaps to B, then forward substitution with the unit L and
+ * back substitution with U (Sec. 3.2: PA = LU).  B is n x nrhs (ld ldb),
+ * overwritten with X.  Arguments: 1 n, 2 nrhs, 3 LU, 4 lda, 5 ipiv, 6 B,
+ * 7 ldb, 8 stream. */
+int calu_getrs(int n, int nrhs, const double *LU, int lda, const int *ipiv, double *B, int ldb,
+               cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* QR by tree-based Householder reflections                                 */
+/* ------------------------------------------------------------------------ */
+
+/* caqr_factor: A = Q R of the m x n matrix A (m >= n) by CAQR, the one-level
+ * base case of ML-CAQR (Algorithm ML-CAQR, Sec. 3.1): for each panel,
+ *   1. TSQR: Householder QR of every leaf, then of every merge node's stacked
+ *      upper-triangular R factors (the R-elimination tree);
+ *   2. the trailing columns get every leaf's Q^T (UPFACT), then every merge
+ *      node's Q^T bottom-up (UPELIM).
+ * Q is kept in the compact Y T Y^T form (Sec. 3.1), stored in a tree
+ * structure:
+ *   - leaf j of panel k: Householder vectors strictly below the leaf-local
+ *     diagonal of its rows (unit diagonal implied), R in its top
+ *     c = min(rows, bk) rows;
+ *   - merge node: the new R overwrites the first child's R rows on and above
+ *     the diagonal; child i >= 1's block of Y (upper trapezoidal, c_i x bk)
+ *     overwrites child i's R rows on and above the diagonal (the first
+ *     child's block of Y is the identity and is not stored);
+ *   - qtree (device doubles): for each panel in order, (nleaves + nmerges)
+ *     blocks of b x b doubles (column-major, ld b): the leaves' T in leaf
+ *     order, then the merges' T in tree order (level by level, left to
+ *     right); each c x c upper-triangular T sits in the block's top-left
+ *     corner, zeros elsewhere.
+ * So the final R is the upper triangle of A's top n rows.  Arguments:
+ * 1 m, 2 n, 3 A, 4 lda, 5 b, 6 tree, 7 qtree, 8 qtree_bytes, 9 work,
+ * 10 lwork, 11 dev_info, 12 stream. */
+int caqr_factor(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, double *qtree,
+                size_t qtree_bytes, void *work, size_t lwork, int *dev_info, cudaStream_t stream);
+
+/* tsqr: the panel factorization alone (TSQR, Sec. 3.1 R-elimination tree):
+ * caqr_factor of an m x n tall-skinny matrix with one panel of width n
+ * (n <= 256). */
+int tsqr(int m, int n, double *A, int lda, const ca_tree_t *tree, double *qtree,
+         size_t qtree_bytes, void *work, size_t lwork, int *dev_info, cudaStream_t stream);
+
+/* caqr_geqrs: least-squares solve min ||A X - B|| from caqr_factor's output
+ * (same m, n, b and tree): B <- Q^T B panel by panel through the tree
+ * (leaves, then merges), then X = R^-1 (Q^T B)(0:n) in B's top n rows
+ * (Sec. 3.1: A = QR).  B is m x nrhs (ld ldb).  Arguments: 1 m, 2 n, 3 nrhs,
+ * 4 QR, 5 lda, 6 b, 7 tree, 8 qtree, 9 qtree_bytes, 10 B, 11 ldb, 12 work,
+ * 13 lwork, 14 stream. */
+int caqr_geqrs(int m, int n, int nrhs, const double *QR, int lda, int b, const ca_tree_t *tree,
+               const double *qtree, size_t qtree_bytes, double *B, int ldb, void *work,
+               size_t lwork, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Instrumentation (no counterpart in the paper): launch counts and device   */
+/* time per kernel class, measured with CUDA events recorded on the stream   */
+/* each kernel is launched on.  Classes: 0 tslu_node, 1 laswp, 2 lu_finish,  */
+/* 3 trsm_u12, 4 gemm_fp64, 5 tsqr_node, 6 tree_apply, 7 solve.              */
+/* ------------------------------------------------------------------------ */
+
+/* on = 1: create a pool of 2 * max_launches events (here, not during a
+ * factorization) and start recording an event pair around every launch;
+ * on = 0: stop.  Either way the recorded launches are cleared.  Launches
+ * beyond the pool are counted but not timed (ca_prof_read then returns 1). */
+int ca_prof_enable(int on, int max_launches);
+
+/* Sum over the recorded launches of class `cls`: count, device time in ms
+ * (waits for the recorded events) and algorithmic flops.  Host pointers;
+ * any may be NULL.  Returns CA_OK, 1 if launches were dropped, -1 for a bad
+ * class, CA_ERR_LAUNCH on a CUDA error. */
+int ca_prof_read(int cls, long long *launches, double *ms, double *flops);
+
+/* Kernel launches issued by the library since it was loaded: all classes
+ * (cls < 0) or one class. */
+long long ca_launch_count(int cls);
+
+/* Name of a kernel class ("" when out of range). */
+const char *ca_kernel_class_name(int cls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CA_GB300_H */

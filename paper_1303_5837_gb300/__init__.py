@@ -1,0 +1,21 @@
+"""GB300-native communication-avoiding LU and QR (CALU / CAQR with TSLU and
+TSQR reduction trees), after Grigori, Jacquelin and Khabou, "Multilevel
+communication optimal LU and QR factorizations for hierarchical platforms".
+
+The compute path is ``libcagb300.so`` (CUDA for sm_103a, C-ABI in
+``include/ca_gb300.h``); this package holds its build script, the thin
+ctypes binding (same names as the C-ABI) and the seeded input generators.
+"""
+_BINDING_NAMES = {
+    "calu_factor", "tslu", "calu_getrs", "caqr_factor", "tsqr", "caqr_geqrs",
+    "ca_calu_workspace", "ca_caqr_workspace", "ca_geqrs_workspace", "make_tree", "colmajor",
+    "ca_tree_t", "CaError", "BINARY", "FLAT", "load", "lib_path",
+    "ca_prof_enable", "ca_prof_read", "ca_launch_count", "ca_kernel_class_name", "KERNEL_CLASSES",
+}
+
+
+def __getattr__(name):
+    if name in _BINDING_NAMES:
+        from . import _binding
+        return getattr(_binding, name)
+    raise AttributeError(name)

@@ -1,0 +1,283 @@
+"""Thin Python binding of the C-ABI in ``include/ca_gb300.h``.
+
+Argument marshalling only: every computation runs in ``libcagb300.so``.
+Matrices are torch CUDA float64 tensors in column-major layout (shape
+(m, n), stride (1, lda)); ``colmajor`` makes such a tensor.  Work is
+enqueued on the current torch CUDA stream.  If the library is missing the
+calls raise; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+MAX_LEVELS = 8
+BINARY = 0
+FLAT = 1
+
+CA_OK = 0
+CA_ERR_WORKSPACE = -1001
+CA_ERR_UNSUPPORTED = -1002
+CA_ERR_LAUNCH = -1003
+CA_ERR_TREE = -1004
+CA_STATUS_NONFINITE = 1
+
+
+class CaError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn} returned {code}: {msg}")
+        self.code = code
+
+
+class ca_tree_t(ctypes.Structure):
+    _fields_ = [
+        ("leaf_rows", ctypes.c_int),
+        ("nlevels", ctypes.c_int),
+        ("fan_in", ctypes.c_int * MAX_LEVELS),
+        ("style", ctypes.c_int * MAX_LEVELS),
+    ]
+
+
+def make_tree(leaf_rows: int, levels=((0, BINARY),)) -> ca_tree_t:
+    """Reduction tree: leaves of ``leaf_rows`` rows, then ``levels`` as
+    (fan_in, style) pairs from the bottom up (the last level merges all)."""
+    t = ca_tree_t()
+    t.leaf_rows = int(leaf_rows)
+    levels = list(levels)
+    if not 1 <= len(levels) <= MAX_LEVELS:
+        raise ValueError("1..8 levels")
+    t.nlevels = len(levels)
+    for i, (f, s) in enumerate(levels):
+        t.fan_in[i] = int(f)
+        t.style[i] = int(s)
+    return t
+
+
+_lib = None
+
+SYMBOLS = ("ca_strerror", "ca_calu_workspace", "ca_caqr_workspace", "ca_geqrs_workspace",
+           "calu_factor", "tslu", "calu_getrs", "caqr_factor", "tsqr", "caqr_geqrs",
+           "ca_prof_enable", "ca_prof_read", "ca_launch_count", "ca_kernel_class_name")
+KERNEL_CLASSES = ("tslu_node", "laswp", "lu_finish", "trsm_u12", "gemm_fp64", "tsqr_node",
+                  "tree_apply", "solve")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcagb300.so (building it first if asked and needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: run __graft_entry__.build()")
+        _build.build()
+    L = ctypes.CDLL(path)
+    I, P, S = ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+    PS = ctypes.POINTER(ctypes.c_size_t)
+    T = ctypes.POINTER(ca_tree_t)
+    L.ca_strerror.argtypes = [I]
+    L.ca_strerror.restype = ctypes.c_char_p
+    L.ca_calu_workspace.argtypes = [I, I, I, T, PS]
+    L.ca_caqr_workspace.argtypes = [I, I, I, T, PS, PS]
+    L.ca_geqrs_workspace.argtypes = [I, I, I, I, T, PS]
+    L.calu_factor.argtypes = [I, I, P, I, I, T, P, P, S, P, P]
+    L.tslu.argtypes = [I, I, P, I, T, P, P, S, P, P]
+    L.calu_getrs.argtypes = [I, I, P, I, P, P, I, P]
+    L.caqr_factor.argtypes = [I, I, P, I, I, T, P, S, P, S, P, P]
+    L.tsqr.argtypes = [I, I, P, I, T, P, S, P, S, P, P]
+    L.caqr_geqrs.argtypes = [I, I, I, P, I, I, T, P, S, P, I, P, S, P]
+    L.ca_prof_enable.argtypes = [I, I]
+    L.ca_prof_read.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)]
+    L.ca_launch_count.argtypes = [I]
+    L.ca_launch_count.restype = ctypes.c_longlong
+    L.ca_kernel_class_name.argtypes = [I]
+    L.ca_kernel_class_name.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(fn: str, rc: int):
+    if rc != CA_OK:
+        raise CaError(fn, rc, load().ca_strerror(rc).decode())
+
+
+def colmajor(t: torch.Tensor) -> torch.Tensor:
+    """Column-major copy of a 2-D tensor (shape kept, stride (1, m))."""
+    return t.t().contiguous().t()
+
+
+def _mat(A: torch.Tensor, name: str):
+    if A.dim() != 2 or A.dtype != torch.float64 or not A.is_cuda:
+        raise TypeError(f"{name} must be a 2-D CUDA float64 tensor")
+    m, n = A.shape
+    if m > 0 and n > 0 and A.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    lda = A.stride(1) if n > 1 else max(1, m)
+    return m, n, max(lda, max(1, m))
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+def _buf(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(1, (nbytes + 7) // 8), dtype=torch.float64, device=device)
+
+
+# ---------------------------------------------------------------------------
+# workspace queries
+# ---------------------------------------------------------------------------
+
+def ca_calu_workspace(m: int, n: int, b: int, tree: ca_tree_t) -> int:
+    out = ctypes.c_size_t(0)
+    _check("ca_calu_workspace", load().ca_calu_workspace(m, n, b, ctypes.byref(tree), ctypes.byref(out)))
+    return out.value
+
+
+def ca_caqr_workspace(m: int, n: int, b: int, tree: ca_tree_t) -> tuple[int, int]:
+    q = ctypes.c_size_t(0)
+    w = ctypes.c_size_t(0)
+    _check("ca_caqr_workspace",
+           load().ca_caqr_workspace(m, n, b, ctypes.byref(tree), ctypes.byref(q), ctypes.byref(w)))
+    return q.value, w.value
+
+
+def ca_geqrs_workspace(m: int, n: int, nrhs: int, b: int, tree: ca_tree_t) -> int:
+    w = ctypes.c_size_t(0)
+    _check("ca_geqrs_workspace", load().ca_geqrs_workspace(m, n, nrhs, b, ctypes.byref(tree), ctypes.byref(w)))
+    return w.value
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C-ABI)
+# ---------------------------------------------------------------------------
+
+def calu_factor(A: torch.Tensor, b: int, tree: ca_tree_t, ipiv=None, work=None, dev_info=None,
+                stream=None):
+    """CALU in place on A.  Returns (ipiv int32[min(m,n)], dev_info int32[2])."""
+    m, n, lda = _mat(A, "A")
+    dev = A.device
+    if ipiv is None:
+        ipiv = torch.empty(max(1, min(m, n)), dtype=torch.int32, device=dev)
+    if dev_info is None:
+        dev_info = torch.zeros(2, dtype=torch.int32, device=dev)
+    if work is None:
+        work = _buf(ca_calu_workspace(m, n, b, tree), dev)
+    rc = load().calu_factor(m, n, _ptr(A), lda, b, ctypes.byref(tree), _ptr(ipiv), _ptr(work),
+                            work.numel() * work.element_size(), _ptr(dev_info), _stream(stream))
+    _check("calu_factor", rc)
+    return ipiv[: min(m, n)], dev_info
+
+
+def tslu(A: torch.Tensor, tree: ca_tree_t, ipiv=None, work=None, dev_info=None, stream=None):
+    m, n, lda = _mat(A, "A")
+    dev = A.device
+    if ipiv is None:
+        ipiv = torch.empty(max(1, min(m, n)), dtype=torch.int32, device=dev)
+    if dev_info is None:
+        dev_info = torch.zeros(2, dtype=torch.int32, device=dev)
+    if work is None:
+        work = _buf(ca_calu_workspace(m, n, max(n, 1), tree), dev)
+    rc = load().tslu(m, n, _ptr(A), lda, ctypes.byref(tree), _ptr(ipiv), _ptr(work),
+                     work.numel() * work.element_size(), _ptr(dev_info), _stream(stream))
+    _check("tslu", rc)
+    return ipiv[: min(m, n)], dev_info
+
+
+def calu_getrs(LU: torch.Tensor, ipiv: torch.Tensor, B: torch.Tensor, stream=None):
+    n, _, lda = _mat(LU, "LU")
+    nb, nrhs, ldb = _mat(B, "B")
+    rc = load().calu_getrs(n, nrhs, _ptr(LU), lda, _ptr(ipiv), _ptr(B), ldb, _stream(stream))
+    _check("calu_getrs", rc)
+    return B
+
+
+def caqr_factor(A: torch.Tensor, b: int, tree: ca_tree_t, qtree=None, work=None, dev_info=None,
+                stream=None):
+    """CAQR in place on A.  Returns (qtree float64 tensor, dev_info)."""
+    m, n, lda = _mat(A, "A")
+    dev = A.device
+    qb, wb = ca_caqr_workspace(m, n, b, tree)
+    if qtree is None:
+        qtree = _buf(qb, dev)
+    if work is None:
+        work = _buf(wb, dev)
+    if dev_info is None:
+        dev_info = torch.zeros(2, dtype=torch.int32, device=dev)
+    rc = load().caqr_factor(m, n, _ptr(A), lda, b, ctypes.byref(tree), _ptr(qtree),
+                            qtree.numel() * 8, _ptr(work), work.numel() * work.element_size(),
+                            _ptr(dev_info), _stream(stream))
+    _check("caqr_factor", rc)
+    return qtree, dev_info
+
+
+def tsqr(A: torch.Tensor, tree: ca_tree_t, qtree=None, work=None, dev_info=None, stream=None):
+    m, n, lda = _mat(A, "A")
+    dev = A.device
+    qb, wb = ca_caqr_workspace(m, n, max(n, 1), tree)
+    if qtree is None:
+        qtree = _buf(qb, dev)
+    if work is None:
+        work = _buf(wb, dev)
+    if dev_info is None:
+        dev_info = torch.zeros(2, dtype=torch.int32, device=dev)
+    rc = load().tsqr(m, n, _ptr(A), lda, ctypes.byref(tree), _ptr(qtree), qtree.numel() * 8,
+                     _ptr(work), work.numel() * work.element_size(), _ptr(dev_info), _stream(stream))
+    _check("tsqr", rc)
+    return qtree, dev_info
+
+
+def caqr_geqrs(QR: torch.Tensor, b: int, tree: ca_tree_t, qtree: torch.Tensor, B: torch.Tensor,
+               work=None, stream=None):
+    """Least squares from CAQR factors; B (m x nrhs) is overwritten, X = B[:n]."""
+    m, n, lda = _mat(QR, "QR")
+    mb, nrhs, ldb = _mat(B, "B")
+    if work is None:
+        work = _buf(ca_geqrs_workspace(m, n, nrhs, b, tree), QR.device)
+    rc = load().caqr_geqrs(m, n, nrhs, _ptr(QR), lda, b, ctypes.byref(tree), _ptr(qtree),
+                           qtree.numel() * 8, _ptr(B), ldb, _ptr(work),
+                           work.numel() * work.element_size(), _stream(stream))
+    _check("caqr_geqrs", rc)
+    return B
+
+
+# ---------------------------------------------------------------------------
+# instrumentation
+# ---------------------------------------------------------------------------
+
+def ca_prof_enable(on: bool, max_launches: int = 65536):
+    _check("ca_prof_enable", load().ca_prof_enable(1 if on else 0, int(max_launches)))
+
+
+def ca_prof_read(cls: int):
+    """(launches, device ms, algorithmic flops, dropped) of one kernel class."""
+    n = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0)
+    fl = ctypes.c_double(0)
+    rc = load().ca_prof_read(int(cls), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl))
+    if rc not in (0, 1):
+        _check("ca_prof_read", rc)
+    return n.value, ms.value, fl.value, rc == 1
+
+
+def ca_launch_count(cls: int = -1) -> int:
+    return int(load().ca_launch_count(int(cls)))
+
+
+def ca_kernel_class_name(cls: int) -> str:
+    return load().ca_kernel_class_name(int(cls)).decode()

@@ -1,0 +1,180 @@
+// ca_internal.cuh -- shared definitions of the GB300 CALU/CAQR library:
+// the reduction-tree plan (host and device), workspace layout, launch
+// helpers and small device utilities.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ca_gb300.h"
+
+namespace cagb {
+
+namespace cg = cooperative_groups;
+
+constexpr int kMaxRounds = 64;
+constexpr int kMaxPanel = 256;  // widest panel any kernel here accepts
+
+// ---------------------------------------------------------------------------
+// Reduction tree plan (Sec. 3.1 / 3.2: leaves of the panel, then log Pr
+// pairwise reduction steps per level).  A round merges groups of consecutive
+// nodes of the previous round.  Its inputs form `ngroups` groups: all but the
+// last hold `s` nodes, the last holds `s_last`.  Output o of a group merges
+// `w` consecutive inputs (w = 2 for a binary step, w = s for a flat merge);
+// a trailing output with a single input is a promotion.
+// ---------------------------------------------------------------------------
+struct RoundDesc {
+  int n_in, n_out;
+  int ngroups, s, s_last;
+  int w, h, h_last;  // merge width; outputs per full / last group
+  int mfull;         // merges in a full group
+  int merge_base;    // merges in all earlier rounds
+  int max_cnt;       // largest number of inputs of one output
+};
+
+struct Plan {
+  int nleaves;
+  int nrounds;
+  int nmerges;
+  RoundDesc r[kMaxRounds];
+};
+
+__host__ __device__ inline void round_node(const RoundDesc &rd, int o, int &start, int &cnt,
+                                           int &midx) {
+  int g = (o < (rd.ngroups - 1) * rd.h) ? o / rd.h : rd.ngroups - 1;
+  int t = o - g * rd.h;
+  int sg = (g == rd.ngroups - 1) ? rd.s_last : rd.s;
+  start = g * rd.s + t * rd.w;
+  int rem = sg - t * rd.w;
+  cnt = rem < rd.w ? rem : rd.w;
+  midx = rd.merge_base + g * rd.mfull + t;
+}
+
+// Builds the plan for `nleaves` leaves; returns false for a malformed tree.
+bool build_plan(int nleaves, const ca_tree_t &t, Plan &p);
+
+// ---------------------------------------------------------------------------
+// Argmax helpers: |x| compared through the bit pattern (an integer compare,
+// so the FP64 pipe is left to the arithmetic); ties go to the lower position.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long absbits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+struct ArgMax {
+  unsigned long long key;  // |x| bits
+  int pos;                 // position (smaller wins on equal key)
+};
+
+__device__ __forceinline__ ArgMax argmax_better(ArgMax a, ArgMax b) {
+  if (b.key > a.key || (b.key == a.key && b.pos < a.pos)) return b;
+  return a;
+}
+
+__device__ __forceinline__ ArgMax warp_argmax(ArgMax v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    ArgMax o;
+    o.key = __shfl_xor_sync(0xffffffffu, v.key, off);
+    o.pos = __shfl_xor_sync(0xffffffffu, v.pos, off);
+    v = argmax_better(v, o);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+__device__ __forceinline__ bool not_finite(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) ==
+         0x7ff0000000000000ull;
+}
+
+// ---------------------------------------------------------------------------
+// Launch accounting (prof.cu): construct a ProfScope right before a launch.
+// ---------------------------------------------------------------------------
+enum KernelClass {
+  kClsTsluNode = 0,
+  kClsLaswp,
+  kClsLuFinish,
+  kClsTrsmU12,
+  kClsGemm,
+  kClsTsqrNode,
+  kClsTreeApply,
+  kClsSolve,
+  kNumClasses
+};
+
+class ProfScope {
+ public:
+  ProfScope(int cls, cudaStream_t st, double flops);
+  ~ProfScope();
+  ProfScope(const ProfScope &) = delete;
+  ProfScope &operator=(const ProfScope &) = delete;
+
+ private:
+  int cls_;
+  cudaStream_t st_;
+  double flops_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+// round up to a multiple of 256 bytes
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------------------
+// Kernel launch entry points implemented in the .cu files (host side).
+// Every function enqueues on `st` and returns a cudaError_t.
+// ---------------------------------------------------------------------------
+
+// LU panel (panel_lu.cu)
+struct LuPanelWs {
+  int *cand[2];      // candidate row labels, [node][b]
+  int *ncand[2];     // candidate count per node
+  double *lu11;      // b x b root factors (column-major, ld b)
+  int *perm_src;     // net row permutation of the panel swap: rows
+  int *perm_dst;     //   perm_src[i] move to perm_dst[i], i < *perm_cnt
+  int *perm_cnt;
+};
+size_t lu_panel_ws_bytes(int nleaves_max, int b);
+void lu_panel_ws_carve(void *work, int nleaves_max, int b, LuPanelWs &ws);
+
+cudaError_t tslu_panel(int mk, int bk, double *P, int lda, int leaf_rows, const Plan &plan,
+                       const LuPanelWs &ws, int *ipiv_k, int ipiv_base, int *dev_info,
+                       cudaStream_t st);
+cudaError_t laswp_apply(int ncols, double *A, int lda, int row0, const LuPanelWs &ws, int bk,
+                        cudaStream_t st);
+cudaError_t lu_panel_finish(int mk, int bk, double *P, int lda, const LuPanelWs &ws,
+                            cudaStream_t st);
+cudaError_t trsm_u12(int bk, int nt, const double *L11, int ldl, double *A12, int lda,
+                     cudaStream_t st);
+
+// FP64 GEMM C -= A B (gemm_fp64.cu); A m x k, B k x n, column-major.
+cudaError_t gemm_minus_f64(int m, int n, int k, const double *A, int lda, const double *B,
+                           int ldb, double *C, int ldc, cudaStream_t st);
+
+// QR panel and tree update (panel_qr.cu)
+struct QrPanelWs {
+  int *top[2];  // first panel row of each node's R rows
+  int *c[2];    // number of R rows of each node
+};
+size_t qr_panel_ws_bytes(int nleaves_max);
+void qr_panel_ws_carve(void *work, int nleaves_max, QrPanelWs &ws);
+
+cudaError_t tsqr_panel(int mk, int bk, int b, double *P, int lda, int leaf_rows,
+                       const Plan &plan, double *Tp, const QrPanelWs &ws, int *dev_info,
+                       cudaStream_t st);
+cudaError_t tree_apply_qt(int mk, int bk, int b, const double *P, int lda, int leaf_rows,
+                          const Plan &plan, const double *Tp, double *C, int ldc, int ncols,
+                          const QrPanelWs &ws, cudaStream_t st);
+
+// triangular solves (solve.cu)
+cudaError_t getrs_swap(int n, int nrhs, const int *ipiv, double *B, int ldb, cudaStream_t st);
+cudaError_t trsm_left(bool lower, bool unit, int n, int nrhs, const double *T, int ldt, double *B,
+                      int ldb, cudaStream_t st);
+
+}  // namespace cagb

@@ -1,0 +1,81 @@
+// gemm_fp64.cu -- C -= A B in FP64 on the DFMA pipe: the Schur-complement
+// update A22 -= L21 U12 of CALU (Sec. 3.2; the dominant 2n^3/3 flops).
+//
+// On GB300 the FP64 pipe retires about two DFMA per SM per clock, so the
+// kernel is bound by the FP64 pipe, not by memory: a register-tiled
+// (8 x 8 or 4 x 4 per thread) block of C, A and B chunks staged in shared
+// memory, one CTA of 256 threads per tile.
+#include "ca_internal.cuh"
+
+namespace cagb {
+
+template <int BM, int BN, int BK>
+__global__ void __launch_bounds__(256) gemm_minus_kernel(int m, int n, int k, const double *__restrict__ A,
+                                                         int lda, const double *__restrict__ B, int ldb,
+                                                         double *__restrict__ C, int ldc) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ double As[BK][BM];
+  __shared__ double Bs[BK][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
+  double acc[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) acc[a][b] = 0.0;
+
+  for (int k0 = 0; k0 < k; k0 += BK) {
+    for (int idx = tid; idx < BK * BM; idx += 256) {
+      int i = idx % BM, kk = idx / BM;
+      int gi = i0 + i, gk = k0 + kk;
+      As[kk][i] = (gi < m && gk < k) ? A[gi + (size_t)gk * lda] : 0.0;
+    }
+    for (int idx = tid; idx < BK * BN; idx += 256) {
+      int kk = idx % BK, j = idx / BK;
+      int gj = j0 + j, gk = k0 + kk;
+      Bs[kk][j] = (gj < n && gk < k) ? B[gk + (size_t)gj * ldb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      double af[TM], bf[TN];
+#pragma unroll
+      for (int a = 0; a < TM; ++a) af[a] = As[kk][tx + 16 * a];
+#pragma unroll
+      for (int b = 0; b < TN; ++b) bf[b] = Bs[kk][ty + 16 * b];
+#pragma unroll
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) acc[a][b] = fma(af[a], bf[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int b = 0; b < TN; ++b) {
+    int gj = j0 + ty + 16 * b;
+    if (gj >= n) continue;
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+      int gi = i0 + tx + 16 * a;
+      if (gi < m) C[gi + (size_t)gj * ldc] -= acc[a][b];
+    }
+  }
+}
+
+cudaError_t gemm_minus_f64(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                           double *C, int ldc, cudaStream_t st) {
+  if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+  ProfScope ps(kClsGemm, st, 2.0 * m * (double)n * k);
+  long long big = (long long)((m + 127) / 128) * ((n + 127) / 128);
+  if (big >= 2 * 152) {
+    dim3 grid((m + 127) / 128, (n + 127) / 128);
+    gemm_minus_kernel<128, 128, 16><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
+  } else {
+    dim3 grid((m + 63) / 64, (n + 63) / 64);
+    gemm_minus_kernel<64, 64, 16><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cagb

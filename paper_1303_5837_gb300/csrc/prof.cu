@@ -1,0 +1,120 @@
+// prof.cu -- launch counting and per-kernel-class device timing.
+//
+// Every kernel launch of the library goes through a ProfScope: it counts the
+// launch and, while profiling is enabled, records a CUDA event before and
+// after it on the launching stream, together with the launch's algorithmic
+// flop count.  Events come from a pool created by ca_prof_enable, never in
+// the middle of a factorization.
+#include <mutex>
+#include <vector>
+
+#include "ca_internal.cuh"
+
+namespace cagb {
+
+namespace {
+struct Rec {
+  int cls;
+  double flops;
+  cudaEvent_t a, b;
+};
+struct Prof {
+  std::mutex mu;
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+  std::vector<Rec> recs;
+  long long dropped = 0;
+  long long launches = 0;
+  long long cls_launches[kNumClasses] = {};
+};
+Prof &prof() {
+  static Prof p;
+  return p;
+}
+const char *kNames[kNumClasses] = {"tslu_node", "laswp", "lu_finish", "trsm_u12",
+                                   "gemm_fp64", "tsqr_node", "tree_apply", "solve"};
+}  // namespace
+
+ProfScope::ProfScope(int cls, cudaStream_t st, double flops) : cls_(cls), st_(st), flops_(flops) {
+  Prof &p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.launches++;
+  p.cls_launches[cls]++;
+  if (p.on && p.next + 2 <= p.pool.size()) {
+    a_ = p.pool[p.next++];
+    b_ = p.pool[p.next++];
+    cudaEventRecord(a_, st_);
+  } else if (p.on) {
+    p.dropped++;
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (!a_) return;
+  cudaEventRecord(b_, st_);
+  Prof &p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.recs.push_back(Rec{cls_, flops_, a_, b_});
+}
+
+}  // namespace cagb
+
+using namespace cagb;
+
+extern "C" {
+
+int ca_prof_enable(int on, int max_launches) {
+  Prof &p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  if (on) {
+    if (max_launches < 1) return -2;
+    size_t want = 2 * (size_t)max_launches;
+    while (p.pool.size() < want) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return CA_ERR_LAUNCH;
+      p.pool.push_back(e);
+    }
+  }
+  p.on = on != 0;
+  p.next = 0;
+  p.recs.clear();
+  p.dropped = 0;
+  return CA_OK;
+}
+
+int ca_prof_read(int cls, long long *launches, double *ms, double *flops) {
+  if (cls < 0 || cls >= kNumClasses) return -1;
+  Prof &p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  long long n = 0;
+  double t = 0.0, f = 0.0;
+  for (const Rec &r : p.recs) {
+    if (r.cls != cls) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return CA_ERR_LAUNCH;
+    float x = 0.f;
+    if (cudaEventElapsedTime(&x, r.a, r.b) != cudaSuccess) return CA_ERR_LAUNCH;
+    ++n;
+    t += x;
+    f += r.flops;
+  }
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  if (flops) *flops = f;
+  return p.dropped ? 1 : CA_OK;
+}
+
+long long ca_launch_count(int cls) {
+  Prof &p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  if (cls < 0) return p.launches;
+  if (cls >= kNumClasses) return -1;
+  return p.cls_launches[cls];
+}
+
+const char *ca_kernel_class_name(int cls) {
+  if (cls < 0 || cls >= kNumClasses) return "";
+  return kNames[cls];
+}
+
+}  // extern "C"

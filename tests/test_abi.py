@@ -1,0 +1,77 @@
+"""The C-ABI library builds for sm_103a, loads, exports every symbol the
+header declares, and rejects bad arguments on the host before any launch."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ca_gb300.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b([a-z_0-9]+)\s*\(", src)) - {"if", "sizeof"})
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1303_5837_gb300 import _binding
+    return _binding.load()
+
+
+def test_header_declares_expected_entry_points():
+    names = declared_functions()
+    for n in ["calu_factor", "caqr_factor", "tslu", "tsqr", "calu_getrs", "caqr_geqrs",
+              "ca_calu_workspace", "ca_caqr_workspace", "ca_geqrs_workspace", "ca_strerror"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_abi():
+    from paper_1303_5837_gb300 import _binding
+    for name in declared_functions():
+        if name != "ca_strerror":
+            assert hasattr(_binding, name), name
+
+
+def test_argument_errors_without_gpu(lib):
+    from paper_1303_5837_gb300 import _binding as B
+    t = B.make_tree(128)
+    size = ctypes.c_size_t()
+    assert lib.ca_calu_workspace(-1, 10, 64, ctypes.byref(t), ctypes.byref(size)) == -1
+    assert lib.ca_calu_workspace(10, -1, 64, ctypes.byref(t), ctypes.byref(size)) == -2
+    assert lib.ca_calu_workspace(10, 10, 0, ctypes.byref(t), ctypes.byref(size)) == -3
+    small = B.make_tree(32)   # leaf_rows < b
+    assert lib.ca_calu_workspace(100, 100, 64, ctypes.byref(small), ctypes.byref(size)) == -4
+    assert lib.ca_calu_workspace(1024, 1024, 64, ctypes.byref(t), ctypes.byref(size)) == 0
+    assert size.value > 0
+    q = ctypes.c_size_t()
+    assert lib.ca_caqr_workspace(10, 20, 8, ctypes.byref(t), ctypes.byref(q), ctypes.byref(size)) == -2
+    assert lib.ca_caqr_workspace(1024, 512, 64, ctypes.byref(t), ctypes.byref(q), ctypes.byref(size)) == 0
+    # bad arguments are reported before anything touches the (null) stream
+    assert lib.calu_factor(-1, 4, None, 4, 4, ctypes.byref(t), None, None, 0, None, None) == -1
+    assert lib.calu_factor(4, 4, None, 4, 4, ctypes.byref(t), None, None, 0, None, None) == -3
+    assert lib.calu_factor(8, 8, ctypes.c_void_p(16), 4, 4, ctypes.byref(t), None, None, 0, None, None) == -4
+    assert lib.calu_getrs(-3, 1, None, 1, None, None, 1, None) == -1
+    assert lib.caqr_factor(4, 8, None, 4, 4, ctypes.byref(t), None, 0, None, 0, None, None) == -2
+    assert lib.ca_strerror(-1001).decode().startswith("workspace")
+    wide = B.make_tree(512)
+    assert lib.ca_calu_workspace(4096, 4096, 256, ctypes.byref(wide), ctypes.byref(size)) == -1002
+
+
+def test_workspace_matches_tree_counts(lib):
+    """qtree bytes = sum over panels of (leaves + merges) b^2 doubles, the
+    layout the header documents (counts from the oracle's tree)."""
+    import oracle
+    from paper_1303_5837_gb300 import _binding as B
+    for (m, n, b, L, lv) in [(1000, 300, 32, 64, [(2, 0), (0, 0)]), (777, 64, 64, 128, [(3, 1), (0, 0)]),
+                             (4096, 128, 64, 256, [(4, 0), (4, 0), (0, 1)])]:
+        qb, _ = B.ca_caqr_workspace(m, n, b, B.make_tree(L, lv))
+        assert qb == 8 * oracle.caqr_tcount(m, n, b, oracle.make_tree(L, lv))
