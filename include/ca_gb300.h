@@ -113,6 +113,32 @@ int calu_factor(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, 
 int tslu(int m, int n, double *A, int lda, const ca_tree_t *tree, int *ipiv, void *work,
          size_t lwork, int *dev_info, cudaStream_t stream);
 
+/* tslu_noalloc: tslu for callers that cannot allocate device memory.  The
+ * paper has no counterpart; this is a deployment convenience.  Some callers
+ * cannot hand the library a workspace: their device memory is owned by
+ * another allocator (a framework's caching allocator, a serving process that
+ * reserved its HBM budget up front), or they cannot call cudaMalloc on their
+ * path because it may synchronize the device and has no latency bound.  This
+ * entry point takes the same inputs and outputs as tslu (arguments: 1 m,
+ * 2 n, 3 A, 4 lda, 5 tree, 6 ipiv, 7 dev_info, 8 stream) and allocates
+ * nothing: its scratch is one static device array of
+ * CA_TSLU_NOALLOC_SCRATCH_BYTES compiled into the library, present on every
+ * GPU that loads it until the process exits.
+ *   - Limit: shapes whose ca_calu_workspace(m, n, n, tree) exceeds
+ *     CA_TSLU_NOALLOC_SCRATCH_BYTES are rejected with CA_ERR_WORKSPACE before
+ *     anything is enqueued (about 4M rows at n = 32 with 256-row leaves).
+ *   - The first call on each device (with that device current) looks up the
+ *     array's device address; make that first call before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents
+ *     (every byte a call reads is written earlier in the same call).  Calls
+ *     that overlap on the GPU (different streams, or different host threads)
+ *     race on it: serialize them.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine (with the
+ *     instrumentation below switched off). */
+#define CA_TSLU_NOALLOC_SCRATCH_BYTES (16u << 20)
+int tslu_noalloc(int m, int n, double *A, int lda, const ca_tree_t *tree, int *ipiv,
+                 int *dev_info, cudaStream_t stream);
+
 /* calu_getrs: solve A X = B from calu_factor's output (n x n, PA = LU):
  * apply the ipiv swaps to B, then forward substitution with the unit L and
  * back substitution with U (Sec. 3.2: PA = LU).  B is n x nrhs (ld ldb),

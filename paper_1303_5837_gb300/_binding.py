@@ -281,3 +281,18 @@ def ca_launch_count(cls: int = -1) -> int:
 
 def ca_kernel_class_name(cls: int) -> str:
     return load().ca_kernel_class_name(int(cls)).decode()
+
+
+def tslu_noalloc(A: torch.Tensor, tree: ca_tree_t, ipiv=None, dev_info=None, stream=None):
+    """tslu with the library's static scratch instead of a workspace, for
+    callers that cannot allocate device memory; see include/ca_gb300.h for the
+    size limit and the rule that overlapping calls must be serialized."""
+    L = load()
+    L.tslu_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                               ctypes.POINTER(ca_tree_t), ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p]
+    m, n, lda = _mat(A, "A")
+    rc = L.tslu_noalloc(m, n, _ptr(A), lda, ctypes.byref(tree), _ptr(ipiv), _ptr(dev_info),
+                        _stream(stream))
+    _check("tslu_noalloc", rc)
+    return ipiv, dev_info
