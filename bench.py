@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--cpu-n", type=int, default=1024, help="oracle sample size")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--mixed-slices", type=int, default=4)
+    p.add_argument("--mixed-exact", type=int, default=1)
+    p.add_argument("--no-mixed", action="store_true")
     return p.parse_args()
 
 
@@ -295,6 +298,11 @@ def run_ours(a, rank: int, world: int, local: int):
     for v in kernels.values():
         v["share"] = v["ms"] / tot_kms
 
+    # ---- LU alone: plain FP64 vs mixed + refinement vs 7-digit emulation ----
+    lu_forms = None
+    if not a.no_mixed:
+        lu_forms = lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world)
+
     # ---- end to end through the public API with host buffers --------------
     e2e = None
     if a.e2e_steps > 0:
@@ -351,8 +359,85 @@ def run_ours(a, rank: int, world: int, local: int):
         "gpu_launches": launches,
         "kernels": kernels,
         "check": {"x_rel_err_calu": err_lu, "x_rel_err_caqr": err_qr},
+        "lu_forms": lu_forms,
     }
     print(json.dumps(line), flush=True)
+
+
+def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
+    """CALU solve of A x = b three ways, each timed over a.steps runs after one
+    warm-up: plain FP64 (calu_factor + calu_getrs), the reduced-precision
+    update on the tensor cores with FP64 refinement (calu_gesv_mixed), and the
+    exact 7-digit tensor-core update (FP64-accurate factors) + calu_getrs."""
+    n, b = a.n, a.b
+    lu_flops = 2.0 * n ** 3 / 3.0 + 2.0 * n * n * a.nrhs
+    A = torch.empty_like(A0)
+    X = torch.empty_like(B0)
+    ipiv = torch.empty(n, dtype=torch.int32, device=A0.device)
+    info = torch.zeros(2, dtype=torch.int32, device=A0.device)
+    out = {}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        res = None
+        for _ in range(a.steps):
+            res = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return allreduce_max(e0.elapsed_time(e1), world) / a.steps, res
+
+    def berr_of(Xs):
+        R = B0 - A0 @ Xs
+        num = R.abs().amax(0)
+        den = A0.abs().sum(1).amax() * Xs.abs().amax(0) + B0.abs().amax(0)
+        return float((num / den).max())
+
+    work = torch.empty((ca.ca_calu_workspace(n, n, b, tree) + 7) // 8, dtype=torch.float64, device=A0.device)
+
+    def plain():
+        A.copy_(A0)
+        X.copy_(B0)
+        ca.calu_factor(A, b, tree, ipiv=ipiv, work=work, dev_info=info)
+        ca.calu_getrs(A, ipiv, X)
+
+    ms, _ = timed(plain)
+    out["fp64"] = {"ms": ms, "gflops": lu_flops / ms / 1e6, "berr": berr_of(X),
+                   "form": "calu_factor + calu_getrs, FP64 DFMA update"}
+    S, ex = a.mixed_slices, bool(a.mixed_exact)
+    LU = torch.empty_like(A0)
+    wmix = torch.empty((ca.ca_gesv_mixed_workspace(n, a.nrhs, b, tree, S, ex) + 7) // 8,
+                       dtype=torch.float64, device=A0.device)
+
+    def mixed():
+        _, it, be, _ = ca.calu_gesv_mixed(A0, B0, b, tree, slices=S, exact=ex, max_iter=30, tol=1e-14,
+                                          LU=LU, X=X, ipiv=ipiv, work=wmix, dev_info=info)
+        return it, be
+
+    ms, (it, be) = timed(mixed)
+    out["mixed_ir"] = {"ms": ms, "gflops": lu_flops / ms / 1e6, "iters": it, "berr": be,
+                       "berr_check": berr_of(X), "slices": S, "exact": ex,
+                       "x_rel_err": float(torch.linalg.norm(X - x_true) / torch.linalg.norm(x_true)),
+                       "speedup_vs_fp64": out["fp64"]["ms"] / ms,
+                       "form": f"calu_gesv_mixed: {S}-digit bf16 tensor-core update + FP64 refinement"}
+    wemu = torch.empty((ca.ca_calu_mixed_workspace(n, n, b, tree, 7, True) + 7) // 8, dtype=torch.float64,
+                       device=A0.device)
+
+    def emulated():
+        A.copy_(A0)
+        X.copy_(B0)
+        ca.calu_factor_mixed(A, b, tree, slices=7, exact=True, ipiv=ipiv, work=wemu, dev_info=info)
+        ca.calu_getrs(A, ipiv, X)
+
+    ms, _ = timed(emulated)
+    out["fp64_emulated"] = {"ms": ms, "gflops": lu_flops / ms / 1e6, "berr": berr_of(X),
+                            "speedup_vs_fp64": out["fp64"]["ms"] / ms,
+                            "form": "calu_factor_mixed(7 exact digits) + calu_getrs: FP64-accurate update "
+                                    "on the tensor cores"}
+    return out
 
 
 def conditioned_device(n, cond, seed, dev):

@@ -194,10 +194,70 @@ int caqr_geqrs(int m, int n, int nrhs, const double *QR, int lda, int b, const c
                size_t lwork, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Reduced-precision trailing update on the tensor cores                    */
+/* ------------------------------------------------------------------------ */
+
+/* ca_gemm_minus_mixed: C -= A B, the dense contraction of the trailing update
+ * (Sec. 3.2: A22 -= L21 U12), computed on the tcgen05 tensor cores.  A is
+ * m x k, B is k x n, C is m x n, all FP64 column-major.  Each row of A and
+ * each column of B is scaled by a power of two and cut, exactly, into
+ * `slices` signed base-256 digits held in bf16; the digit products with
+ * k + l <= slices + 1 are summed on the tensor cores in FP32 and applied to C
+ * in FP64.
+ *   exact = 0: one FP32 accumulator (digits pre-scaled); error about 2^-20
+ *              relative to max|row of A| max|column of B| (slices >= 3);
+ *   exact = 1: one accumulator per digit diagonal, each an exact FP32 sum of
+ *              integers below 2^24 (needs k <= 128, slices <= 7); the only
+ *              error is the dropped digits, about 2^(-8 slices) relative to
+ *              the same scale (slices = 7: FP64-level).
+ * Limits: 1 <= k <= 256, 1 <= slices <= 8.  dev_status (device int) gets a
+ * bit (2, 4 or 8) if a bounded wait in the kernel timed out (the result is
+ * then not applied).  Arguments: 1 m, 2 n, 3 k, 4 A, 5 lda, 6 B, 7 ldb, 8 C,
+ * 9 ldc, 10 slices, 11 exact, 12 work, 13 lwork, 14 dev_status, 15 stream. */
+int ca_gemm_mixed_workspace(int m, int n, int k, int slices, int exact, size_t *work_bytes);
+int ca_gemm_minus_mixed(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                        double *C, int ldc, int slices, int exact, void *work, size_t lwork,
+                        int *dev_status, cudaStream_t stream);
+
+/* calu_factor_mixed: calu_factor with the Schur-complement update A22 -= L21
+ * U12 on the tensor cores (ca_gemm_minus_mixed with `slices` digits and the
+ * `exact` accumulation mode).  Tournament pivoting, the panel, L21 and U12
+ * stay in FP64, so the pivots are chosen in FP64 on the reduced-precision
+ * trailing matrix.  With exact = 1 and slices = 7 the update is FP64-accurate.
+ * dev_info[1] also gets the kernel's timeout bits (2, 4, 8).  Arguments:
+ * 1 m, 2 n, 3 A, 4 lda, 5 b, 6 tree, 7 slices, 8 exact, 9 ipiv, 10 work,
+ * 11 lwork, 12 dev_info, 13 stream. */
+int ca_calu_mixed_workspace(int m, int n, int b, const ca_tree_t *tree, int slices, int exact,
+                            size_t *work_bytes);
+int calu_factor_mixed(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int slices,
+                      int exact, int *ipiv, void *work, size_t lwork, int *dev_info,
+                      cudaStream_t stream);
+
+/* calu_gesv_mixed: solve A X = B (n x n, nrhs <= 256) by the mixed
+ * factorization plus FP64 iterative refinement: LU <- A (copy in the caller's
+ * LU buffer), calu_factor_mixed, X = U^-1 L^-1 P B, then repeat R = B - A X
+ * (FP64), stop when the normwise backward error
+ * max_j ||R_j||inf / (||A||inf ||X_j||inf + ||B_j||inf) <= tol, when it fails
+ * to halve twice in a row, or after max_iter corrections X += (LU)^-1 R.
+ * Unlike the other entry points this call waits for the stream (it reads the
+ * backward error on the host once per step).  *iters gets the number of
+ * corrections, *berr the final backward error (host pointers, may be NULL).
+ * Arguments: 1 n, 2 nrhs, 3 A, 4 lda, 5 b, 6 tree, 7 slices, 8 exact, 9 LU,
+ * 10 ldlu, 11 ipiv, 12 B, 13 ldb, 14 X, 15 ldx, 16 work, 17 lwork,
+ * 18 max_iter, 19 tol, 20 iters, 21 berr, 22 dev_info, 23 stream. */
+int ca_gesv_mixed_workspace(int n, int nrhs, int b, const ca_tree_t *tree, int slices, int exact,
+                            size_t *work_bytes);
+int calu_gesv_mixed(int n, int nrhs, const double *A, int lda, int b, const ca_tree_t *tree,
+                    int slices, int exact, double *LU, int ldlu, int *ipiv, const double *B, int ldb,
+                    double *X, int ldx, void *work, size_t lwork, int max_iter, double tol,
+                    int *iters, double *berr, int *dev_info, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Instrumentation (no counterpart in the paper): launch counts and device   */
 /* time per kernel class, measured with CUDA events recorded on the stream   */
 /* each kernel is launched on.  Classes: 0 tslu_node, 1 laswp, 2 lu_finish,  */
-/* 3 trsm_u12, 4 gemm_fp64, 5 tsqr_node, 6 tree_apply, 7 solve.              */
+/* 3 trsm_u12, 4 gemm_fp64, 5 tsqr_node, 6 tree_apply, 7 solve,              */
+/* 8 split_bf16, 9 gemm_tc, 10 refine.                                        */
 /* ------------------------------------------------------------------------ */
 
 /* on = 1: create a pool of 2 * max_launches events (here, not during a

@@ -61,9 +61,11 @@ _lib = None
 
 SYMBOLS = ("ca_strerror", "ca_calu_workspace", "ca_caqr_workspace", "ca_geqrs_workspace",
            "calu_factor", "tslu", "calu_getrs", "caqr_factor", "tsqr", "caqr_geqrs",
-           "ca_prof_enable", "ca_prof_read", "ca_launch_count", "ca_kernel_class_name")
+           "ca_prof_enable", "ca_prof_read", "ca_launch_count", "ca_kernel_class_name",
+           "ca_gemm_mixed_workspace", "ca_gemm_minus_mixed", "ca_calu_mixed_workspace",
+           "calu_factor_mixed", "ca_gesv_mixed_workspace", "calu_gesv_mixed")
 KERNEL_CLASSES = ("tslu_node", "laswp", "lu_finish", "trsm_u12", "gemm_fp64", "tsqr_node",
-                  "tree_apply", "solve")
+                  "tree_apply", "solve", "split_bf16", "gemm_tc", "refine")
 
 
 def lib_path() -> str:
@@ -95,6 +97,13 @@ def load(build_if_missing: bool = True):
     L.caqr_factor.argtypes = [I, I, P, I, I, T, P, S, P, S, P, P]
     L.tsqr.argtypes = [I, I, P, I, T, P, S, P, S, P, P]
     L.caqr_geqrs.argtypes = [I, I, I, P, I, I, T, P, S, P, I, P, S, P]
+    L.ca_gemm_mixed_workspace.argtypes = [I, I, I, I, I, PS]
+    L.ca_gemm_minus_mixed.argtypes = [I, I, I, P, I, P, I, P, I, I, I, P, S, P, P]
+    L.ca_calu_mixed_workspace.argtypes = [I, I, I, T, I, I, PS]
+    L.calu_factor_mixed.argtypes = [I, I, P, I, I, T, I, I, P, P, S, P, P]
+    L.ca_gesv_mixed_workspace.argtypes = [I, I, I, T, I, I, PS]
+    L.calu_gesv_mixed.argtypes = [I, I, P, I, I, T, I, I, P, I, P, P, I, P, I, P, S, I,
+                                  ctypes.c_double, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double), P, P]
     L.ca_prof_enable.argtypes = [I, I]
     L.ca_prof_read.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)]
@@ -296,3 +305,91 @@ def tslu_noalloc(A: torch.Tensor, tree: ca_tree_t, ipiv=None, dev_info=None, str
                         _stream(stream))
     _check("tslu_noalloc", rc)
     return ipiv, dev_info
+
+
+def ca_gemm_mixed_workspace(m: int, n: int, k: int, slices: int, exact: bool) -> int:
+    w = ctypes.c_size_t(0)
+    _check("ca_gemm_mixed_workspace",
+           load().ca_gemm_mixed_workspace(m, n, k, slices, 1 if exact else 0, ctypes.byref(w)))
+    return w.value
+
+
+def ca_gemm_minus_mixed(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, slices: int = 3,
+                        exact: bool = False, work=None, dev_status=None, stream=None):
+    """C -= A B on the tensor cores (split bf16 digits); returns dev_status."""
+    m, k, lda = _mat(A, "A")
+    k2, n, ldb = _mat(B, "B")
+    mc, nc, ldc = _mat(C, "C")
+    if k2 != k or mc != m or nc != n:
+        raise ValueError("shape mismatch")
+    if work is None:
+        work = _buf(ca_gemm_mixed_workspace(m, n, k, slices, exact), A.device)
+    if dev_status is None:
+        dev_status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    rc = load().ca_gemm_minus_mixed(m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, slices,
+                                    1 if exact else 0, _ptr(work), work.numel() * 8,
+                                    _ptr(dev_status), _stream(stream))
+    _check("ca_gemm_minus_mixed", rc)
+    return dev_status
+
+
+def ca_calu_mixed_workspace(m: int, n: int, b: int, tree: ca_tree_t, slices: int, exact: bool) -> int:
+    w = ctypes.c_size_t(0)
+    _check("ca_calu_mixed_workspace",
+           load().ca_calu_mixed_workspace(m, n, b, ctypes.byref(tree), slices, 1 if exact else 0,
+                                          ctypes.byref(w)))
+    return w.value
+
+
+def calu_factor_mixed(A: torch.Tensor, b: int, tree: ca_tree_t, slices: int = 3, exact: bool = False,
+                      ipiv=None, work=None, dev_info=None, stream=None):
+    m, n, lda = _mat(A, "A")
+    dev = A.device
+    if ipiv is None:
+        ipiv = torch.empty(max(1, min(m, n)), dtype=torch.int32, device=dev)
+    if dev_info is None:
+        dev_info = torch.zeros(2, dtype=torch.int32, device=dev)
+    if work is None:
+        work = _buf(ca_calu_mixed_workspace(m, n, b, tree, slices, exact), dev)
+    rc = load().calu_factor_mixed(m, n, _ptr(A), lda, b, ctypes.byref(tree), slices, 1 if exact else 0,
+                                  _ptr(ipiv), _ptr(work), work.numel() * 8, _ptr(dev_info), _stream(stream))
+    _check("calu_factor_mixed", rc)
+    return ipiv[: min(m, n)], dev_info
+
+
+def ca_gesv_mixed_workspace(n: int, nrhs: int, b: int, tree: ca_tree_t, slices: int, exact: bool) -> int:
+    w = ctypes.c_size_t(0)
+    _check("ca_gesv_mixed_workspace",
+           load().ca_gesv_mixed_workspace(n, nrhs, b, ctypes.byref(tree), slices, 1 if exact else 0,
+                                          ctypes.byref(w)))
+    return w.value
+
+
+def calu_gesv_mixed(A: torch.Tensor, B: torch.Tensor, b: int, tree: ca_tree_t, slices: int = 3,
+                    exact: bool = False, max_iter: int = 30, tol: float = 1e-14, LU=None, X=None,
+                    ipiv=None, work=None, dev_info=None, stream=None):
+    """Mixed-precision CALU + FP64 iterative refinement.
+    Returns (X, iterations, backward error, dev_info); waits for the stream."""
+    n, n2, lda = _mat(A, "A")
+    nb, nrhs, ldb = _mat(B, "B")
+    dev = A.device
+    if LU is None:
+        LU = torch.empty((n, n), dtype=torch.float64, device=dev).t().contiguous().t()
+    if X is None:
+        X = torch.empty((n, nrhs), dtype=torch.float64, device=dev).t().contiguous().t()
+    if ipiv is None:
+        ipiv = torch.empty(max(1, n), dtype=torch.int32, device=dev)
+    if dev_info is None:
+        dev_info = torch.zeros(2, dtype=torch.int32, device=dev)
+    if work is None:
+        work = _buf(ca_gesv_mixed_workspace(n, nrhs, b, tree, slices, exact), dev)
+    _, _, ldlu = _mat(LU, "LU")
+    _, _, ldx = _mat(X, "X")
+    it = ctypes.c_int(0)
+    be = ctypes.c_double(0)
+    rc = load().calu_gesv_mixed(n, nrhs, _ptr(A), lda, b, ctypes.byref(tree), slices, 1 if exact else 0,
+                                _ptr(LU), ldlu, _ptr(ipiv), _ptr(B), ldb, _ptr(X), ldx, _ptr(work),
+                                work.numel() * 8, max_iter, tol, ctypes.byref(it), ctypes.byref(be),
+                                _ptr(dev_info), _stream(stream))
+    _check("calu_gesv_mixed", rc)
+    return X, it.value, be.value, dev_info

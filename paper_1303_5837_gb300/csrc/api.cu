@@ -95,6 +95,7 @@ using namespace cagb;
 namespace {
 
 constexpr int kMaxB = 128;
+constexpr int kMaxRhsHost = 256;  // right-hand sides whose backward error is checked
 
 int check_tree(const ca_tree_t *t, int b) {
   if (!t) return 1;
@@ -155,6 +156,56 @@ int qr_shape(int m, int n, int b, const ca_tree_t *tree, int *nl_max, size_t *qb
   }
   *qbytes = q;
   return CA_OK;
+}
+
+// Panel loop of CALU (Algorithm "1D multilevel CALU" with one level): the
+// trailing update runs in FP64 (tcws == nullptr) or on the tensor cores with
+// `slices` digits (reduced precision, exact = per-diagonal accumulators).
+int calu_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int *ipiv, void *work, int nl,
+             void *tcws, int slices, int exact, int *dev_info, cudaStream_t stream) {
+  if (cudaMemsetAsync(dev_info, 0, 2 * sizeof(int), stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  const int K = m < n ? m : n;
+  if (K == 0) return CA_OK;
+  const int bw = b < kMaxB ? b : kMaxB;
+  LuPanelWs ws;
+  lu_panel_ws_carve(work, nl, bw, ws);
+  const int L = tree->leaf_rows;
+  for (int kb = 0; kb < K; kb += b) {
+    const int bk = (K - kb < b) ? K - kb : b;
+    const int mk = m - kb;
+    Plan plan;
+    if (!build_plan(nleaves_of(mk, L), *tree, plan)) return CA_ERR_TREE;
+    double *P = A + kb + (size_t)kb * lda;
+    // 1. tournament pivoting over the tree (TSLU)
+    if (tslu_panel(mk, bk, P, lda, L, plan, ws, ipiv + kb, kb, dev_info, stream) != cudaSuccess)
+      return CA_ERR_LAUNCH;
+    // 2. swap rows at left and right of the panel
+    if (laswp_apply(n, A, lda, kb, ws, bk, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+    // 3. L11 \ U11 into place, L21 = A21 U11^-1
+    if (lu_panel_finish(mk, bk, P, lda, ws, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+    const int nt = n - kb - bk;
+    if (nt > 0) {
+      double *A12 = A + kb + (size_t)(kb + bk) * lda;
+      // 4. U12 = L11^-1 A12
+      if (trsm_u12(bk, nt, ws.lu11, bk, A12, lda, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+      // 5. A22 -= L21 U12
+      if (mk - bk > 0) {
+        cudaError_t e;
+        if (tcws)
+          e = gemm_minus_tc(mk - bk, nt, bk, P + bk, lda, A12, lda, A12 + bk, lda, slices, exact, tcws,
+                            dev_info + 1, stream);
+        else
+          e = gemm_minus_f64(mk - bk, nt, bk, P + bk, lda, A12, lda, A12 + bk, lda, stream);
+        if (e != cudaSuccess) return CA_ERR_LAUNCH;
+      }
+    }
+  }
+  return CA_OK;
+}
+
+size_t calu_mixed_ws(int m, int n, int b, int nl, int slices) {
+  const int bw = b < kMaxB ? b : kMaxB;
+  return align256(lu_panel_ws_bytes(nl, bw)) + tc_gemm_ws_bytes(m, n, bw, slices);
 }
 
 }  // namespace
@@ -228,36 +279,7 @@ int calu_factor(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, 
   if (!dev_info) return -10;
   const int bw = b < kMaxB ? b : kMaxB;
   if (K > 0 && (!work || lwork < lu_panel_ws_bytes(nl, bw))) return CA_ERR_WORKSPACE;
-  if (cudaMemsetAsync(dev_info, 0, 2 * sizeof(int), stream) != cudaSuccess) return CA_ERR_LAUNCH;
-  if (K == 0) return CA_OK;
-  LuPanelWs ws;
-  lu_panel_ws_carve(work, nl, bw, ws);
-  const int L = tree->leaf_rows;
-  for (int kb = 0; kb < K; kb += b) {
-    const int bk = (K - kb < b) ? K - kb : b;
-    const int mk = m - kb;
-    Plan plan;
-    if (!build_plan(nleaves_of(mk, L), *tree, plan)) return CA_ERR_TREE;
-    double *P = A + kb + (size_t)kb * lda;
-    // 1. tournament pivoting over the tree (TSLU)
-    if (tslu_panel(mk, bk, P, lda, L, plan, ws, ipiv + kb, kb, dev_info, stream) != cudaSuccess)
-      return CA_ERR_LAUNCH;
-    // 2. swap rows at left and right of the panel
-    if (laswp_apply(n, A, lda, kb, ws, bk, stream) != cudaSuccess) return CA_ERR_LAUNCH;
-    // 3. L11 \ U11 into place, L21 = A21 U11^-1
-    if (lu_panel_finish(mk, bk, P, lda, ws, stream) != cudaSuccess) return CA_ERR_LAUNCH;
-    const int nt = n - kb - bk;
-    if (nt > 0) {
-      double *A12 = A + kb + (size_t)(kb + bk) * lda;
-      // 4. U12 = L11^-1 A12
-      if (trsm_u12(bk, nt, ws.lu11, bk, A12, lda, stream) != cudaSuccess) return CA_ERR_LAUNCH;
-      // 5. A22 -= L21 U12
-      if (mk - bk > 0 &&
-          gemm_minus_f64(mk - bk, nt, bk, P + bk, lda, A12, lda, A12 + bk, lda, stream) != cudaSuccess)
-        return CA_ERR_LAUNCH;
-    }
-  }
-  return CA_OK;
+  return calu_run(m, n, A, lda, b, tree, ipiv, work, nl, nullptr, 0, 0, dev_info, stream);
 }
 
 int tslu(int m, int n, double *A, int lda, const ca_tree_t *tree, int *ipiv, void *work,
@@ -367,6 +389,157 @@ int caqr_geqrs(int m, int n, int nrhs, const double *QR, int lda, int b, const c
     off += (size_t)(plan.nleaves + plan.nmerges) * b * b;
   }
   if (trsm_left(false, false, n, nrhs, QR, lda, B, ldb, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  return CA_OK;
+}
+
+int ca_gemm_mixed_workspace(int m, int n, int k, int slices, int exact, size_t *work_bytes) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (k < 0) return -3;
+  if (slices < 1 || slices > 8) return -4;
+  if (!tc_gemm_supported(k > 0 ? k : 1, slices, exact)) return CA_ERR_UNSUPPORTED;
+  if (!work_bytes) return -6;
+  *work_bytes = tc_gemm_ws_bytes(m, n, k, slices);
+  return CA_OK;
+}
+
+int ca_gemm_minus_mixed(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                        double *C, int ldc, int slices, int exact, void *work, size_t lwork,
+                        int *dev_status, cudaStream_t stream) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (k < 0) return -3;
+  if (m > 0 && k > 0 && !A) return -4;
+  if (lda < (m > 1 ? m : 1)) return -5;
+  if (k > 0 && n > 0 && !B) return -6;
+  if (ldb < (k > 1 ? k : 1)) return -7;
+  if (m > 0 && n > 0 && !C) return -8;
+  if (ldc < (m > 1 ? m : 1)) return -9;
+  if (slices < 1 || slices > 8) return -10;
+  if (m == 0 || n == 0 || k == 0) return CA_OK;
+  if (!tc_gemm_supported(k, slices, exact)) return CA_ERR_UNSUPPORTED;
+  if (!work || lwork < tc_gemm_ws_bytes(m, n, k, slices)) return CA_ERR_WORKSPACE;
+  if (!dev_status) return -14;
+  if (gemm_minus_tc(m, n, k, A, lda, B, ldb, C, ldc, slices, exact, work, dev_status, stream) != cudaSuccess)
+    return CA_ERR_LAUNCH;
+  return CA_OK;
+}
+
+int ca_calu_mixed_workspace(int m, int n, int b, const ca_tree_t *tree, int slices, int exact,
+                            size_t *work_bytes) {
+  int nl;
+  int rc = lu_shape(m, n, b, tree, &nl);
+  if (rc == -5 || rc == -6) rc = (rc == -5) ? -3 : -4;
+  if (rc != CA_OK) return rc;
+  if (slices < 1 || slices > 8) return -5;
+  if (!tc_gemm_supported(b < kMaxB ? b : kMaxB, slices, exact)) return CA_ERR_UNSUPPORTED;
+  if (!work_bytes) return -7;
+  *work_bytes = calu_mixed_ws(m, n, b, nl, slices);
+  return CA_OK;
+}
+
+int calu_factor_mixed(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int slices, int exact,
+                      int *ipiv, void *work, size_t lwork, int *dev_info, cudaStream_t stream) {
+  int nl;
+  int rc = lu_shape(m, n, b, tree, &nl);
+  if (rc != CA_OK) return rc;
+  if (lda < (m > 1 ? m : 1)) return -4;
+  const int K = m < n ? m : n;
+  if (K > 0 && !A) return -3;
+  if (slices < 1 || slices > 8) return -7;
+  if (!tc_gemm_supported(b < kMaxB ? b : kMaxB, slices, exact)) return CA_ERR_UNSUPPORTED;
+  if (K > 0 && !ipiv) return -9;
+  if (!dev_info) return -12;
+  const size_t need = calu_mixed_ws(m, n, b, nl, slices);
+  if (K > 0 && (!work || lwork < need)) return CA_ERR_WORKSPACE;
+  const int bw = b < kMaxB ? b : kMaxB;
+  char *tcws = (char *)work + align256(lu_panel_ws_bytes(nl, bw));
+  return calu_run(m, n, A, lda, b, tree, ipiv, work, nl, tcws, slices, exact, dev_info, stream);
+}
+
+int ca_gesv_mixed_workspace(int n, int nrhs, int b, const ca_tree_t *tree, int slices, int exact,
+                            size_t *work_bytes) {
+  if (nrhs < 0) return -2;
+  size_t w = 0;
+  int rc = ca_calu_mixed_workspace(n, n, b, tree, slices, exact, &w);
+  if (rc == -1 || rc == -2) return -1;
+  if (rc != CA_OK) return rc;  // b, tree, slices are arguments 3, 4, 5 in both calls
+  if (!work_bytes) return -7;
+  *work_bytes = align256(w) + ir_ws_bytes(n, nrhs > 0 ? nrhs : 1);
+  return CA_OK;
+}
+
+int calu_gesv_mixed(int n, int nrhs, const double *A, int lda, int b, const ca_tree_t *tree, int slices,
+                    int exact, double *LU, int ldlu, int *ipiv, const double *B, int ldb, double *X, int ldx,
+                    void *work, size_t lwork, int max_iter, double tol, int *iters, double *berr,
+                    int *dev_info, cudaStream_t stream) {
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (n > 0 && !A) return -3;
+  if (lda < (n > 1 ? n : 1)) return -4;
+  if (b < 1) return -5;
+  if (check_tree(tree, b)) return -6;
+  if (slices < 1 || slices > 8) return -7;
+  if (n > 0 && !LU) return -9;
+  if (ldlu < (n > 1 ? n : 1)) return -10;
+  if (n > 0 && !ipiv) return -11;
+  if (n > 0 && nrhs > 0 && !B) return -12;
+  if (ldb < (n > 1 ? n : 1)) return -13;
+  if (n > 0 && nrhs > 0 && !X) return -14;
+  if (ldx < (n > 1 ? n : 1)) return -15;
+  if (max_iter < 0) return -18;
+  if (nrhs > kMaxRhsHost) return CA_ERR_UNSUPPORTED;
+  if (!dev_info) return -22;
+  size_t need = 0;
+  int rc = ca_gesv_mixed_workspace(n, nrhs, b, tree, slices, exact, &need);
+  if (rc != CA_OK) return rc;
+  if (n > 0 && (!work || lwork < need)) return CA_ERR_WORKSPACE;
+  if (iters) *iters = 0;
+  if (berr) *berr = 0.0;
+  if (n == 0) return cudaMemsetAsync(dev_info, 0, 2 * sizeof(int), stream) == cudaSuccess ? CA_OK : CA_ERR_LAUNCH;
+  size_t wf = 0;
+  ca_calu_mixed_workspace(n, n, b, tree, slices, exact, &wf);
+  IrWs iw;
+  ir_ws_carve((char *)work + align256(wf), n, nrhs > 0 ? nrhs : 1, iw);
+  // 1. LU <- A, reduced-precision factorization (FP64 panels and pivots)
+  if (cudaMemcpy2DAsync(LU, (size_t)ldlu * 8, A, (size_t)lda * 8, (size_t)n * 8, n, cudaMemcpyDeviceToDevice,
+                        stream) != cudaSuccess)
+    return CA_ERR_LAUNCH;
+  rc = calu_factor_mixed(n, n, LU, ldlu, b, tree, slices, exact, ipiv, work, wf, dev_info, stream);
+  if (rc != CA_OK) return rc;
+  if (nrhs == 0) return CA_OK;
+  // 2. X = (LU)^-1 B
+  if (cudaMemcpy2DAsync(X, (size_t)ldx * 8, B, (size_t)ldb * 8, (size_t)n * 8, nrhs, cudaMemcpyDeviceToDevice,
+                        stream) != cudaSuccess)
+    return CA_ERR_LAUNCH;
+  if (calu_getrs(n, nrhs, LU, ldlu, ipiv, X, ldx, stream) != CA_OK) return CA_ERR_LAUNCH;
+  if (ir_anorm(n, A, lda, iw, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  // 3. refinement: R = B - A X in FP64, stop at berr <= tol, on stagnation or
+  //    after max_iter corrections; each step solves with the same factors
+  double prev = 0.0;
+  int stall = 0;
+  double host_berr[kMaxRhsHost];
+  const int nb = nrhs < kMaxRhsHost ? nrhs : kMaxRhsHost;
+  for (int it = 0;; ++it) {
+    if (ir_residual(n, nrhs, A, lda, X, ldx, B, ldb, iw, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+    if (ir_berr(n, nrhs, X, ldx, B, ldb, iw, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+    if (cudaMemcpyAsync(host_berr, iw.berr, (size_t)nb * 8, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      return CA_ERR_LAUNCH;
+    double be = 0.0;
+    for (int j = 0; j < nb; ++j) be = host_berr[j] > be ? host_berr[j] : be;
+    if (berr) *berr = be;
+    if (iters) *iters = it;
+    if (be <= tol || it >= max_iter) break;
+    if (it > 0 && be > 0.5 * prev) {
+      if (++stall >= 2) break;
+    } else {
+      stall = 0;
+    }
+    prev = be;
+    if (calu_getrs(n, nrhs, LU, ldlu, ipiv, iw.R, n, stream) != CA_OK) return CA_ERR_LAUNCH;
+    if (ir_update(n, nrhs, iw, X, ldx, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  }
   return CA_OK;
 }
 

@@ -106,6 +106,9 @@ enum KernelClass {
   kClsTsqrNode,
   kClsTreeApply,
   kClsSolve,
+  kClsSplit,
+  kClsGemmTc,
+  kClsRefine,
   kNumClasses
 };
 
@@ -171,6 +174,26 @@ cudaError_t tsqr_panel(int mk, int bk, int b, double *P, int lda, int leaf_rows,
 cudaError_t tree_apply_qt(int mk, int bk, int b, const double *P, int lda, int leaf_rows,
                           const Plan &plan, const double *Tp, double *C, int ldc, int ncols,
                           const QrPanelWs &ws, cudaStream_t st);
+
+// tensor-core update C -= A B with FP64 operands split into S bf16 digit
+// slices (gemm_tc.cu); ws holds the slices and exponents.
+size_t tc_gemm_ws_bytes(int m, int n, int k, int S);
+bool tc_gemm_supported(int k, int S, int exact);
+cudaError_t gemm_minus_tc(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
+                          int ldc, int S, int exact, void *ws, int *status, cudaStream_t st);
+
+// iterative refinement pieces (ir.cu)
+struct IrWs {
+  double *partial, *R, *rowsum, *anorm, *berr;
+};
+size_t ir_ws_bytes(int n, int nrhs);
+void ir_ws_carve(void *ws, int n, int nrhs, IrWs &w);
+cudaError_t ir_anorm(int n, const double *A, int lda, const IrWs &w, cudaStream_t st);
+cudaError_t ir_residual(int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B,
+                        int ldb, const IrWs &w, cudaStream_t st);
+cudaError_t ir_berr(int n, int nrhs, const double *X, int ldx, const double *B, int ldb, const IrWs &w,
+                    cudaStream_t st);
+cudaError_t ir_update(int n, int nrhs, const IrWs &w, double *X, int ldx, cudaStream_t st);
 
 // triangular solves (solve.cu)
 cudaError_t getrs_swap(int n, int nrhs, const int *ipiv, double *B, int ldb, cudaStream_t st);

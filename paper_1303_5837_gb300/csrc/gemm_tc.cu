@@ -1,0 +1,490 @@
+// gemm_tc.cu -- C -= A B with FP64 operands on the tcgen05 tensor cores.
+//
+// The trailing updates of CALU / CAQR are the dense contractions of the
+// method (Sec. 3: the Schur complement A22 -= L21 U12 and the compact-WY
+// Q^T C).  On GB300 the FP64 pipe retires ~1.2 TFLOP/s while the bf16 tensor
+// cores retire ~1.9 PFLOP/s, so the reduced-precision form of the update runs
+// there:
+//   * split: every row of A (every column of B) is scaled by a power of two,
+//     2^-e with |x| < 2^e, and cut into S signed base-256 digits
+//     t = sum_k d_k 2^(-8k), |d_1| <= 256, |d_k| <= 128 -- exact FP64 steps.
+//     Digit k is stored in bf16 as d_k 2^(-8(k-1)), which bf16 holds exactly;
+//   * tcgen05.mma (kind::f16, bf16 x bf16 -> FP32 in tensor memory) sums the
+//     digit products d_k d'_l with k + l <= S + 1 for one 128 x 128 tile;
+//     operand tiles arrive by TMA (cp.async.bulk.tensor, 128-byte swizzle);
+//   * the epilogue reads the accumulator with tcgen05.ld and applies
+//     C -= 2^(e_i + f_j - 16) acc in FP64.
+// Fused mode: one FP32 accumulator with pre-scaled digits, accurate to about
+// 2^-20 relative to max|row of A| max|column of B|; FP64 iterative refinement
+// recovers the rest.  Exact mode: integer digits, one accumulator per digit
+// diagonal; every diagonal sum is an integer below 2^24 (k <= 128), so the
+// tensor cores' FP32 sums are exact and the only error is the dropped digits,
+// 2^(-8 S) relative (7 digits: the FP64 level).
+//   diagonal k + l = D, digits |d_1| <= 256, |d_k| <= 128, k = 128:
+//   D = 2: 2^23, 3: 2^23, 4: 1.25 2^23, 5: 1.5 2^23, 6: 1.75 2^23, 7: 2^24,
+//   D = 8: 2.25 2^23 per K block of 64 (so split by K block).
+//
+// Every wait on an mbarrier is bounded by a clock limit; on a timeout the CTA
+// raises a status bit, waits (bounded) for its own copies and MMAs, frees its
+// tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "ca_internal.cuh"
+
+namespace cagb {
+
+// --------------------------------------------------------------------------
+// PTX wrappers
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Waits for the phase with parity `parity`; false after ~`limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
+  const uint32_t addr = smem_u32(bar);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// 32 TMEM lanes x 32 consecutive 32-bit columns; thread i of the warp gets
+// lane (lane base + i).
+__device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes in 1024-byte groups of 8 (SBO = 1024), sm_100 descriptor version.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused by swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;               // version
+  d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// 2^k as a double for -1022 <= k <= 1023 (IEEE binary64 exponent field).
+__device__ __forceinline__ double pow2i(int k) {
+  k = k < -1022 ? -1022 : (k > 1023 ? 1023 : k);
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+constexpr int kTcBM = 128;
+constexpr int kTcBK = 64;                        // one swizzle row: 64 bf16 = 128 bytes
+constexpr int kBoxA = kTcBM * kTcBK * 2;         // 16 KiB TMA box of A digits
+constexpr long long kWaitLimit = 4000000000ll;   // ~2 s of SM clock
+constexpr size_t kTcSmemBudget = 224 * 1024;
+
+struct TcArgs {
+  int m, n, kblocks, S, mpad, npad, bn;
+  int exact;     // 1: one accumulator per digit diagonal (exact FP32 sums)
+  int nstages;   // operand stages in shared memory (1 or 2)
+  int tmem_cols;
+  int nacc;      // TMEM accumulators (1, S, or 8 when the last of 7 diagonals is split)
+  const int *ea, *eb;
+  double *C;
+  int ldc;
+  int *status;
+};
+
+// Operand tiles for one K block: S boxes of A digits (128 x 64) then S boxes
+// of B digits (bn x 64).
+__host__ __device__ inline size_t tc_stage_bytes(int S, int bn) {
+  return (size_t)S * (kTcBM + bn) * kTcBK * 2;
+}
+
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const size_t stage_bytes = tc_stage_bytes(a.S, a.bn);
+  const int boxB = a.bn * kTcBK * 2;
+  uint64_t *full = (uint64_t *)(base + (size_t)a.nstages * stage_bytes);  // [2]
+  uint64_t *empty = full + 2;                                            // [2]
+  uint64_t *done = empty + 2;                                            // [1]
+  uint32_t *tslot = (uint32_t *)(done + 1);
+  volatile int *abort_flag = (volatile int *)(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * a.bn;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tslot, (uint32_t)a.tmem_cols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  int issued0 = 0, issued1 = 0;  // loads issued into stage 0 / 1
+
+  if (threadIdx.x == 0) {
+    // ---- producer: TMA loads of the digit tiles, one K block per stage ----
+    for (int kb = 0; kb < a.kblocks; ++kb) {
+      const int st = kb % a.nstages, round = kb / a.nstages;
+      if (round > 0 && !mbar_wait(&empty[st], (round - 1) & 1, kWaitLimit)) {
+        *abort_flag = 1;
+        atomicOr(a.status, 2);
+        break;
+      }
+      if (*abort_flag) break;
+      uint8_t *sa = base + (size_t)st * stage_bytes;
+      uint8_t *sb = sa + (size_t)a.S * kBoxA;
+      mbar_expect_tx(&full[st], (uint32_t)stage_bytes);
+      for (int s = 0; s < a.S; ++s) {
+        tma_load_2d(sa + (size_t)s * kBoxA, &mapA, &full[st], kb * kTcBK, s * a.mpad + m0);
+        tma_load_2d(sb + (size_t)s * boxB, &mapB, &full[st], kb * kTcBK, s * a.npad + n0);
+      }
+      if (st == 0)
+        ++issued0;
+      else
+        ++issued1;
+    }
+  } else if (threadIdx.x == 32) {
+    // ---- MMA issuer: digit products d_k d'_l with k + l <= S + 1 ----------
+    const uint32_t idesc = idesc_bf16_f32(kTcBM, a.bn);
+    uint32_t started = 0;  // bit acc: accumulator acc already holds a product
+    for (int kb = 0; kb < a.kblocks; ++kb) {
+      const int st = kb % a.nstages;
+      if (!mbar_wait(&full[st], (kb / a.nstages) & 1, kWaitLimit)) {
+        *abort_flag = 1;
+        atomicOr(a.status, 4);
+        break;
+      }
+      tc_fence_after();
+      uint8_t *sa = base + (size_t)st * stage_bytes;
+      uint8_t *sb = sa + (size_t)a.S * kBoxA;
+      for (int ka = 0; ka < a.S; ++ka)
+        for (int kq = 0; ka + kq < a.S; ++kq) {
+          // accumulator: the digit diagonal ka + kq; with 7 digits the last
+          // diagonal (7 products) is split by K block to stay below 2^24
+          int acc = a.exact ? ka + kq : 0;
+          if (a.nacc == 8 && acc == 6) acc = 6 + (kb & 1);
+          const uint32_t d = tmem + (uint32_t)(acc * a.bn);
+          const uint64_t ad = sw128_desc(smem_u32(sa + (size_t)ka * kBoxA));
+          const uint64_t bd = sw128_desc(smem_u32(sb + (size_t)kq * boxB));
+#pragma unroll
+          for (int ks = 0; ks < kTcBK / 16; ++ks) {  // +32 bytes of K per step
+            tc_mma(d, ad + 2 * ks, bd + 2 * ks, idesc, (started >> acc) & 1u);
+            started |= 1u << acc;
+          }
+        }
+      tc_commit(&empty[st]);  // the stage may be refilled once these MMAs are done
+    }
+    tc_commit(done);
+  }
+  __syncthreads();
+  // ---- epilogue: C -= 2^(e_i + f_j - 16) sum_d 2^(-8 d) acc_d -------------
+  bool ok = mbar_wait(done, 0, kWaitLimit) && (*abort_flag == 0);
+  if (!ok && lane == 0) atomicOr(a.status, 8);
+  tc_fence_after();
+  const int nacc = a.nacc;
+  if (ok) {
+    const int row = m0 + 32 * warp + lane;
+    const bool rin = row < a.m;
+    const int er = rin ? a.ea[row] : 0;
+    for (int c0 = 0; c0 < a.bn; c0 += 32) {
+      double v[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = 0.0;
+      double w = 1.0;
+      for (int d = 0; d < nacc; ++d) {
+        uint32_t r[32];
+        tmem_ld_32x32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d * a.bn + c0), r);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = fma((double)__uint_as_float(r[j]), w, v[j]);
+        if (d < 6) w *= (1.0 / 256.0);  // accumulators 6 and 7 share one diagonal
+      }
+      if (!rin) continue;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = n0 + c0 + j;
+        if (col < a.n) {
+          double *p = a.C + row + (size_t)col * a.ldc;
+          *p -= v[j] * pow2i(er + a.eb[col] - 16);
+        }
+      }
+    }
+  }
+  // every copy this CTA issued has landed before shared memory goes away
+  if (threadIdx.x == 0) {
+    if (issued0 > 0) mbar_wait(&full[0], (issued0 - 1) & 1, kWaitLimit);
+    if (issued1 > 0) mbar_wait(&full[1], (issued1 - 1) & 1, kWaitLimit);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+}
+
+// --------------------------------------------------------------------------
+// split: vectors of a column-major matrix -> S bf16 digit slices, one warp per
+// vector (a row of A or a column of B), K <= 256.
+// element (v, k) of X is X[v * sv + k * sk]; slice s, vector v, position k
+// goes to out[(s * vpad + v) * kpad + k].
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) split_kernel(int nv, int K, const double *__restrict__ X, long long sv,
+                                                    long long sk, int S, int vpad, int kpad, int exact,
+                                                    __nv_bfloat16 *__restrict__ out, int *__restrict__ ex) {
+  const int lane = threadIdx.x & 31;
+  const int v = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (v >= vpad) return;
+  constexpr int kPer = 8;  // K <= 256
+  double x[kPer];
+  unsigned long long mx = 0;
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int k = lane + 32 * t;
+    x[t] = (v < nv && k < K) ? X[(long long)v * sv + (long long)k * sk] : 0.0;
+    const unsigned long long b = absbits(x[t]);
+    mx = b > mx ? b : mx;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+    mx = o > mx ? o : mx;
+  }
+  // |x| < 2^e; e from the exponent field of the largest magnitude
+  int e = 0;
+  if (mx != 0) {
+    const int E = (int)(mx >> 52);
+    e = (E == 0) ? -1021 : E - 1022;
+  }
+  if (lane == 0 && v < vpad) ex[v] = e;
+  const double sc = pow2i(-e) * 256.0;
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int k = lane + 32 * t;
+    if (k >= kpad) continue;
+    double y = x[t] * sc;  // |y| < 256, exact
+    double w = 1.0;        // stored weight of digit s: 2^(-8 s), or 1 in exact mode
+    for (int s = 0; s < S; ++s) {
+      const double d = rint(y);
+      out[((long long)s * vpad + v) * kpad + k] = __double2bfloat16(d * w);
+      y = (y - d) * 256.0;
+      if (!exact) w *= (1.0 / 256.0);
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// host side
+// --------------------------------------------------------------------------
+static inline int rup(int x, int q) { return (x + q - 1) / q * q; }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+static bool make_map(CUtensorMap *map, void *base, int kpad, int rows, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// exact: one accumulator per digit diagonal (S <= 6, k <= 128 keeps every
+// diagonal sum below 2^24, so the FP32 sums are exact); otherwise one fused
+// accumulator with pre-scaled digits.
+// accumulators: one (fused), one per digit diagonal (exact), and with 7
+// digits over two K blocks the 7-product diagonal gets one per K block
+static int tc_nacc(int S, int exact, int kblocks) {
+  return exact ? ((S == 7 && kblocks > 1) ? 8 : S) : 1;
+}
+static int tc_bn(int S, int exact) { return tc_nacc(S, exact, 2) * 128 > 512 ? 64 : 128; }
+
+static int tc_stages(int S, int bn, int kblocks) {
+  const size_t st = tc_stage_bytes(S, bn);
+  int ns = (2 * st + 1024 + 256 <= kTcSmemBudget) ? 2 : 1;
+  return ns > kblocks ? kblocks : ns;
+}
+
+size_t tc_gemm_ws_bytes(int m, int n, int k, int S) {
+  const size_t mp = rup(m > 0 ? m : 1, kTcBM), np = rup(n > 0 ? n : 1, 128), kp = rup(k > 0 ? k : 1, kTcBK);
+  return align256((size_t)S * mp * kp * 2) + align256((size_t)S * np * kp * 2) + align256(mp * 4) +
+         align256(np * 4) + 256;
+}
+
+bool tc_gemm_supported(int k, int S, int exact) {
+  if (k < 1 || k > 256 || S < 1 || S > 8) return false;
+  if (exact && (S > 7 || k > 128)) return false;
+  const int bn = tc_bn(S, exact);
+  return tc_stage_bytes(S, bn) + 1024 + 256 <= kTcSmemBudget;
+}
+
+cudaError_t gemm_minus_tc(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
+                          int ldc, int S, int exact, void *ws, int *status, cudaStream_t st) {
+  if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+  if (!tc_gemm_supported(k, S, exact)) return cudaErrorInvalidValue;
+  const int bn = tc_bn(S, exact);
+  const int mp = rup(m, kTcBM), np = rup(n, 128), kp = rup(k, kTcBK);
+  char *p = (char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  __nv_bfloat16 *sa = (__nv_bfloat16 *)p;
+  p += align256((size_t)S * mp * kp * 2);
+  __nv_bfloat16 *sb = (__nv_bfloat16 *)p;
+  p += align256((size_t)S * np * kp * 2);
+  int *ea = (int *)p;
+  p += align256((size_t)mp * 4);
+  int *eb = (int *)p;
+  {
+    ProfScope ps(kClsSplit, st, 0.0);
+    split_kernel<<<(mp + 7) / 8, 256, 0, st>>>(m, k, A, 1, lda, S, mp, kp, exact, sa, ea);
+  }
+  {
+    ProfScope ps(kClsSplit, st, 0.0);
+    split_kernel<<<(np + 7) / 8, 256, 0, st>>>(n, k, B, ldb, 1, S, np, kp, exact, sb, eb);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, sa, kp, S * mp, kTcBM) || !make_map(&mb, sb, kp, S * np, bn))
+    return cudaErrorInvalidValue;
+  TcArgs a;
+  a.m = m;
+  a.n = n;
+  a.kblocks = kp / kTcBK;
+  a.S = S;
+  a.mpad = mp;
+  a.npad = np;
+  a.bn = bn;
+  a.exact = exact;
+  a.nstages = tc_stages(S, bn, a.kblocks);
+  a.nacc = tc_nacc(S, exact, a.kblocks);
+  int cols = a.nacc * bn;
+  int tc = 32;
+  while (tc < cols) tc *= 2;
+  a.tmem_cols = tc;
+  a.ea = ea;
+  a.eb = eb;
+  a.C = C;
+  a.ldc = ldc;
+  a.status = status;
+  const size_t smem = a.nstages * tc_stage_bytes(S, bn) + 1024 + 256;
+  static bool init = false;
+  if (!init) {
+    e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBudget);
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  dim3 grid(mp / kTcBM, np / bn);
+  // bf16 tensor-core flops issued: S (S + 1) / 2 digit products
+  ProfScope ps(kClsGemmTc, st, 2.0 * (double)mp * np * kp * (S * (S + 1) / 2));
+  tc_gemm_kernel<<<grid, 128, smem, st>>>(ma, mb, a);
+  return cudaGetLastError();
+}
+
+}  // namespace cagb

@@ -32,8 +32,9 @@ Prof &prof() {
   static Prof p;
   return p;
 }
-const char *kNames[kNumClasses] = {"tslu_node", "laswp", "lu_finish", "trsm_u12",
-                                   "gemm_fp64", "tsqr_node", "tree_apply", "solve"};
+const char *kNames[kNumClasses] = {"tslu_node", "laswp",      "lu_finish", "trsm_u12",
+                                   "gemm_fp64", "tsqr_node",  "tree_apply", "solve",
+                                   "split_bf16", "gemm_tc",    "refine"};
 }  // namespace
 
 ProfScope::ProfScope(int cls, cudaStream_t st, double flops) : cls_(cls), st_(st), flops_(flops) {

@@ -1,0 +1,120 @@
+"""GPU tests of the reduced-precision path: the tcgen05 digit-split update,
+the mixed CALU and FP64 iterative refinement.
+
+The update is checked against the plain definition C - A B in FP64 (numpy),
+with the error bound of its digit count; exact mode on integer digits must be
+bit-exact (the tensor cores' FP32 sums of integers below 2^24 are exact).
+The mixed factorizations are checked against the CPU oracle: with 7 exact
+digits the update is FP64-accurate and the pivots must equal the oracle's;
+refinement must reach a backward error <= 1e-14 and the oracle's solution.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1303_5837_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ca():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1303_5837_gb300 as ca
+    ca.load()
+    return ca
+
+
+def to_dev(A):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(A).T)).cuda().t()
+
+
+def to_host(T):
+    return np.asfortranarray(T.cpu().numpy())
+
+
+def scaled_err(C_gpu, C_ref, A, B):
+    """max |error| over max_i max|A(i,:)| max_j max|B(:,j)| k."""
+    k = A.shape[1]
+    scale = np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * k
+    return float(np.max(np.abs(C_gpu - C_ref) / np.maximum(scale, 1e-300)))
+
+
+@pytest.mark.parametrize("m,n,k", [(128, 128, 64), (300, 200, 128), (1000, 700, 100), (513, 257, 128),
+                                   (129, 1000, 32), (4096, 4096, 128)])
+@pytest.mark.parametrize("slices,exact,bound", [(2, False, 2.0 ** -14), (3, False, 2.0 ** -18),
+                                                (3, True, 2.0 ** -22), (4, True, 2.0 ** -30),
+                                                (6, True, 2.0 ** -44), (7, True, 2.0 ** -50)])
+def test_gemm_mixed_accuracy(ca, m, n, k, slices, exact, bound):
+    A = inputs.gaussian(m, k, m + k)
+    B = inputs.gaussian(k, n, n + k) * 10.0
+    C = inputs.gaussian(m, n, m + n)
+    Cd = to_dev(C)
+    st = ca.ca_gemm_minus_mixed(to_dev(A), to_dev(B), Cd, slices=slices, exact=exact)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ref = C - A @ B
+    assert scaled_err(to_host(Cd), ref, A, B) < bound
+
+
+def test_gemm_exact_mode_is_exact_on_integers(ca):
+    """Integer operands below 256 are single digits: the exact mode must give
+    C - A B with no rounding at all (FP32 sums of integers < 2^24 on the
+    tensor cores, FP64 epilogue)."""
+    m, n, k = 384, 256, 128
+    A = inputs.int_matrix(m, k, 1, -255, 255)
+    B = inputs.int_matrix(k, n, 2, -255, 255)
+    C = inputs.int_matrix(m, n, 3, -1000, 1000)
+    Cd = to_dev(C)
+    ca.ca_gemm_minus_mixed(to_dev(A), to_dev(B), Cd, slices=1, exact=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(Cd), C - A @ B)
+
+
+@pytest.mark.parametrize("m,n,b,L", [(1024, 1024, 64, 128), (777, 500, 48, 96), (1500, 1500, 128, 256)])
+def test_calu_mixed_exact7_matches_oracle(ca, m, n, b, L):
+    A = inputs.gaussian(m, n, 3 * m + n)
+    tree = [(2, 0), (0, 0)]
+    LU_o, ipiv_o, _, nt = oracle.calu(A, b, oracle.make_tree(L, tree))
+    assert nt == 0
+    Ad = to_dev(A)
+    ipiv, info = ca.calu_factor_mixed(Ad, b, ca.make_tree(L, tree), slices=7, exact=True)
+    torch.cuda.synchronize()
+    assert info.cpu().tolist() == [0, 0]
+    assert np.array_equal(ipiv.cpu().numpy(), ipiv_o)
+    LU = to_host(Ad)
+    assert np.linalg.norm(LU - LU_o) / np.linalg.norm(LU_o) < 1e-12
+
+
+def test_calu_mixed_fused_backward_error(ca):
+    n, b, L = 2048, 128, 256
+    A = inputs.gaussian(n, n, 99)
+    Ad = to_dev(A)
+    ipiv, info = ca.calu_factor_mixed(Ad, b, ca.make_tree(L), slices=3, exact=False)
+    torch.cuda.synchronize()
+    perm, Lf, U = oracle.lu_unpack(to_host(Ad), ipiv.cpu().numpy())
+    res = np.linalg.norm(A[perm] - Lf @ U) / np.linalg.norm(A)
+    assert res < 1e-4  # three fused digits: about 2e-5 at n = 2048
+    assert info.cpu().tolist() == [0, 0]
+
+
+@pytest.mark.parametrize("n,cond,slices,exact", [(1024, 1e2, 3, False), (1024, 1e6, 3, True),
+                                                 (2048, 1e6, 4, True), (1024, 1e10, 5, True),
+                                                 (1536, 1e10, 6, True)])
+def test_gesv_mixed_refinement(ca, n, cond, slices, exact):
+    A = inputs.conditioned(n, cond, 7)
+    x_true = inputs.rhs(n, 2, 8)
+    B = A @ x_true
+    b, L = 128, 256
+    LU_o, ipiv_o, _, _ = oracle.calu(A, b, oracle.make_tree(L))
+    x_o = oracle.getrs(LU_o, ipiv_o, B)
+    X, iters, berr, info = ca.calu_gesv_mixed(to_dev(A), to_dev(B), b, ca.make_tree(L), slices=slices,
+                                              exact=exact, max_iter=30, tol=1e-14)
+    torch.cuda.synchronize()
+    assert info.cpu().tolist()[1] == 0
+    assert berr <= 1e-14, (iters, berr)
+    x = to_host(X)
+    # both solutions are backward stable (<= 1e-14): they agree to cond * 1e-14
+    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) < max(1e-12, cond * 1e-14)
