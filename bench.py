@@ -377,17 +377,29 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
     info = torch.zeros(2, dtype=torch.int32, device=A0.device)
     out = {}
 
-    def timed(fn):
+    kernels_of = {}
+
+    def timed(fn, name=None):
         fn()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        if name:
+            ca.ca_prof_enable(True, 200000)
         e0.record(st)
         res = None
         for _ in range(a.steps):
             res = fn()
         e1.record(st)
         torch.cuda.synchronize()
+        if name:
+            ks = {}
+            for c, kn in enumerate(ca.KERNEL_CLASSES):
+                cnt, kms, kfl, _ = ca.ca_prof_read(c)
+                if cnt:
+                    ks[kn] = {"launches": cnt // a.steps, "ms": kms / a.steps, "gflop": kfl / a.steps / 1e9}
+            ca.ca_prof_enable(False, 1)
+            kernels_of[name] = ks
         return allreduce_max(e0.elapsed_time(e1), world) / a.steps, res
 
     def berr_of(Xs):
@@ -417,7 +429,7 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
                                           LU=LU, X=X, ipiv=ipiv, work=wmix, dev_info=info)
         return it, be
 
-    ms, (it, be) = timed(mixed)
+    ms, (it, be) = timed(mixed, "mixed_ir")
     out["mixed_ir"] = {"ms": ms, "gflops": lu_flops / ms / 1e6, "iters": it, "berr": be,
                        "berr_check": berr_of(X), "slices": S, "exact": ex,
                        "x_rel_err": float(torch.linalg.norm(X - x_true) / torch.linalg.norm(x_true)),
@@ -432,11 +444,43 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
         ca.calu_factor_mixed(A, b, tree, slices=7, exact=True, ipiv=ipiv, work=wemu, dev_info=info)
         ca.calu_getrs(A, ipiv, X)
 
-    ms, _ = timed(emulated)
+    ms, _ = timed(emulated, "fp64_emulated")
     out["fp64_emulated"] = {"ms": ms, "gflops": lu_flops / ms / 1e6, "berr": berr_of(X),
                             "speedup_vs_fp64": out["fp64"]["ms"] / ms,
                             "form": "calu_factor_mixed(7 exact digits) + calu_getrs: FP64-accurate update "
                                     "on the tensor cores"}
+    # QR: least squares, plain FP64 vs the 7-digit tensor-core tree update
+    qr_flops = 4.0 * n ** 3 / 3.0 + 3.0 * n * n * a.nrhs
+    qb, qw = ca.ca_caqr_workspace(n, n, b, tree)
+    qtree = torch.empty((qb + 7) // 8, dtype=torch.float64, device=A0.device)
+    qwork = torch.empty((max(qw, ca.ca_geqrs_workspace(n, n, a.nrhs, b, tree)) + 7) // 8, dtype=torch.float64,
+                        device=A0.device)
+    _, qwm = ca.ca_caqr_mixed_workspace(n, n, b, tree, 7, True)
+    qwmix = torch.empty((qwm + 7) // 8, dtype=torch.float64, device=A0.device)
+
+    def qr_plain():
+        A.copy_(A0)
+        X.copy_(B0)
+        ca.caqr_factor(A, b, tree, qtree=qtree, work=qwork, dev_info=info)
+        ca.caqr_geqrs(A, b, tree, qtree, X, work=qwork)
+
+    ms, _ = timed(qr_plain)
+    out["qr_fp64"] = {"ms": ms, "gflops": qr_flops / ms / 1e6, "berr": berr_of(X),
+                      "form": "caqr_factor + caqr_geqrs, FP64 DFMA tree update"}
+
+    def qr_emulated():
+        A.copy_(A0)
+        X.copy_(B0)
+        ca.caqr_factor_mixed(A, b, tree, slices=7, exact=True, qtree=qtree, work=qwmix, dev_info=info)
+        ca.caqr_geqrs(A, b, tree, qtree, X, work=qwork)
+
+    ms, _ = timed(qr_emulated, "qr_fp64_emulated")
+    out["qr_fp64_emulated"] = {"ms": ms, "gflops": qr_flops / ms / 1e6, "berr": berr_of(X),
+                               "speedup_vs_fp64": out["qr_fp64"]["ms"] / ms,
+                               "form": "caqr_factor_mixed(7 exact digits) + caqr_geqrs: FP64-accurate tree "
+                                       "update on the tensor cores"}
+    for k, v in kernels_of.items():
+        out[k]["kernels"] = v
     return out
 
 

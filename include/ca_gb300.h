@@ -233,6 +233,20 @@ int calu_factor_mixed(int m, int n, double *A, int lda, int b, const ca_tree_t *
                       int exact, int *ipiv, void *work, size_t lwork, int *dev_info,
                       cudaStream_t stream);
 
+/* caqr_factor_mixed: caqr_factor with the tree update of the trailing
+ * columns (W = Y^T C, W = T^T W, C -= Y W for every leaf and merge node,
+ * Sec. 3.1 UPFACT / UPELIM) on the tensor cores with `slices` digits and the
+ * `exact` mode of ca_gemm_minus_mixed; TSQR (reflectors, norms, T) stays in
+ * FP64.  Same outputs and storage as caqr_factor; with exact = 1 and
+ * slices = 7 they agree with the FP64 form to FP64 rounding.  Arguments:
+ * 1 m, 2 n, 3 A, 4 lda, 5 b, 6 tree, 7 slices, 8 exact, 9 qtree,
+ * 10 qtree_bytes, 11 work, 12 lwork, 13 dev_info, 14 stream. */
+int ca_caqr_mixed_workspace(int m, int n, int b, const ca_tree_t *tree, int slices, int exact,
+                            size_t *qtree_bytes, size_t *work_bytes);
+int caqr_factor_mixed(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int slices,
+                      int exact, double *qtree, size_t qtree_bytes, void *work, size_t lwork,
+                      int *dev_info, cudaStream_t stream);
+
 /* calu_gesv_mixed: solve A X = B (n x n, nrhs <= 256) by the mixed
  * factorization plus FP64 iterative refinement: LU <- A (copy in the caller's
  * LU buffer), calu_factor_mixed, X = U^-1 L^-1 P B, then repeat R = B - A X

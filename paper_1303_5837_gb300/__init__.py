@@ -12,7 +12,8 @@ _BINDING_NAMES = {
     "ca_tree_t", "CaError", "BINARY", "FLAT", "load", "lib_path",
     "ca_prof_enable", "ca_prof_read", "ca_launch_count", "ca_kernel_class_name", "KERNEL_CLASSES",
     "ca_gemm_mixed_workspace", "ca_gemm_minus_mixed", "tslu_noalloc", "ca_calu_mixed_workspace",
-    "calu_factor_mixed", "ca_gesv_mixed_workspace", "calu_gesv_mixed",
+    "calu_factor_mixed", "ca_gesv_mixed_workspace", "calu_gesv_mixed", "ca_caqr_mixed_workspace",
+    "caqr_factor_mixed",
 }
 
 

@@ -63,7 +63,8 @@ SYMBOLS = ("ca_strerror", "ca_calu_workspace", "ca_caqr_workspace", "ca_geqrs_wo
            "calu_factor", "tslu", "calu_getrs", "caqr_factor", "tsqr", "caqr_geqrs",
            "ca_prof_enable", "ca_prof_read", "ca_launch_count", "ca_kernel_class_name",
            "ca_gemm_mixed_workspace", "ca_gemm_minus_mixed", "ca_calu_mixed_workspace",
-           "calu_factor_mixed", "ca_gesv_mixed_workspace", "calu_gesv_mixed")
+           "calu_factor_mixed", "ca_gesv_mixed_workspace", "calu_gesv_mixed", "ca_caqr_mixed_workspace",
+           "caqr_factor_mixed")
 KERNEL_CLASSES = ("tslu_node", "laswp", "lu_finish", "trsm_u12", "gemm_fp64", "tsqr_node",
                   "tree_apply", "solve", "split_bf16", "gemm_tc", "refine")
 
@@ -104,6 +105,8 @@ def load(build_if_missing: bool = True):
     L.ca_gesv_mixed_workspace.argtypes = [I, I, I, T, I, I, PS]
     L.calu_gesv_mixed.argtypes = [I, I, P, I, I, T, I, I, P, I, P, P, I, P, I, P, S, I,
                                   ctypes.c_double, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double), P, P]
+    L.ca_caqr_mixed_workspace.argtypes = [I, I, I, T, I, I, PS, PS]
+    L.caqr_factor_mixed.argtypes = [I, I, P, I, I, T, I, I, P, S, P, S, P, P]
     L.ca_prof_enable.argtypes = [I, I]
     L.ca_prof_read.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)]
@@ -393,3 +396,31 @@ def calu_gesv_mixed(A: torch.Tensor, B: torch.Tensor, b: int, tree: ca_tree_t, s
                                 _ptr(dev_info), _stream(stream))
     _check("calu_gesv_mixed", rc)
     return X, it.value, be.value, dev_info
+
+
+def ca_caqr_mixed_workspace(m: int, n: int, b: int, tree: ca_tree_t, slices: int, exact: bool):
+    q = ctypes.c_size_t(0)
+    w = ctypes.c_size_t(0)
+    _check("ca_caqr_mixed_workspace",
+           load().ca_caqr_mixed_workspace(m, n, b, ctypes.byref(tree), slices, 1 if exact else 0,
+                                          ctypes.byref(q), ctypes.byref(w)))
+    return q.value, w.value
+
+
+def caqr_factor_mixed(A: torch.Tensor, b: int, tree: ca_tree_t, slices: int = 7, exact: bool = True,
+                      qtree=None, work=None, dev_info=None, stream=None):
+    """CAQR with the tree update on the tensor cores.  Returns (qtree, dev_info)."""
+    m, n, lda = _mat(A, "A")
+    dev = A.device
+    qb, wb = ca_caqr_mixed_workspace(m, n, b, tree, slices, exact)
+    if qtree is None:
+        qtree = _buf(qb, dev)
+    if work is None:
+        work = _buf(wb, dev)
+    if dev_info is None:
+        dev_info = torch.zeros(2, dtype=torch.int32, device=dev)
+    rc = load().caqr_factor_mixed(m, n, _ptr(A), lda, b, ctypes.byref(tree), slices, 1 if exact else 0,
+                                  _ptr(qtree), qtree.numel() * 8, _ptr(work), work.numel() * 8,
+                                  _ptr(dev_info), _stream(stream))
+    _check("caqr_factor_mixed", rc)
+    return qtree, dev_info

@@ -203,6 +203,48 @@ int calu_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int
   return CA_OK;
 }
 
+// Panel loop of CAQR (Algorithm ML-CAQR with one level): TSQR, then the tree
+// update of the trailing columns in FP64 (tcws == nullptr) or on the tensor
+// cores.
+int caqr_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, double *qtree, void *work, int nl,
+             void *tcws, int slices, int exact, int *dev_info, cudaStream_t stream) {
+  if (cudaMemsetAsync(dev_info, 0, 2 * sizeof(int), stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if (n == 0) return CA_OK;
+  QrPanelWs ws;
+  qr_panel_ws_carve(work, nl, ws);
+  const int L = tree->leaf_rows;
+  size_t off = 0;
+  for (int kb = 0; kb < n; kb += b) {
+    const int bk = (n - kb < b) ? n - kb : b;
+    const int mk = m - kb;
+    Plan plan;
+    if (!build_plan(nleaves_of(mk, L), *tree, plan)) return CA_ERR_TREE;
+    double *P = A + kb + (size_t)kb * lda;
+    double *Tp = qtree + off;
+    // 1. TSQR: leaves, then the R-elimination tree
+    if (tsqr_panel(mk, bk, b, P, lda, L, plan, Tp, ws, dev_info, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+    // 2. trailing columns: leaves' Q^T (UPFACT), then merges' Q^T (UPELIM)
+    const int nt = n - kb - bk;
+    if (nt > 0) {
+      cudaError_t e;
+      if (tcws)
+        e = tree_apply_qt_tc(mk, bk, b, P, lda, L, plan, Tp, P + (size_t)bk * lda, lda, nt, ws, tcws, slices,
+                             exact, dev_info + 1, stream);
+      else
+        e = tree_apply_qt(mk, bk, b, P, lda, L, plan, Tp, P + (size_t)bk * lda, lda, nt, ws, stream);
+      if (e != cudaSuccess) return CA_ERR_LAUNCH;
+    }
+    off += (size_t)(plan.nleaves + plan.nmerges) * b * b;
+  }
+  return CA_OK;
+}
+
+size_t caqr_mixed_ws(int m, int n, int b, const ca_tree_t *tree, int nl, int slices) {
+  const int bk = b < n ? b : n;
+  return align256(qr_panel_ws_bytes(nl)) +
+         tree_tc_ws_bytes(m, bk, n - bk > 0 ? n - bk : 1, tree->leaf_rows, nl, slices);
+}
+
 size_t calu_mixed_ws(int m, int n, int b, int nl, int slices) {
   const int bw = b < kMaxB ? b : kMaxB;
   return align256(lu_panel_ws_bytes(nl, bw)) + tc_gemm_ws_bytes(m, n, bw, slices);
@@ -320,30 +362,7 @@ int caqr_factor(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, 
   if (!dev_info) return -11;
   if (n > 0 && (!qtree || qtree_bytes < qneed)) return CA_ERR_WORKSPACE;
   if (n > 0 && (!work || lwork < qr_panel_ws_bytes(nl))) return CA_ERR_WORKSPACE;
-  if (cudaMemsetAsync(dev_info, 0, 2 * sizeof(int), stream) != cudaSuccess) return CA_ERR_LAUNCH;
-  if (n == 0) return CA_OK;
-  QrPanelWs ws;
-  qr_panel_ws_carve(work, nl, ws);
-  const int L = tree->leaf_rows;
-  size_t off = 0;
-  for (int kb = 0; kb < n; kb += b) {
-    const int bk = (n - kb < b) ? n - kb : b;
-    const int mk = m - kb;
-    Plan plan;
-    if (!build_plan(nleaves_of(mk, L), *tree, plan)) return CA_ERR_TREE;
-    double *P = A + kb + (size_t)kb * lda;
-    double *Tp = qtree + off;
-    // 1. TSQR: leaves, then the R-elimination tree
-    if (tsqr_panel(mk, bk, b, P, lda, L, plan, Tp, ws, dev_info, stream) != cudaSuccess)
-      return CA_ERR_LAUNCH;
-    // 2. trailing columns: leaves' Q^T (UPFACT), then merges' Q^T (UPELIM)
-    const int nt = n - kb - bk;
-    if (nt > 0 && tree_apply_qt(mk, bk, b, P, lda, L, plan, Tp, P + (size_t)bk * lda, lda, nt, ws,
-                                stream) != cudaSuccess)
-      return CA_ERR_LAUNCH;
-    off += (size_t)(plan.nleaves + plan.nmerges) * b * b;
-  }
-  return CA_OK;
+  return caqr_run(m, n, A, lda, b, tree, qtree, work, nl, nullptr, 0, 0, dev_info, stream);
 }
 
 int tsqr(int m, int n, double *A, int lda, const ca_tree_t *tree, double *qtree,
@@ -541,6 +560,40 @@ int calu_gesv_mixed(int n, int nrhs, const double *A, int lda, int b, const ca_t
     if (ir_update(n, nrhs, iw, X, ldx, stream) != cudaSuccess) return CA_ERR_LAUNCH;
   }
   return CA_OK;
+}
+
+int ca_caqr_mixed_workspace(int m, int n, int b, const ca_tree_t *tree, int slices, int exact,
+                            size_t *qtree_bytes, size_t *work_bytes) {
+  int nl;
+  size_t q;
+  int rc = qr_shape(m, n, b, tree, &nl, &q);
+  if (rc == -5 || rc == -6) rc = (rc == -5) ? -3 : -4;
+  if (rc != CA_OK) return rc;
+  if (slices < 1 || slices > 8) return -5;
+  if (!tc_gemm_supported(b < kMaxB ? b : kMaxB, slices, exact)) return CA_ERR_UNSUPPORTED;
+  if (!qtree_bytes) return -7;
+  if (!work_bytes) return -8;
+  *qtree_bytes = q;
+  *work_bytes = n > 0 ? caqr_mixed_ws(m, n, b, tree, nl, slices) : 256;
+  return CA_OK;
+}
+
+int caqr_factor_mixed(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int slices, int exact,
+                      double *qtree, size_t qtree_bytes, void *work, size_t lwork, int *dev_info,
+                      cudaStream_t stream) {
+  int nl;
+  size_t qneed;
+  int rc = qr_shape(m, n, b, tree, &nl, &qneed);
+  if (rc != CA_OK) return rc;
+  if (lda < (m > 1 ? m : 1)) return -4;
+  if (n > 0 && !A) return -3;
+  if (slices < 1 || slices > 8) return -7;
+  if (!tc_gemm_supported(b < kMaxB ? b : kMaxB, slices, exact)) return CA_ERR_UNSUPPORTED;
+  if (!dev_info) return -13;
+  if (n > 0 && (!qtree || qtree_bytes < qneed)) return CA_ERR_WORKSPACE;
+  if (n > 0 && (!work || lwork < caqr_mixed_ws(m, n, b, tree, nl, slices))) return CA_ERR_WORKSPACE;
+  char *tcws = n > 0 ? (char *)work + align256(qr_panel_ws_bytes(nl)) : nullptr;
+  return caqr_run(m, n, A, lda, b, tree, qtree, work, nl, tcws, slices, exact, dev_info, stream);
 }
 
 }  // extern "C"

@@ -175,12 +175,44 @@ cudaError_t tree_apply_qt(int mk, int bk, int b, const double *P, int lda, int l
                           const Plan &plan, const double *Tp, double *C, int ldc, int ncols,
                           const QrPanelWs &ws, cudaStream_t st);
 
-// tensor-core update C -= A B with FP64 operands split into S bf16 digit
+// tensor-core update C -= sign A B with FP64 operands split into S bf16 digit
 // slices (gemm_tc.cu); ws holds the slices and exponents.
+// An operand is a batch of matrices given as vectors of length K (the rows of
+// A, the columns of B): element (v, k) of item b is
+// X[b * sb + off[b] + v * sv + k * sk] under a structure rule (shape 0 dense,
+// 1 unit lower, 2 upper on (r, q) = (v + roff, k), or (k + roff, v) if trans).
+struct TcOperand {
+  const double *X;
+  long long sv, sk, sb;
+  const int *off;       // per-item element offset (device), or null
+  int nv, nv_last;      // vectors per item / in the last item
+  const int *nv_item;   // per-item vector count (device), or null
+  int K, K_last;        // contraction length per item / in the last item
+  const int *K_item;    // per-item length (device), or null
+  int shape, trans, roff;
+};
+struct TcGemm {
+  TcOperand A, B;
+  int nbatch;
+  double *C;            // item b: C + b * sbc + coff[b], ld ldc
+  int ldc;
+  long long sbc;
+  const int *coff;
+  double sign;
+  int S, exact;
+};
+cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st);
+size_t tc_gemm_ws_bytes_batched(int m, int n, int k, int S, int nbatch);
 size_t tc_gemm_ws_bytes(int m, int n, int k, int S);
 bool tc_gemm_supported(int k, int S, int exact);
 cudaError_t gemm_minus_tc(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
                           int ldc, int S, int exact, void *ws, int *status, cudaStream_t st);
+
+// CAQR tree update on the tensor cores (update_tc.cu)
+size_t tree_tc_ws_bytes(int mk, int bk, int ncols, int leaf_rows, int nleaves, int S);
+cudaError_t tree_apply_qt_tc(int mk, int bk, int b, const double *P, int lda, int leaf_rows, const Plan &plan,
+                             const double *Tp, double *C, int ldc, int ncols, const QrPanelWs &ws, void *tcws,
+                             int S, int exact, int *status, cudaStream_t st);
 
 // iterative refinement pieces (ir.cu)
 struct IrWs {

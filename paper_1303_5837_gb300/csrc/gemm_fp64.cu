@@ -51,14 +51,20 @@ __global__ void __launch_bounds__(256) gemm_minus_kernel(int m, int n, int k, co
     }
     __syncthreads();
   }
+  // per column: the TM loads of C in flight before the stores
 #pragma unroll
   for (int b = 0; b < TN; ++b) {
-    int gj = j0 + ty + 16 * b;
-    if (gj >= n) continue;
+    const int gj = j0 + ty + 16 * b;
+    double cv[TM];
 #pragma unroll
     for (int a = 0; a < TM; ++a) {
-      int gi = i0 + tx + 16 * a;
-      if (gi < m) C[gi + (size_t)gj * ldc] -= acc[a][b];
+      const int gi = i0 + tx + 16 * a;
+      cv[a] = (gi < m && gj < n) ? C[gi + (size_t)gj * ldc] : 0.0;
+    }
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+      const int gi = i0 + tx + 16 * a;
+      if (gi < m && gj < n) C[gi + (size_t)gj * ldc] = cv[a] - acc[a][b];
     }
   }
 }

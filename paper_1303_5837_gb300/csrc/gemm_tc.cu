@@ -131,6 +131,18 @@ __device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, uint32_t (&r)[32])
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 32 TMEM lanes x 16 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld_32x16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes in 1024-byte groups of 8 (SBO = 1024), sm_100 descriptor version.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -154,6 +166,54 @@ __device__ __forceinline__ double pow2i(int k) {
   return __longlong_as_double((long long)(k + 1023) << 52);
 }
 
+// v * 2^e2 as a double, from the integer bits (round to nearest even) -- no
+// FP64-pipe instruction; exact when |v| < 2^53.  The results here stay far
+// inside the normal range.
+__device__ __forceinline__ double i64_scaled_to_double(long long v, int e2) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+  unsigned long long u = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int nbits = 64 - __clzll((long long)u);  // significant bits
+  int sh = nbits - 53;
+  unsigned long long m;
+  if (sh <= 0) {
+    m = u << (-sh);
+  } else {
+    m = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) ++m;
+    if (m >> 53) {
+      m >>= 1;
+      ++sh;
+    }
+  }
+  const long long E = 52 + sh + e2 + 1023;  // m in [2^52, 2^53)
+  if (E <= 0 || E >= 2047) return (double)v * pow2i(e2);  // outside the normal range: rare path
+  return __longlong_as_double((long long)(sign | ((unsigned long long)E << 52) | (m & ((1ull << 52) - 1))));
+}
+
+// Digits of x for the split: F = round(|x| 2^(8S - e)) (|x| < 2^e), as a
+// signed integer with at most 8 S + 1 bits, from the FP64 bit pattern.
+__device__ __forceinline__ long long fixed_point_digits(double x, int e, int S) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7ff);
+  if (E == 0) return 0;  // zero or subnormal: below every digit
+  const unsigned long long mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+  // |x| = mant 2^(E - 1075); F = mant 2^(E - 1075 + 8 S - e)
+  const int sh = E - 1075 + 8 * S - e;
+  unsigned long long F;
+  if (sh >= 0) {
+    F = mant << sh;  // |x| < 2^e keeps F < 2^(8S) <= 2^56
+  } else if (sh > -64) {
+    F = mant >> (-sh);
+    const unsigned long long rem = mant & ((1ull << (-sh)) - 1), half = 1ull << (-sh - 1);
+    if (rem > half || (rem == half && (F & 1ull))) ++F;
+  } else {
+    F = 0;
+  }
+  return (bits >> 63) ? -(long long)F : (long long)F;
+}
+
 constexpr int kTcBM = 128;
 constexpr int kTcBK = 64;                        // one swizzle row: 64 bf16 = 128 bytes
 constexpr int kBoxA = kTcBM * kTcBK * 2;         // 16 KiB TMA box of A digits
@@ -161,14 +221,21 @@ constexpr long long kWaitLimit = 4000000000ll;   // ~2 s of SM clock
 constexpr size_t kTcSmemBudget = 224 * 1024;
 
 struct TcArgs {
-  int m, n, kblocks, S, mpad, npad, bn;
+  int kblocks, S, mpad, npad, bn;
   int exact;     // 1: one accumulator per digit diagonal (exact FP32 sums)
   int nstages;   // operand stages in shared memory (1 or 2)
   int tmem_cols;
   int nacc;      // TMEM accumulators (1, S, or 8 when the last of 7 diagonals is split)
-  const int *ea, *eb;
-  double *C;
+  int nbatch;    // batch items (grid z)
+  // valid rows / columns of item b: m_item[b] (or m, and m_last for the last item)
+  int m, m_last, n, n_last;
+  const int *m_item, *n_item;
+  const int *ea, *eb;  // exponents, [item][mpad] and [item][npad]
+  double *C;           // item b: C + b * sbc + coff[b], ld ldc
   int ldc;
+  long long sbc;
+  const int *coff;
+  double sign;         // C -= sign * A B
   int *status;
 };
 
@@ -192,6 +259,11 @@ __global__ void __launch_bounds__(128, 1)
   volatile int *abort_flag = (volatile int *)(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * a.bn;
+  const int item = blockIdx.z;
+  const bool last = item == a.nbatch - 1;
+  const int mv = a.m_item ? a.m_item[item] : (last ? a.m_last : a.m);
+  const int nvv = a.n_item ? a.n_item[item] : (last ? a.n_last : a.n);
+  if (m0 >= mv || n0 >= nvv) return;  // an empty tile of a short batch item (uniform per CTA)
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
@@ -226,8 +298,8 @@ __global__ void __launch_bounds__(128, 1)
       uint8_t *sb = sa + (size_t)a.S * kBoxA;
       mbar_expect_tx(&full[st], (uint32_t)stage_bytes);
       for (int s = 0; s < a.S; ++s) {
-        tma_load_2d(sa + (size_t)s * kBoxA, &mapA, &full[st], kb * kTcBK, s * a.mpad + m0);
-        tma_load_2d(sb + (size_t)s * boxB, &mapB, &full[st], kb * kTcBK, s * a.npad + n0);
+        tma_load_2d(sa + (size_t)s * kBoxA, &mapA, &full[st], kb * kTcBK, (item * a.S + s) * a.mpad + m0);
+        tma_load_2d(sb + (size_t)s * boxB, &mapB, &full[st], kb * kTcBK, (item * a.S + s) * a.npad + n0);
       }
       if (st == 0)
         ++issued0;
@@ -275,28 +347,67 @@ __global__ void __launch_bounds__(128, 1)
   const int nacc = a.nacc;
   if (ok) {
     const int row = m0 + 32 * warp + lane;
-    const bool rin = row < a.m;
-    const int er = rin ? a.ea[row] : 0;
-    for (int c0 = 0; c0 < a.bn; c0 += 32) {
-      double v[32];
+    const bool rin = row < mv;
+    const int er = rin ? a.ea[(size_t)item * a.mpad + row] : 0;
+    const int *ebi = a.eb + (size_t)item * a.npad;
+    double *Cb = a.C + (size_t)item * a.sbc + (a.coff ? a.coff[item] : 0);
+    // exact mode: the digit diagonals D = 0 .. S-1 (weights 2^(-8 D)) are
+    // integers below 2^24; combine them in integer arithmetic,
+    //   T_hi = sum_{D <= 4} acc_D 2^(8 (4 - D)),  T_lo = sum_{D > 4} acc_D 2^(8 (6 - D)),
+    // and turn each into a double with integer instructions (the FP64 pipe
+    // is left with the two subtractions from C).
+    const int dmax = a.exact ? a.S - 1 : 0;
+    constexpr int kEp = 16;  // columns per epilogue step
+    for (int c0 = 0; c0 < a.bn; c0 += kEp) {
+      long long thi[kEp], tlo[kEp];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = 0.0;
-      double w = 1.0;
+      for (int j = 0; j < kEp; ++j) thi[j] = tlo[j] = 0;
+      float vf[kEp];
       for (int d = 0; d < nacc; ++d) {
-        uint32_t r[32];
-        tmem_ld_32x32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d * a.bn + c0), r);
+        uint32_t r[kEp];
+        tmem_ld_32x16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d * a.bn + c0), r);
+        if (!a.exact) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = fma((double)__uint_as_float(r[j]), w, v[j]);
-        if (d < 6) w *= (1.0 / 256.0);  // accumulators 6 and 7 share one diagonal
+          for (int j = 0; j < kEp; ++j) vf[j] = __uint_as_float(r[j]);
+          continue;
+        }
+        const int D = d < 7 ? d : 6;  // accumulator 7 is the second half of diagonal 6
+#pragma unroll
+        for (int j = 0; j < kEp; ++j) {
+          const long long q = (long long)__float2int_rn(__uint_as_float(r[j]));
+          if (D <= 4)
+            thi[j] += q << (8 * (4 - D));
+          else
+            tlo[j] += q << (8 * (6 - D));
+        }
       }
       if (!rin) continue;
+      // all loads of C in flight before any store
+      double cv[kEp];
+      int ec[kEp];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
+      for (int j = 0; j < kEp; ++j) {
         const int col = n0 + c0 + j;
-        if (col < a.n) {
-          double *p = a.C + row + (size_t)col * a.ldc;
-          *p -= v[j] * pow2i(er + a.eb[col] - 16);
+        const bool ok_c = col < nvv;
+        cv[j] = ok_c ? __ldcg(Cb + row + (size_t)col * a.ldc) : 0.0;
+        ec[j] = ok_c ? __ldg(ebi + col) : 0;
+      }
+#pragma unroll
+      for (int j = 0; j < kEp; ++j) {
+        const int col = n0 + c0 + j;
+        if (col >= nvv) continue;
+        const int sc = er + ec[j] - 16;  // C -= sign 2^sc value
+        double c = cv[j];
+        if (a.exact) {
+          // value = T_hi 2^(8 (4 - dmax)) ... written relative to diagonal dmax:
+          // sum_D acc_D 2^(-8 D) = T_hi 2^(-32) + T_lo 2^(-48)
+          const long long sh = a.sign > 0 ? 1 : -1;
+          c -= i64_scaled_to_double(sh * thi[j], sc - 32);
+          if (dmax > 4) c -= i64_scaled_to_double(sh * tlo[j], sc - 48);
+        } else {
+          c = fma(-a.sign * (double)vf[j], pow2i(sc), c);
         }
+        Cb[row + (size_t)col * a.ldc] = c;
       }
     }
   }
@@ -311,31 +422,46 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // --------------------------------------------------------------------------
-// split: vectors of a column-major matrix -> S bf16 digit slices, one warp per
-// vector (a row of A or a column of B), K <= 256.
-// element (v, k) of X is X[v * sv + k * sk]; slice s, vector v, position k
-// goes to out[(s * vpad + v) * kpad + k].
+// split: the vectors of an operand (rows of A, columns of B) -> S bf16 digit
+// slices, one warp per vector, K <= 256.  Item b, vector v, position k reads
+// element (v, k) of the source: X[b * sb + off[b] + v * sv + k * sk], through
+// the structure rule on (r, q) = (row, column) of the source:
+// shape 0 dense, 1 unit lower (r > q stored, r == q is one, r < q zero),
+// 2 upper (r <= q stored); (r, q) = (v + roff, k) or, transposed, (k + roff, v).
+// Output: out[((b * S + s) * vpad + v) * kpad + k], exponent ex[b * vpad + v].
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) split_kernel(int nv, int K, const double *__restrict__ X, long long sv,
-                                                    long long sk, int S, int vpad, int kpad, int exact,
+__global__ void __launch_bounds__(256) split_kernel(TcOperand o, int nbatch, int S, int vpad, int kpad, int exact,
                                                     __nv_bfloat16 *__restrict__ out, int *__restrict__ ex) {
   const int lane = threadIdx.x & 31;
   const int v = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int b = blockIdx.y;
   if (v >= vpad) return;
+  const bool last = b == nbatch - 1;
+  const int nv = o.nv_item ? o.nv_item[b] : (last ? o.nv_last : o.nv);
+  const int K = o.K_item ? o.K_item[b] : (last ? o.K_last : o.K);
+  const double *X = o.X + (long long)b * o.sb + (o.off ? o.off[b] : 0);
   constexpr int kPer = 8;  // K <= 256
   double x[kPer];
   unsigned long long mx = 0;
 #pragma unroll
   for (int t = 0; t < kPer; ++t) {
     const int k = lane + 32 * t;
-    x[t] = (v < nv && k < K) ? X[(long long)v * sv + (long long)k * sk] : 0.0;
-    const unsigned long long b = absbits(x[t]);
-    mx = b > mx ? b : mx;
+    double val = 0.0;
+    if (v < nv && k < K) {
+      const int r = (o.trans ? k : v) + o.roff, q = o.trans ? v : k;
+      if (o.shape == 0 || (o.shape == 1 && r > q) || (o.shape == 2 && r <= q))
+        val = X[(long long)v * o.sv + (long long)k * o.sk];
+      else if (o.shape == 1 && r == q)
+        val = 1.0;
+    }
+    x[t] = val;
+    const unsigned long long bits = absbits(val);
+    mx = bits > mx ? bits : mx;
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
-    mx = o > mx ? o : mx;
+    const unsigned long long ot = __shfl_xor_sync(0xffffffffu, mx, off);
+    mx = ot > mx ? ot : mx;
   }
   // |x| < 2^e; e from the exponent field of the largest magnitude
   int e = 0;
@@ -343,19 +469,32 @@ __global__ void __launch_bounds__(256) split_kernel(int nv, int K, const double 
     const int E = (int)(mx >> 52);
     e = (E == 0) ? -1021 : E - 1022;
   }
-  if (lane == 0 && v < vpad) ex[v] = e;
-  const double sc = pow2i(-e) * 256.0;
+  if (lane == 0) ex[(long long)b * vpad + v] = e;
 #pragma unroll
   for (int t = 0; t < kPer; ++t) {
     const int k = lane + 32 * t;
     if (k >= kpad) continue;
-    double y = x[t] * sc;  // |y| < 256, exact
-    double w = 1.0;        // stored weight of digit s: 2^(-8 s), or 1 in exact mode
-    for (int s = 0; s < S; ++s) {
-      const double d = rint(y);
-      out[((long long)s * vpad + v) * kpad + k] = __double2bfloat16(d * w);
-      y = (y - d) * 256.0;
-      if (!exact) w *= (1.0 / 256.0);
+    // F = round(x 2^(8S - e)) = sum_s d_s 256^(S-1-s), balanced digits
+    // d_s in [-128, 127] for s >= 1 and |d_0| <= 256, all integer arithmetic
+    long long F = fixed_point_digits(x[t], e, S);
+    int dg[8];
+#pragma unroll
+    for (int s = 7; s >= 1; --s) {
+      if (s >= S) continue;
+      int d = (int)(F & 255);
+      if (d >= 128) d -= 256;
+      dg[s] = d;
+      F = (F - d) >> 8;
+    }
+    dg[0] = (int)F;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      if (s >= S) break;
+      // stored value: d_s (exact mode) or d_s 2^(-8 s) (fused mode), exact in bf16
+      // 2^(-8 s) as a float from its exponent field (s <= 7: a normal number)
+      const float w = exact ? 1.0f : __int_as_float((127 - 8 * s) << 23);
+      const float val = (float)dg[s] * w;
+      out[(((long long)b * S + s) * vpad + v) * kpad + k] = __float2bfloat16_rn(val);
     }
   }
 }
@@ -413,11 +552,14 @@ static int tc_stages(int S, int bn, int kblocks) {
   return ns > kblocks ? kblocks : ns;
 }
 
-size_t tc_gemm_ws_bytes(int m, int n, int k, int S) {
+size_t tc_gemm_ws_bytes_batched(int m, int n, int k, int S, int nbatch) {
   const size_t mp = rup(m > 0 ? m : 1, kTcBM), np = rup(n > 0 ? n : 1, 128), kp = rup(k > 0 ? k : 1, kTcBK);
-  return align256((size_t)S * mp * kp * 2) + align256((size_t)S * np * kp * 2) + align256(mp * 4) +
-         align256(np * 4) + 256;
+  const size_t nb = nbatch > 0 ? nbatch : 1;
+  return align256(nb * S * mp * kp * 2) + align256(nb * S * np * kp * 2) + align256(nb * mp * 4) +
+         align256(nb * np * 4) + 256;
 }
+
+size_t tc_gemm_ws_bytes(int m, int n, int k, int S) { return tc_gemm_ws_bytes_batched(m, n, k, S, 1); }
 
 bool tc_gemm_supported(int k, int S, int exact) {
   if (k < 1 || k > 256 || S < 1 || S > 8) return false;
@@ -426,36 +568,36 @@ bool tc_gemm_supported(int k, int S, int exact) {
   return tc_stage_bytes(S, bn) + 1024 + 256 <= kTcSmemBudget;
 }
 
-cudaError_t gemm_minus_tc(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
-                          int ldc, int S, int exact, void *ws, int *status, cudaStream_t st) {
-  if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
-  if (!tc_gemm_supported(k, S, exact)) return cudaErrorInvalidValue;
+cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st) {
+  const int m = g.A.nv, n = g.B.nv, k = g.A.K > g.A.K_last ? g.A.K : g.A.K_last;
+  if (m <= 0 || n <= 0 || k <= 0 || g.nbatch <= 0) return cudaSuccess;
+  if (!tc_gemm_supported(k, g.S, g.exact)) return cudaErrorInvalidValue;
+  const int S = g.S, exact = g.exact;
   const int bn = tc_bn(S, exact);
   const int mp = rup(m, kTcBM), np = rup(n, 128), kp = rup(k, kTcBK);
+  const size_t nb = g.nbatch;
   char *p = (char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
   __nv_bfloat16 *sa = (__nv_bfloat16 *)p;
-  p += align256((size_t)S * mp * kp * 2);
+  p += align256(nb * S * mp * kp * 2);
   __nv_bfloat16 *sb = (__nv_bfloat16 *)p;
-  p += align256((size_t)S * np * kp * 2);
+  p += align256(nb * S * np * kp * 2);
   int *ea = (int *)p;
-  p += align256((size_t)mp * 4);
+  p += align256(nb * mp * 4);
   int *eb = (int *)p;
   {
     ProfScope ps(kClsSplit, st, 0.0);
-    split_kernel<<<(mp + 7) / 8, 256, 0, st>>>(m, k, A, 1, lda, S, mp, kp, exact, sa, ea);
+    split_kernel<<<dim3((mp + 7) / 8, g.nbatch), 256, 0, st>>>(g.A, g.nbatch, S, mp, kp, exact, sa, ea);
   }
   {
     ProfScope ps(kClsSplit, st, 0.0);
-    split_kernel<<<(np + 7) / 8, 256, 0, st>>>(n, k, B, ldb, 1, S, np, kp, exact, sb, eb);
+    split_kernel<<<dim3((np + 7) / 8, g.nbatch), 256, 0, st>>>(g.B, g.nbatch, S, np, kp, exact, sb, eb);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, sa, kp, S * mp, kTcBM) || !make_map(&mb, sb, kp, S * np, bn))
+  if (!make_map(&ma, sa, kp, (int)(nb * S * mp), kTcBM) || !make_map(&mb, sb, kp, (int)(nb * S * np), bn))
     return cudaErrorInvalidValue;
   TcArgs a;
-  a.m = m;
-  a.n = n;
   a.kblocks = kp / kTcBK;
   a.S = S;
   a.mpad = mp;
@@ -468,10 +610,20 @@ cudaError_t gemm_minus_tc(int m, int n, int k, const double *A, int lda, const d
   int tc = 32;
   while (tc < cols) tc *= 2;
   a.tmem_cols = tc;
+  a.nbatch = g.nbatch;
+  a.m = g.A.nv;
+  a.m_last = g.A.nv_last;
+  a.n = g.B.nv;
+  a.n_last = g.B.nv_last;
+  a.m_item = g.A.nv_item;
+  a.n_item = g.B.nv_item;
   a.ea = ea;
   a.eb = eb;
-  a.C = C;
-  a.ldc = ldc;
+  a.C = g.C;
+  a.ldc = g.ldc;
+  a.sbc = g.sbc;
+  a.coff = g.coff;
+  a.sign = g.sign;
   a.status = status;
   const size_t smem = a.nstages * tc_stage_bytes(S, bn) + 1024 + 256;
   static bool init = false;
@@ -480,11 +632,33 @@ cudaError_t gemm_minus_tc(int m, int n, int k, const double *A, int lda, const d
     if (e != cudaSuccess) return e;
     init = true;
   }
-  dim3 grid(mp / kTcBM, np / bn);
+  dim3 grid(mp / kTcBM, np / bn, g.nbatch);
   // bf16 tensor-core flops issued: S (S + 1) / 2 digit products
-  ProfScope ps(kClsGemmTc, st, 2.0 * (double)mp * np * kp * (S * (S + 1) / 2));
+  ProfScope ps(kClsGemmTc, st, 2.0 * (double)mp * np * kp * (S * (S + 1) / 2) * nb);
   tc_gemm_kernel<<<grid, 128, smem, st>>>(ma, mb, a);
   return cudaGetLastError();
+}
+
+cudaError_t gemm_minus_tc(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
+                          int ldc, int S, int exact, void *ws, int *status, cudaStream_t st) {
+  TcGemm g = {};
+  g.A.X = A;  // rows of A: element (i, k) at A[i + k lda]
+  g.A.sv = 1;
+  g.A.sk = lda;
+  g.A.nv = g.A.nv_last = m;
+  g.A.K = g.A.K_last = k;
+  g.B.X = B;  // columns of B: element (j, k) at B[k + j ldb]
+  g.B.sv = ldb;
+  g.B.sk = 1;
+  g.B.nv = g.B.nv_last = n;
+  g.B.K = g.B.K_last = k;
+  g.nbatch = 1;
+  g.C = C;
+  g.ldc = ldc;
+  g.sign = 1.0;
+  g.S = S;
+  g.exact = exact;
+  return gemm_tc(g, ws, status, st);
 }
 
 }  // namespace cagb

@@ -118,3 +118,58 @@ def test_gesv_mixed_refinement(ca, n, cond, slices, exact):
     x = to_host(X)
     # both solutions are backward stable (<= 1e-14): they agree to cond * 1e-14
     assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) < max(1e-12, cond * 1e-14)
+
+
+CAQR_CASES = [
+    (1024, 1024, 64, 128, [(0, 0)]),
+    (1200, 700, 64, 128, [(2, 0), (0, 0)]),
+    (640, 256, 128, 256, [(0, 0)]),
+    (900, 333, 32, 100, [(4, 0), (0, 1)]),
+    (1000, 300, 48, 96, [(3, 1), (0, 0)]),
+]
+
+
+@pytest.mark.parametrize("m,n,b,L,tree", CAQR_CASES)
+def test_caqr_mixed_exact7_matches_oracle(ca, m, n, b, L, tree):
+    """The tree update on the tensor cores with 7 exact digits reproduces the
+    FP64 oracle's factors, every stored Y and every T to 1e-12."""
+    A = inputs.gaussian(m, n, 17 + m + n)
+    QR_o, T_o = oracle.caqr(A, b, oracle.make_tree(L, tree))
+    Ad = to_dev(A)
+    qtree, info = ca.caqr_factor_mixed(Ad, b, ca.make_tree(L, tree), slices=7, exact=True)
+    torch.cuda.synchronize()
+    assert info.cpu().tolist() == [0, 0]
+    QR = to_host(Ad)
+    assert np.linalg.norm(QR - QR_o) / np.linalg.norm(QR_o) < 1e-12
+    T = qtree.cpu().numpy()[: T_o.size]
+    assert np.linalg.norm(T - T_o) / np.linalg.norm(T_o) < 1e-12
+
+
+def test_caqr_mixed_fused_r(ca):
+    m, n, b, L = 2048, 1024, 128, 256
+    A = inputs.gaussian(m, n, 5)
+    Ad = to_dev(A)
+    ca.caqr_factor_mixed(Ad, b, ca.make_tree(L), slices=3, exact=False)
+    torch.cuda.synchronize()
+    R = np.triu(to_host(Ad)[:n])
+    Rl = np.linalg.qr(A, mode="r")
+    d = np.sign(np.diag(R)) * np.sign(np.diag(Rl))
+    assert np.linalg.norm(d[:, None] * R - Rl) / np.linalg.norm(Rl) < 1e-4
+
+
+def test_caqr_mixed_geqrs(ca):
+    """Least squares on the emulated factors equals the oracle's."""
+    m, n, b, L = 1500, 400, 64, 128
+    tree = [(2, 0), (0, 0)]
+    A = inputs.gaussian(m, n, 31)
+    B = inputs.rhs(m, 3, 32)
+    QR_o, T_o = oracle.caqr(A, b, oracle.make_tree(L, tree))
+    x_o = oracle.geqrs(QR_o, T_o, b, oracle.make_tree(L, tree), B)
+    Ad = to_dev(A)
+    t = ca.make_tree(L, tree)
+    qtree, _ = ca.caqr_factor_mixed(Ad, b, t, slices=7, exact=True)
+    Bd = to_dev(B)
+    ca.caqr_geqrs(Ad, b, t, qtree, Bd)
+    torch.cuda.synchronize()
+    x = to_host(Bd)[:n]
+    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) < 1e-12
