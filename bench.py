@@ -517,11 +517,14 @@ def barrier(world):
 
 
 def allreduce_max(x: float, world: int) -> float:
+    """Max over ranks (the timing rule); on the CUDA device for NCCL, on the
+    host for gloo."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

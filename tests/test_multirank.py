@@ -1,0 +1,52 @@
+"""The multi-rank plumbing of bench.py on CPU: two gloo ranks (127.0.0.1)
+agree on the barrier and take the maximum of their step times; the whole-job
+value aggregates every rank's units (weak scaling, independent replicas)."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    bench.barrier(world)
+    ms = bench.allreduce_max(100.0 + 50.0 * rank, world)
+    flops = bench.step_flops(1024, 1)
+    value = world * flops * 2 / (ms / 1e3) / 1e9  # 2 steps, as bench computes it
+    q.put((rank, ms, value))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_max_time():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    times = {r: ms for r, ms, _ in out}
+    assert times == {0: 150.0, 1: 150.0}
+    vals = {v for _, _, v in out}
+    assert len(vals) == 1
