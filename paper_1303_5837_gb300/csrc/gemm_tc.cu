@@ -143,15 +143,17 @@ __device__ __forceinline__ void tmem_ld_32x16(uint32_t taddr, uint32_t (&r)[16])
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes in 1024-byte groups of 8 (SBO = 1024), sm_100 descriptor version.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major operand written by TMA with a
+// 128-byte swizzle (rows of 128 bytes, groups of 8 rows = 1024 bytes, layout
+// type 2) or a 64-byte swizzle (rows of 64 bytes, groups of 8 = 512 bytes,
+// layout type 4); sm_100 descriptor version.
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr, int swz) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;               // leading byte offset (unused by swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
-  d |= (uint64_t)1 << 46;               // version
-  d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+  d |= (uint64_t)1 << 16;                              // leading byte offset (unused, swizzled K-major)
+  d |= (uint64_t)((swz == 2 ? 1024 : 512) >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;                              // version
+  d |= (uint64_t)swz << 61;                            // layout type
   return d;
 }
 
@@ -215,13 +217,13 @@ __device__ __forceinline__ long long fixed_point_digits(double x, int e, int S) 
 }
 
 constexpr int kTcBM = 128;
-constexpr int kTcBK = 64;                        // one swizzle row: 64 bf16 = 128 bytes
-constexpr int kBoxA = kTcBM * kTcBK * 2;         // 16 KiB TMA box of A digits
+constexpr int kTcKpad = 64;                      // K is padded to a multiple of 64
 constexpr long long kWaitLimit = 4000000000ll;   // ~2 s of SM clock
 constexpr size_t kTcSmemBudget = 224 * 1024;
 
 struct TcArgs {
   int kblocks, S, mpad, npad, bn;
+  int bk, swz;   // K block (32 or 64 bf16) and its swizzle layout (4: 64 B, 2: 128 B)
   int exact;     // 1: one accumulator per digit diagonal (exact FP32 sums)
   int nstages;   // operand stages in shared memory (1 or 2)
   int tmem_cols;
@@ -235,23 +237,24 @@ struct TcArgs {
   int ldc;
   long long sbc;
   const int *coff;
-  double sign;         // C -= sign * A B
+  int sign;            // C -= sign * A B, sign = +1 or -1
   int *status;
 };
 
-// Operand tiles for one K block: S boxes of A digits (128 x 64) then S boxes
-// of B digits (bn x 64).
-__host__ __device__ inline size_t tc_stage_bytes(int S, int bn) {
-  return (size_t)S * (kTcBM + bn) * kTcBK * 2;
+// Operand tiles for one K block: S boxes of A digits (128 x bk) then S boxes
+// of B digits (bn x bk).
+__host__ __device__ inline size_t tc_stage_bytes(int S, int bn, int bk) {
+  return (size_t)S * (kTcBM + bn) * bk * 2;
 }
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const size_t stage_bytes = tc_stage_bytes(a.S, a.bn);
-  const int boxB = a.bn * kTcBK * 2;
+  const size_t stage_bytes = tc_stage_bytes(a.S, a.bn, a.bk);
+  const int boxA = kTcBM * a.bk * 2;
+  const int boxB = a.bn * a.bk * 2;
   uint64_t *full = (uint64_t *)(base + (size_t)a.nstages * stage_bytes);  // [2]
   uint64_t *empty = full + 2;                                            // [2]
   uint64_t *done = empty + 2;                                            // [1]
@@ -295,11 +298,11 @@ __global__ void __launch_bounds__(128, 1)
       }
       if (*abort_flag) break;
       uint8_t *sa = base + (size_t)st * stage_bytes;
-      uint8_t *sb = sa + (size_t)a.S * kBoxA;
+      uint8_t *sb = sa + (size_t)a.S * boxA;
       mbar_expect_tx(&full[st], (uint32_t)stage_bytes);
       for (int s = 0; s < a.S; ++s) {
-        tma_load_2d(sa + (size_t)s * kBoxA, &mapA, &full[st], kb * kTcBK, (item * a.S + s) * a.mpad + m0);
-        tma_load_2d(sb + (size_t)s * boxB, &mapB, &full[st], kb * kTcBK, (item * a.S + s) * a.npad + n0);
+        tma_load_2d(sa + (size_t)s * boxA, &mapA, &full[st], kb * a.bk, (item * a.S + s) * a.mpad + m0);
+        tma_load_2d(sb + (size_t)s * boxB, &mapB, &full[st], kb * a.bk, (item * a.S + s) * a.npad + n0);
       }
       if (st == 0)
         ++issued0;
@@ -319,18 +322,18 @@ __global__ void __launch_bounds__(128, 1)
       }
       tc_fence_after();
       uint8_t *sa = base + (size_t)st * stage_bytes;
-      uint8_t *sb = sa + (size_t)a.S * kBoxA;
+      uint8_t *sb = sa + (size_t)a.S * boxA;
+      const int khalf = (kb * a.bk >= 64) ? 1 : 0;  // which 64-wide half of K
       for (int ka = 0; ka < a.S; ++ka)
         for (int kq = 0; ka + kq < a.S; ++kq) {
           // accumulator: the digit diagonal ka + kq; with 7 digits the last
           // diagonal (7 products) is split by K block to stay below 2^24
           int acc = a.exact ? ka + kq : 0;
-          if (a.nacc == 8 && acc == 6) acc = 6 + (kb & 1);
+          if (a.nacc == 8 && acc == 6) acc = 6 + khalf;
           const uint32_t d = tmem + (uint32_t)(acc * a.bn);
-          const uint64_t ad = sw128_desc(smem_u32(sa + (size_t)ka * kBoxA));
-          const uint64_t bd = sw128_desc(smem_u32(sb + (size_t)kq * boxB));
-#pragma unroll
-          for (int ks = 0; ks < kTcBK / 16; ++ks) {  // +32 bytes of K per step
+          const uint64_t ad = sw_desc(smem_u32(sa + (size_t)ka * boxA), a.swz);
+          const uint64_t bd = sw_desc(smem_u32(sb + (size_t)kq * boxB), a.swz);
+          for (int ks = 0; ks < a.bk / 16; ++ks) {  // +32 bytes of K per step
             tc_mma(d, ad + 2 * ks, bd + 2 * ks, idesc, (started >> acc) & 1u);
             started |= 1u << acc;
           }
@@ -346,7 +349,10 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const int nacc = a.nacc;
   if (ok) {
-    const int row = m0 + 32 * warp + lane;
+    // 8 warps: warp w reads TMEM lanes 32 (w % 4) .. + 31, column chunks
+    // alternate between warps w and w + 4
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = m0 + 32 * quad + lane;
     const bool rin = row < mv;
     const int er = rin ? a.ea[(size_t)item * a.mpad + row] : 0;
     const int *ebi = a.eb + (size_t)item * a.npad;
@@ -358,14 +364,14 @@ __global__ void __launch_bounds__(128, 1)
     // is left with the two subtractions from C).
     const int dmax = a.exact ? a.S - 1 : 0;
     constexpr int kEp = 16;  // columns per epilogue step
-    for (int c0 = 0; c0 < a.bn; c0 += kEp) {
+    for (int c0 = half * kEp; c0 < a.bn; c0 += 2 * kEp) {
       long long thi[kEp], tlo[kEp];
 #pragma unroll
       for (int j = 0; j < kEp; ++j) thi[j] = tlo[j] = 0;
       float vf[kEp];
       for (int d = 0; d < nacc; ++d) {
         uint32_t r[kEp];
-        tmem_ld_32x16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d * a.bn + c0), r);
+        tmem_ld_32x16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(d * a.bn + c0), r);
         if (!a.exact) {
 #pragma unroll
           for (int j = 0; j < kEp; ++j) vf[j] = __uint_as_float(r[j]);
@@ -401,11 +407,11 @@ __global__ void __launch_bounds__(128, 1)
         if (a.exact) {
           // value = T_hi 2^(8 (4 - dmax)) ... written relative to diagonal dmax:
           // sum_D acc_D 2^(-8 D) = T_hi 2^(-32) + T_lo 2^(-48)
-          const long long sh = a.sign > 0 ? 1 : -1;
+          const long long sh = a.sign;
           c -= i64_scaled_to_double(sh * thi[j], sc - 32);
           if (dmax > 4) c -= i64_scaled_to_double(sh * tlo[j], sc - 48);
         } else {
-          c = fma(-a.sign * (double)vf[j], pow2i(sc), c);
+          c = fma((double)(-a.sign * vf[j]), pow2i(sc), c);
         }
         Cb[row + (size_t)col * a.ldc] = c;
       }
@@ -524,36 +530,62 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-static bool make_map(CUtensorMap *map, void *base, int kpad, int rows, int box_rows) {
+static bool make_map(CUtensorMap *map, void *base, int kpad, int rows, int box_rows, int bk) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// exact: one accumulator per digit diagonal (S <= 6, k <= 128 keeps every
-// diagonal sum below 2^24, so the FP32 sums are exact); otherwise one fused
-// accumulator with pre-scaled digits.
-// accumulators: one (fused), one per digit diagonal (exact), and with 7
-// digits over two K blocks the 7-product diagonal gets one per K block
-static int tc_nacc(int S, int exact, int kblocks) {
-  return exact ? ((S == 7 && kblocks > 1) ? 8 : S) : 1;
+// Accumulators: one (fused), one per digit diagonal (exact), and with 7
+// digits over K > 64 the 7-product diagonal gets one per 64-wide half of K.
+static int tc_nacc(int S, int exact, int kpad) {
+  return exact ? ((S == 7 && kpad > 64) ? 8 : S) : 1;
 }
-static int tc_bn(int S, int exact) { return tc_nacc(S, exact, 2) * 128 > 512 ? 64 : 128; }
 
-static int tc_stages(int S, int bn, int kblocks) {
-  const size_t st = tc_stage_bytes(S, bn);
-  int ns = (2 * st + 1024 + 256 <= kTcSmemBudget) ? 2 : 1;
-  return ns > kblocks ? kblocks : ns;
+static int pow2_at_least(int x) {
+  int p = 32;
+  while (p < x) p *= 2;
+  return p;
+}
+
+struct TcCfg {
+  int bn, bk, swz, nstages, tmem_cols;
+  size_t smem;
+};
+
+// Tile width, K block and stages: one CTA of 8 warps per SM; the widest
+// tile whose accumulators fit in the 512 tensor-memory columns, then the
+// deepest K-block pipeline that fits in shared memory (two stages overlap the
+// loads of one K block with the MMAs of the previous one).
+static bool tc_config(int S, int exact, int kpad, TcCfg &c) {
+  const int nacc = tc_nacc(S, exact, kpad);
+  int bn = 128;
+  while (bn > 32 && nacc * bn > 512) bn /= 2;
+  if (nacc * bn > 512) return false;
+  const int opts[4][2] = {{64, 2}, {32, 2}, {64, 1}, {32, 1}};
+  for (auto &o : opts) {
+    const int bk = o[0];
+    int ns = o[1];
+    const int kblocks = kpad / bk;
+    if (ns > kblocks) ns = kblocks;
+    const size_t smem = ns * tc_stage_bytes(S, bn, bk) + 1024 + 256;
+    if (smem <= kTcSmemBudget) {
+      c = {bn, bk, bk == 64 ? 2 : 4, ns, pow2_at_least(nacc * bn), smem};
+      return true;
+    }
+  }
+  return false;
 }
 
 size_t tc_gemm_ws_bytes_batched(int m, int n, int k, int S, int nbatch) {
-  const size_t mp = rup(m > 0 ? m : 1, kTcBM), np = rup(n > 0 ? n : 1, 128), kp = rup(k > 0 ? k : 1, kTcBK);
+  const size_t mp = rup(m > 0 ? m : 1, kTcBM), np = rup(n > 0 ? n : 1, 128), kp = rup(k > 0 ? k : 1, kTcKpad);
   const size_t nb = nbatch > 0 ? nbatch : 1;
   return align256(nb * S * mp * kp * 2) + align256(nb * S * np * kp * 2) + align256(nb * mp * 4) +
          align256(nb * np * 4) + 256;
@@ -564,8 +596,8 @@ size_t tc_gemm_ws_bytes(int m, int n, int k, int S) { return tc_gemm_ws_bytes_ba
 bool tc_gemm_supported(int k, int S, int exact) {
   if (k < 1 || k > 256 || S < 1 || S > 8) return false;
   if (exact && (S > 7 || k > 128)) return false;
-  const int bn = tc_bn(S, exact);
-  return tc_stage_bytes(S, bn) + 1024 + 256 <= kTcSmemBudget;
+  TcCfg c;
+  return tc_config(S, exact, rup(k, kTcKpad), c);
 }
 
 cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st) {
@@ -573,8 +605,10 @@ cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st) {
   if (m <= 0 || n <= 0 || k <= 0 || g.nbatch <= 0) return cudaSuccess;
   if (!tc_gemm_supported(k, g.S, g.exact)) return cudaErrorInvalidValue;
   const int S = g.S, exact = g.exact;
-  const int bn = tc_bn(S, exact);
-  const int mp = rup(m, kTcBM), np = rup(n, 128), kp = rup(k, kTcBK);
+  const int mp = rup(m, kTcBM), np = rup(n, 128), kp = rup(k, kTcKpad);
+  TcCfg cfg;
+  if (!tc_config(S, exact, kp, cfg)) return cudaErrorInvalidValue;
+  const int bn = cfg.bn;
   const size_t nb = g.nbatch;
   char *p = (char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
   __nv_bfloat16 *sa = (__nv_bfloat16 *)p;
@@ -595,21 +629,21 @@ cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, sa, kp, (int)(nb * S * mp), kTcBM) || !make_map(&mb, sb, kp, (int)(nb * S * np), bn))
+  if (!make_map(&ma, sa, kp, (int)(nb * S * mp), kTcBM, cfg.bk) ||
+      !make_map(&mb, sb, kp, (int)(nb * S * np), bn, cfg.bk))
     return cudaErrorInvalidValue;
   TcArgs a;
-  a.kblocks = kp / kTcBK;
+  a.kblocks = kp / cfg.bk;
   a.S = S;
   a.mpad = mp;
   a.npad = np;
   a.bn = bn;
+  a.bk = cfg.bk;
+  a.swz = cfg.swz;
   a.exact = exact;
-  a.nstages = tc_stages(S, bn, a.kblocks);
-  a.nacc = tc_nacc(S, exact, a.kblocks);
-  int cols = a.nacc * bn;
-  int tc = 32;
-  while (tc < cols) tc *= 2;
-  a.tmem_cols = tc;
+  a.nstages = cfg.nstages;
+  a.nacc = tc_nacc(S, exact, kp);
+  a.tmem_cols = cfg.tmem_cols;
   a.nbatch = g.nbatch;
   a.m = g.A.nv;
   a.m_last = g.A.nv_last;
@@ -623,9 +657,9 @@ cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st) {
   a.ldc = g.ldc;
   a.sbc = g.sbc;
   a.coff = g.coff;
-  a.sign = g.sign;
+  a.sign = g.sign > 0 ? 1 : -1;
   a.status = status;
-  const size_t smem = a.nstages * tc_stage_bytes(S, bn) + 1024 + 256;
+  const size_t smem = cfg.smem;
   static bool init = false;
   if (!init) {
     e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBudget);
@@ -635,7 +669,7 @@ cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st) {
   dim3 grid(mp / kTcBM, np / bn, g.nbatch);
   // bf16 tensor-core flops issued: S (S + 1) / 2 digit products
   ProfScope ps(kClsGemmTc, st, 2.0 * (double)mp * np * kp * (S * (S + 1) / 2) * nb);
-  tc_gemm_kernel<<<grid, 128, smem, st>>>(ma, mb, a);
+  tc_gemm_kernel<<<grid, 256, smem, st>>>(ma, mb, a);
   return cudaGetLastError();
 }
 

@@ -48,6 +48,7 @@ struct TsluSmem {
   int *lab;         // rloc labels (panel rows)
   ArgMax *wbest;    // kNodeWarps
   ArgMax *slot;     // 1 (this CTA's partial argmax, read by peers)
+  ArgMax *gslot;    // 8 (the cluster's partial maxima, gathered)
   double *scal;     // [0] = 1 / pivot
   int *iscal;       // [0] pivot pos, [1] pivot label, [2] label at j, [3] zero column
   int *work;        // 4 * bk ints (root permutation bookkeeping)
@@ -55,7 +56,7 @@ struct TsluSmem {
 
 __host__ __device__ inline size_t tslu_smem_bytes(int rloc, int bk) {
   size_t s = (size_t)rloc * bk * 8 + 2 * (size_t)bk * 8;
-  s += (size_t)rloc * 4 + 16 * (kNodeWarps + 1) + 16 + 16 + 4 * (size_t)bk * 4 + 64;
+  s += (size_t)rloc * 4 + 16 * (kNodeWarps + 1) + 16 * 8 + 16 + 16 + 4 * (size_t)bk * 4 + 64;
   return s;
 }
 
@@ -71,6 +72,8 @@ __device__ inline TsluSmem tslu_carve(char *base, int rloc, int bk) {
   base += 16 * kNodeWarps;
   s.slot = (ArgMax *)base;
   base += 16;
+  s.gslot = (ArgMax *)base;
+  base += 16 * 8;
   s.scal = (double *)base;
   base += 16;
   s.iscal = (int *)base;
@@ -173,15 +176,14 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
       *s.slot = b;
     }
     node_sync(cl, G);
-    // (b) cluster argmax; read the pivot row and (owner of the pivot
-    //     position) the row at position j
+    // (b) cluster argmax (the G partial maxima read in parallel through
+    //     DSMEM); read the pivot row and (owner of the pivot position) the
+    //     row at position j
+    if (tid < G) s.gslot[tid] = (tid == rank) ? *s.slot : *cl.map_shared_rank(s.slot, tid);
+    __syncthreads();
     if (tid == 0) {
-      ArgMax b = *s.slot;
-      for (int q = 0; q < G; ++q) {
-        if (q == rank) continue;
-        ArgMax o = *cl.map_shared_rank(s.slot, q);
-        b = argmax_better(b, o);
-      }
+      ArgMax b = s.gslot[0];
+      for (int q = 1; q < G; ++q) b = argmax_better(b, s.gslot[q]);
       s.iscal[0] = b.pos;
       s.iscal[3] = (b.key == 0ull);
     }

@@ -160,11 +160,15 @@ __global__ void __launch_bounds__(kQrThreads, 1) tsqr_node_kernel(TsqrNodeArgs a
     qr_sync(cl, G);
     // (b) reflector from the cluster's partials (fixed order: same value in
     //     every CTA)
+    // the G partial sums and alpha, read in parallel through DSMEM
+    if (tid < G) part[tid] = (tid == rank) ? sc[0] : *cl.map_shared_rank(sc, tid);
+    if (tid == 32)
+      sc[5] = (oj == rank) ? tile[lj + (size_t)j * ld] : *cl.map_shared_rank(tile + lj + (size_t)j * ld, oj);
+    __syncthreads();
     if (tid == 0) {
       double xn2 = 0.0;
-      for (int q = 0; q < G; ++q) xn2 += (q == rank) ? sc[0] : *cl.map_shared_rank(sc, q);
-      double alpha = (oj == rank) ? tile[lj + (size_t)j * ld]
-                                  : *cl.map_shared_rank(tile + lj + (size_t)j * ld, oj);
+      for (int q = 0; q < G; ++q) xn2 += part[q];  // fixed order: the same value in every CTA
+      const double alpha = sc[5];
       if (xn2 == 0.0) {
         sc[4] = 1.0;
         sc[2] = 0.0;
@@ -211,8 +215,14 @@ __global__ void __launch_bounds__(kQrThreads, 1) tsqr_node_kernel(TsqrNodeArgs a
     }
     qr_sync(cl, G);
     for (int q = j + 1 + tid; q < bk; q += kQrThreads) {
+      double v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)  // all remote loads in flight, then the ordered sum
+        v[r] = (r < G) ? ((r == rank) ? wcta[q] : *cl.map_shared_rank(wcta + q, r)) : 0.0;
       double s = 0.0;
-      for (int r = 0; r < G; ++r) s += (r == rank) ? wcta[q] : *cl.map_shared_rank(wcta + q, r);
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (r < G) s += v[r];
       w[q] = tj * s;
     }
     __syncthreads();
