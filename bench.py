@@ -56,6 +56,10 @@ def parse():
     p.add_argument("--mixed-slices", type=int, default=4)
     p.add_argument("--mixed-exact", type=int, default=1)
     p.add_argument("--no-mixed", action="store_true")
+    p.add_argument("--serve-rate", type=float, default=100.0)
+    p.add_argument("--serve-duration", type=float, default=3.0)
+    p.add_argument("--serve-nmax", type=int, default=2048)
+    p.add_argument("--no-serve", action="store_true")
     return p.parse_args()
 
 
@@ -303,6 +307,11 @@ def run_ours(a, rank: int, world: int, local: int):
     if not a.no_mixed:
         lu_forms = lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world)
 
+    # ---- serving: continuous batching of an open-loop Poisson stream ---------
+    serving = None
+    if not a.no_serve and world == 1:
+        serving = serving_run(a)
+
     # ---- end to end through the public API with host buffers --------------
     e2e = None
     if a.e2e_steps > 0:
@@ -360,6 +369,7 @@ def run_ours(a, rank: int, world: int, local: int):
         "kernels": kernels,
         "check": {"x_rel_err_calu": err_lu, "x_rel_err_caqr": err_qr},
         "lu_forms": lu_forms,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
 
@@ -481,6 +491,39 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
                                        "update on the tensor cores"}
     for k, v in kernels_of.items():
         out[k]["kernels"] = v
+    return out
+
+
+def serving_run(a):
+    """Open-loop Poisson stream of A x = b (CALU) and least-squares (CAQR, m = 4n)
+    requests, n log-uniform in [64, nmax], 1-16 right-hand sides, replayed in
+    real time into the continuous-batching server; plain FP64 and mixed forms.
+    Matrices come from a pre-generated pool per size (untimed)."""
+    from paper_1303_5837_gb300 import inputs, serve
+    work = serve.poisson_workload(a.serve_rate, a.serve_duration, seed=11, nmax=a.serve_nmax)
+    pool = {}
+    for _, kind, m, n, nrhs in work:
+        key = (kind, n)
+        if key not in pool:
+            pool[key] = (inputs.gaussian(m, n, n + (7 if kind == "ls" else 0)), inputs.gaussian(m, 16, n + 1))
+    out = {"rate_per_s": a.serve_rate, "duration_s": a.serve_duration, "requests": len(work),
+           "n_range": [64, a.serve_nmax], "pool_sizes": len(pool)}
+    for form in ("fp64", "mixed"):
+        srv = serve.SolveServer(hbm_budget=64 << 30, slots=4, form=form)
+        try:
+            t0 = time.perf_counter()
+            for t, kind, m, n, nrhs in work:
+                now = time.perf_counter() - t0
+                if t > now:
+                    time.sleep(t - now)
+                A, Bm = pool[(kind, n)]
+                srv.submit(kind, A, Bm[:, :nrhs])
+            srv.drain(timeout=600)
+            st = srv.stats()
+            st["failed"] = sum(1 for r in srv.completed if r.status != "done")
+        finally:
+            srv.close()
+        out[form] = st
     return out
 
 

@@ -1,0 +1,249 @@
+"""Continuous-batching solve server on one GPU.
+
+Requests (A x = b by CALU + getrs, or least squares by CAQR + geqrs) arrive
+at any time.  A scheduler thread admits them in arrival order as soon as a
+slot is free and their HBM footprint (matrix, right-hand sides, solution and
+the library's workspace, sized by the C-ABI workspace queries) fits in the
+remaining budget; a request larger than the whole budget is rejected.  Each
+slot is a worker thread with its own CUDA stream, so admitted requests run
+concurrently on the device while later ones wait.  Factors stay on the device
+for the life of a request; the result comes back to the host.
+
+Every computation goes through the C-ABI (``_binding``); this module only
+schedules, allocates (torch caching allocator) and moves data.
+"""
+from __future__ import annotations
+
+import math
+import queue
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _binding as B
+
+LU, LS = "lu", "ls"
+
+
+@dataclass(eq=False)  # requests compare by identity
+class Request:
+    kind: str                   # "lu" (square A x = b) or "ls" (least squares, m >= n)
+    A: np.ndarray               # host, column-major float64
+    B: np.ndarray               # host, m x nrhs
+    arrival: float = 0.0
+    footprint: int = 0
+    status: str = "pending"     # pending, running, done, rejected, failed
+    X: np.ndarray | None = None
+    t_done: float = 0.0
+    error: str = ""
+    done: threading.Event = field(default_factory=threading.Event)
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.arrival
+
+
+def footprint(kind: str, m: int, n: int, nrhs: int, b: int, tree, form: str = "fp64") -> int:
+    """Device bytes a request holds while it runs."""
+    mats = 8 * (m * n + 2 * m * nrhs)
+    if kind == LU:
+        if form == "mixed":
+            w = B.ca_gesv_mixed_workspace(n, nrhs, b, tree, 4, True)
+            return mats + 8 * n * n + w + 4 * n + 4096
+        return mats + B.ca_calu_workspace(m, n, b, tree) + 4 * n + 4096
+    if form == "mixed":
+        q, w = B.ca_caqr_mixed_workspace(m, n, b, tree, 7, True)
+    else:
+        q, w = B.ca_caqr_workspace(m, n, b, tree)
+    w = max(w, B.ca_geqrs_workspace(m, n, nrhs, b, tree))
+    return mats + q + w + 4096
+
+
+class SolveServer:
+    """``form``: "fp64" (plain FP64 factorizations) or "mixed" (LU: tensor-core
+    update + FP64 refinement; LS: 7-digit tensor-core tree update)."""
+
+    def __init__(self, hbm_budget: int, slots: int = 4, b: int = 128, leaf_rows: int = 256,
+                 levels=((4, 0), (0, 0)), form: str = "fp64", device: int = 0, execute=None):
+        self.budget = int(hbm_budget)
+        self.b = b
+        self.leaf_rows = leaf_rows
+        self.levels = tuple(levels)
+        self.form = form
+        self.device = device
+        self._on_gpu = execute is None
+        self._execute = execute or self._run_on_gpu
+        self._pending: queue.Queue = queue.Queue()
+        self._cv = threading.Condition()
+        self._used = 0
+        self._free_slots = list(range(slots))
+        self._work = [queue.Queue() for _ in range(slots)]
+        self.max_used = 0
+        self._submitted = 0
+        self._finished = 0
+        self.completed: list[Request] = []
+        self.rejected: list[Request] = []
+        self._stop = False
+        self._sched = threading.Thread(target=self._schedule, daemon=True)
+        self._workers = [threading.Thread(target=self._worker, args=(i,), daemon=True) for i in range(slots)]
+        self._sched.start()
+        for w in self._workers:
+            w.start()
+
+    # ---- public ------------------------------------------------------------
+    def tree(self):
+        lv = self.levels
+        return B.make_tree(self.leaf_rows, lv)
+
+    def submit(self, kind: str, A: np.ndarray, Bm: np.ndarray) -> Request:
+        if Bm.ndim == 1:
+            Bm = Bm[:, None]
+        r = Request(kind, np.asfortranarray(A), np.asfortranarray(Bm), arrival=time.perf_counter())
+        m, n = r.A.shape
+        if kind == LU and m != n:
+            raise ValueError("lu requests need a square matrix")
+        if kind == LS and m < n:
+            raise ValueError("ls requests need m >= n")
+        r.footprint = footprint(kind, m, n, r.B.shape[1], self.b, self.tree(), self.form)
+        with self._cv:
+            self._submitted += 1
+        self._pending.put(r)
+        return r
+
+    def _finish(self, r: Request):
+        with self._cv:
+            self._finished += 1
+            self._cv.notify_all()
+        r.done.set()
+
+    def drain(self, timeout: float = 600.0):
+        """Wait until every submitted request is done, failed or rejected."""
+        deadline = time.perf_counter() + timeout
+        with self._cv:
+            while self._finished < self._submitted:
+                left = deadline - time.perf_counter()
+                if left <= 0:
+                    raise TimeoutError("requests still pending")
+                self._cv.wait(timeout=min(left, 0.05))
+
+    def close(self):
+        self._stop = True
+        self._pending.put(None)
+        for q in self._work:
+            q.put(None)
+        self._sched.join(timeout=10)
+        for w in self._workers:
+            w.join(timeout=10)
+
+    def stats(self) -> dict:
+        lat = sorted(r.latency for r in self.completed)
+        if not lat:
+            return {"completed": 0, "rejected": len(self.rejected)}
+        pct = lambda p: lat[min(len(lat) - 1, int(math.ceil(p * len(lat))) - 1)]
+        span = max(r.t_done for r in self.completed) - min(r.arrival for r in self.completed)
+        return {"completed": len(lat), "rejected": len(self.rejected), "p50_s": pct(0.50),
+                "p99_s": pct(0.99), "solves_per_s": len(lat) / span if span > 0 else float("inf"),
+                "max_hbm_in_use": self.max_used, "budget": self.budget}
+
+    # ---- scheduler: admission by HBM footprint, arrival order ---------------
+    def _schedule(self):
+        while not self._stop:
+            r = self._pending.get()
+            if r is None:
+                return
+            if r.footprint > self.budget:
+                r.status = "rejected"
+                r.t_done = time.perf_counter()
+                self.rejected.append(r)
+                self._finish(r)
+                continue
+            with self._cv:
+                # arrival order: the head request waits for a slot and memory
+                while not self._stop and (not self._free_slots or self._used + r.footprint > self.budget):
+                    self._cv.wait(timeout=0.05)
+                if self._stop:
+                    return
+                slot = self._free_slots.pop(0)
+                self._used += r.footprint
+                self.max_used = max(self.max_used, self._used)
+                r.status = "running"
+            self._work[slot].put(r)
+
+    def _release(self, slot: int, r: Request):
+        with self._cv:
+            self._used -= r.footprint
+            self._free_slots.append(slot)
+            self._cv.notify_all()
+
+    def _worker(self, slot: int):
+        ctx = None
+        while True:
+            r = self._work[slot].get()
+            if r is None:
+                return
+            try:
+                if ctx is None:
+                    ctx = self._make_context()
+                r.X = self._execute(r, ctx)
+                r.status = "done"
+            except Exception as e:  # the request fails, the server keeps serving
+                r.status = "failed"
+                r.error = repr(e)
+            r.t_done = time.perf_counter()
+            if r.status == "done":
+                self.completed.append(r)
+            self._release(slot, r)
+            self._finish(r)
+
+    # ---- execution on the GPU -------------------------------------------------
+    def _make_context(self):
+        if not self._on_gpu:
+            return None
+        import torch
+        torch.cuda.set_device(self.device)
+        return torch.cuda.Stream(device=self.device)
+
+    def _run_on_gpu(self, r: Request, stream):
+        import torch
+        dev = torch.device("cuda", self.device)
+        m, n = r.A.shape
+        nrhs = r.B.shape[1]
+        tree = self.tree()
+        with torch.cuda.stream(stream):
+            A = torch.from_numpy(np.ascontiguousarray(r.A.T)).to(dev, non_blocking=True).t()
+            Bm = torch.from_numpy(np.ascontiguousarray(r.B.T)).to(dev, non_blocking=True).t()
+            if r.kind == LU and self.form == "mixed":
+                X, it, be, info = B.calu_gesv_mixed(A, Bm, self.b, tree, slices=4, exact=True, tol=1e-14,
+                                                     stream=stream)
+            elif r.kind == LU:
+                ipiv, info = B.calu_factor(A, self.b, tree, stream=stream)
+                B.calu_getrs(A, ipiv, Bm, stream=stream)
+                X = Bm
+            else:
+                if self.form == "mixed":
+                    qtree, info = B.caqr_factor_mixed(A, self.b, tree, slices=7, exact=True, stream=stream)
+                else:
+                    qtree, info = B.caqr_factor(A, self.b, tree, stream=stream)
+                B.caqr_geqrs(A, self.b, tree, qtree, Bm, stream=stream)
+                X = Bm[:n]
+            out = X.cpu()  # waits for this request's stream only
+            stream.synchronize()
+        return np.asfortranarray(out.numpy())
+
+
+def poisson_workload(rate: float, duration: float, seed: int, nmin: int = 64, nmax: int = 2048,
+                     ls_fraction: float = 0.5, max_rhs: int = 16):
+    """Arrival times and shapes of an open-loop Poisson stream: n log-uniform in
+    [nmin, nmax], LU (m = n) or LS (m = 4n) requests, 1..max_rhs right-hand sides."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    t, out = 0.0, []
+    while True:
+        t += g.exponential(1.0 / rate)
+        if t > duration:
+            return out
+        n = int(round(math.exp(g.uniform(math.log(nmin), math.log(nmax)))))
+        kind = LS if g.uniform() < ls_fraction else LU
+        m = 4 * n if kind == LS else n
+        out.append((t, kind, m, n, int(g.integers(1, max_rhs + 1))))

@@ -1,0 +1,72 @@
+"""The serving loop's scheduling on the host (no GPU): requests are admitted in
+arrival order only while their HBM footprint fits the budget and a slot is
+free, oversized requests are rejected, work overlaps across slots, and the
+latency statistics cover every completed request."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_1303_5837_gb300 import serve
+
+
+def test_admission_by_footprint_and_slots():
+    active = []
+    peak = {"n": 0, "bytes": 0}
+    lock = threading.Lock()
+
+    def fake_execute(r, ctx):
+        with lock:
+            active.append(r)
+            peak["n"] = max(peak["n"], len(active))
+            peak["bytes"] = max(peak["bytes"], sum(x.footprint for x in active))
+        time.sleep(0.02)
+        with lock:
+            active.remove(r)
+        return np.zeros((r.A.shape[1], r.B.shape[1]))
+
+    n = 256
+    one = serve.footprint("lu", n, n, 1, 128, serve.B.make_tree(256, [(4, 0), (0, 0)]))
+    srv = serve.SolveServer(hbm_budget=int(2.5 * one), slots=4, execute=fake_execute)
+    try:
+        reqs = [srv.submit("lu", np.eye(n), np.ones(n)) for _ in range(8)]
+        huge = srv.submit("lu", np.eye(2 * n), np.ones(2 * n))  # 4x the footprint: over budget
+        srv.drain(timeout=30)
+    finally:
+        srv.close()
+    assert all(r.status == "done" for r in reqs)
+    assert huge.status == "rejected"
+    assert peak["n"] == 2                     # the budget holds two at a time, not four slots' worth
+    assert peak["bytes"] <= srv.budget
+    assert srv.max_used <= srv.budget
+    st = srv.stats()
+    assert st["completed"] == 8 and st["rejected"] == 1
+    assert st["p99_s"] >= st["p50_s"] > 0
+
+
+def test_poisson_workload_shapes():
+    w = serve.poisson_workload(rate=200.0, duration=2.0, seed=1, nmin=64, nmax=2048)
+    assert 300 < len(w) < 500
+    ts = [x[0] for x in w]
+    assert ts == sorted(ts) and ts[-1] <= 2.0
+    for t, kind, m, n, nrhs in w:
+        assert 64 <= n <= 2048 and 1 <= nrhs <= 16
+        assert m == (4 * n if kind == "ls" else n)
+
+
+def test_failed_request_does_not_stop_the_server():
+    def flaky(r, ctx):
+        if r.B[0, 0] < 0:
+            raise RuntimeError("planted failure")
+        return np.zeros((1, 1))
+
+    srv = serve.SolveServer(hbm_budget=1 << 40, slots=2, execute=flaky)
+    try:
+        bad = srv.submit("lu", np.eye(64), -np.ones(64))
+        good = srv.submit("lu", np.eye(64), np.ones(64))
+        srv.drain(timeout=30)
+    finally:
+        srv.close()
+    assert bad.status == "failed" and "planted" in bad.error
+    assert good.status == "done"
