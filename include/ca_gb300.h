@@ -35,6 +35,16 @@
  *     The tree fixes the numerical result; where each node runs on the GPU
  *     (one CTA, a thread-block cluster sharing its rows through distributed
  *     shared memory, successive grid launches) is the library's choice.
+ *   - Look-ahead (calu_factor, caqr_factor and their _mixed forms, when there
+ *     is more than one panel): the next panel's tree factorization runs on a
+ *     helper stream of the highest priority while the current trailing
+ *     update finishes on `stream`.  The library creates one helper stream and
+ *     two events per (device, caller stream) on first use (up to 64 pairs,
+ *     beyond that plain stream order) and keeps them until the process exits.
+ *     Every piece of work is ordered by events that start from and end on
+ *     `stream`, so the caller sees ordinary stream semantics; results are
+ *     bit-identical to the serial order.  Calls on one caller stream must not
+ *     be enqueued from two host threads at once.
  */
 #ifndef CA_GB300_H
 #define CA_GB300_H

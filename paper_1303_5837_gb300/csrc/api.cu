@@ -2,6 +2,7 @@
 // layout and the panel loops of CALU and CAQR (host side; every step runs in
 // the kernels of panel_lu.cu, panel_qr.cu, gemm_fp64.cu and solve.cu).
 #include <cstring>
+#include <mutex>
 
 #include "ca_internal.cuh"
 
@@ -158,6 +159,39 @@ int qr_shape(int m, int n, int b, const ca_tree_t *tree, int *nl_max, size_t *qb
   return CA_OK;
 }
 
+// Look-ahead: the next panel's factorization (TSLU / TSQR) runs on a helper
+// stream of the highest priority as soon as the current update has reached
+// its columns, while the rest of the update continues on the caller's
+// stream.  One helper stream and two events per (device, caller stream),
+// created on first use; they never hold memory of the caller.
+struct Lookahead {
+  int dev;
+  cudaStream_t user, helper;
+  cudaEvent_t ev_next, ev_panel;
+};
+
+Lookahead *lookahead_for(cudaStream_t user) {
+  static std::mutex mu;
+  static Lookahead pool[64];
+  static int used = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  for (int i = 0; i < used; ++i)
+    if (pool[i].dev == dev && pool[i].user == user) return &pool[i];
+  if (used == 64) return nullptr;  // plain stream order beyond 64 caller streams
+  Lookahead la;
+  la.dev = dev;
+  la.user = user;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return nullptr;
+  if (cudaStreamCreateWithPriority(&la.helper, cudaStreamNonBlocking, greatest) != cudaSuccess) return nullptr;
+  if (cudaEventCreateWithFlags(&la.ev_next, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+  if (cudaEventCreateWithFlags(&la.ev_panel, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+  pool[used] = la;
+  return &pool[used++];
+}
+
 // Panel loop of CALU (Algorithm "1D multilevel CALU" with one level): the
 // trailing update runs in FP64 (tcws == nullptr) or on the tensor cores with
 // `slices` digits (reduced precision, exact = per-diagonal accumulators).
@@ -170,33 +204,49 @@ int calu_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int
   LuPanelWs ws;
   lu_panel_ws_carve(work, nl, bw, ws);
   const int L = tree->leaf_rows;
+  Lookahead *la = (K > b) ? lookahead_for(stream) : nullptr;
+  if (la && cudaEventRecord(la->ev_next, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  auto update = [&](int mrows, int ncols, int kdim, const double *L21, const double *U12, double *C) -> cudaError_t {
+    if (mrows <= 0 || ncols <= 0) return cudaSuccess;
+    if (tcws)
+      return gemm_minus_tc(mrows, ncols, kdim, L21, lda, U12, lda, C, lda, slices, exact, tcws, dev_info + 1, stream);
+    return gemm_minus_f64(mrows, ncols, kdim, L21, lda, U12, lda, C, lda, stream);
+  };
   for (int kb = 0; kb < K; kb += b) {
     const int bk = (K - kb < b) ? K - kb : b;
     const int mk = m - kb;
     Plan plan;
     if (!build_plan(nleaves_of(mk, L), *tree, plan)) return CA_ERR_TREE;
     double *P = A + kb + (size_t)kb * lda;
+    cudaStream_t ps = la ? la->helper : stream;
+    if (la && cudaStreamWaitEvent(ps, la->ev_next, 0) != cudaSuccess) return CA_ERR_LAUNCH;
     // 1. tournament pivoting over the tree (TSLU)
-    if (tslu_panel(mk, bk, P, lda, L, plan, ws, ipiv + kb, kb, dev_info, stream) != cudaSuccess)
+    if (tslu_panel(mk, bk, P, lda, L, plan, ws, ipiv + kb, kb, dev_info, ps) != cudaSuccess)
+      return CA_ERR_LAUNCH;
+    if (la && (cudaEventRecord(la->ev_panel, ps) != cudaSuccess ||
+               cudaStreamWaitEvent(stream, la->ev_panel, 0) != cudaSuccess))
       return CA_ERR_LAUNCH;
     // 2. swap rows at left and right of the panel
     if (laswp_apply(n, A, lda, kb, ws, bk, stream) != cudaSuccess) return CA_ERR_LAUNCH;
-    // 3. L11 \ U11 into place, L21 = A21 U11^-1
+    // 3. L11 \\ U11 into place, L21 = A21 U11^-1
     if (lu_panel_finish(mk, bk, P, lda, ws, stream) != cudaSuccess) return CA_ERR_LAUNCH;
     const int nt = n - kb - bk;
     if (nt > 0) {
       double *A12 = A + kb + (size_t)(kb + bk) * lda;
       // 4. U12 = L11^-1 A12
       if (trsm_u12(bk, nt, ws.lu11, bk, A12, lda, stream) != cudaSuccess) return CA_ERR_LAUNCH;
-      // 5. A22 -= L21 U12
-      if (mk - bk > 0) {
-        cudaError_t e;
-        if (tcws)
-          e = gemm_minus_tc(mk - bk, nt, bk, P + bk, lda, A12, lda, A12 + bk, lda, slices, exact, tcws,
-                            dev_info + 1, stream);
-        else
-          e = gemm_minus_f64(mk - bk, nt, bk, P + bk, lda, A12, lda, A12 + bk, lda, stream);
-        if (e != cudaSuccess) return CA_ERR_LAUNCH;
+      // 5. A22 -= L21 U12: first the next panel's columns, then the rest
+      //    (the next tournament starts in between)
+      const int nnext = (kb + bk < K) ? ((K - kb - bk < b) ? K - kb - bk : b) : 0;
+      if (la && nnext > 0 && nnext < nt) {
+        if (update(mk - bk, nnext, bk, P + bk, A12, A12 + bk) != cudaSuccess) return CA_ERR_LAUNCH;
+        if (cudaEventRecord(la->ev_next, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+        if (update(mk - bk, nt - nnext, bk, P + bk, A12 + (size_t)nnext * lda, A12 + bk + (size_t)nnext * lda) !=
+            cudaSuccess)
+          return CA_ERR_LAUNCH;
+      } else {
+        if (update(mk - bk, nt, bk, P + bk, A12, A12 + bk) != cudaSuccess) return CA_ERR_LAUNCH;
+        if (la && cudaEventRecord(la->ev_next, stream) != cudaSuccess) return CA_ERR_LAUNCH;
       }
     }
   }
@@ -205,34 +255,53 @@ int calu_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int
 
 // Panel loop of CAQR (Algorithm ML-CAQR with one level): TSQR, then the tree
 // update of the trailing columns in FP64 (tcws == nullptr) or on the tensor
-// cores.
+// cores.  With look-ahead the per-node arrays alternate between two copies.
 int caqr_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, double *qtree, void *work, int nl,
              void *tcws, int slices, int exact, int *dev_info, cudaStream_t stream) {
   if (cudaMemsetAsync(dev_info, 0, 2 * sizeof(int), stream) != cudaSuccess) return CA_ERR_LAUNCH;
   if (n == 0) return CA_OK;
-  QrPanelWs ws;
-  qr_panel_ws_carve(work, nl, ws);
+  QrPanelWs wsv[2];
+  qr_panel_ws_carve(work, nl, wsv[0]);
+  qr_panel_ws_carve((char *)work + align256(qr_panel_ws_bytes(nl)), nl, wsv[1]);
   const int L = tree->leaf_rows;
+  Lookahead *la = (n > b) ? lookahead_for(stream) : nullptr;
+  if (la && cudaEventRecord(la->ev_next, stream) != cudaSuccess) return CA_ERR_LAUNCH;
   size_t off = 0;
-  for (int kb = 0; kb < n; kb += b) {
+  for (int kb = 0, k = 0; kb < n; kb += b, ++k) {
     const int bk = (n - kb < b) ? n - kb : b;
     const int mk = m - kb;
     Plan plan;
     if (!build_plan(nleaves_of(mk, L), *tree, plan)) return CA_ERR_TREE;
     double *P = A + kb + (size_t)kb * lda;
     double *Tp = qtree + off;
+    const QrPanelWs &ws = wsv[k & 1];
+    cudaStream_t ps = la ? la->helper : stream;
+    if (la && cudaStreamWaitEvent(ps, la->ev_next, 0) != cudaSuccess) return CA_ERR_LAUNCH;
     // 1. TSQR: leaves, then the R-elimination tree
-    if (tsqr_panel(mk, bk, b, P, lda, L, plan, Tp, ws, dev_info, stream) != cudaSuccess) return CA_ERR_LAUNCH;
-    // 2. trailing columns: leaves' Q^T (UPFACT), then merges' Q^T (UPELIM)
+    if (tsqr_panel(mk, bk, b, P, lda, L, plan, Tp, ws, dev_info, ps) != cudaSuccess) return CA_ERR_LAUNCH;
+    if (la && (cudaEventRecord(la->ev_panel, ps) != cudaSuccess ||
+               cudaStreamWaitEvent(stream, la->ev_panel, 0) != cudaSuccess))
+      return CA_ERR_LAUNCH;
+    // 2. trailing columns: leaves' Q^T (UPFACT), then merges' Q^T (UPELIM);
+    //    the next panel's columns first
     const int nt = n - kb - bk;
-    if (nt > 0) {
-      cudaError_t e;
+    auto apply = [&](double *C, int ncols) -> cudaError_t {
+      if (ncols <= 0) return cudaSuccess;
       if (tcws)
-        e = tree_apply_qt_tc(mk, bk, b, P, lda, L, plan, Tp, P + (size_t)bk * lda, lda, nt, ws, tcws, slices,
-                             exact, dev_info + 1, stream);
-      else
-        e = tree_apply_qt(mk, bk, b, P, lda, L, plan, Tp, P + (size_t)bk * lda, lda, nt, ws, stream);
-      if (e != cudaSuccess) return CA_ERR_LAUNCH;
+        return tree_apply_qt_tc(mk, bk, b, P, lda, L, plan, Tp, C, lda, ncols, ws, tcws, slices, exact,
+                                dev_info + 1, stream);
+      return tree_apply_qt(mk, bk, b, P, lda, L, plan, Tp, C, lda, ncols, ws, stream);
+    };
+    if (nt > 0) {
+      const int nnext = nt < b ? nt : b;
+      if (la && nnext < nt) {
+        if (apply(P + (size_t)bk * lda, nnext) != cudaSuccess) return CA_ERR_LAUNCH;
+        if (cudaEventRecord(la->ev_next, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+        if (apply(P + (size_t)(bk + nnext) * lda, nt - nnext) != cudaSuccess) return CA_ERR_LAUNCH;
+      } else {
+        if (apply(P + (size_t)bk * lda, nt) != cudaSuccess) return CA_ERR_LAUNCH;
+        if (la && cudaEventRecord(la->ev_next, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+      }
     }
     off += (size_t)(plan.nleaves + plan.nmerges) * b * b;
   }
@@ -241,7 +310,7 @@ int caqr_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, dou
 
 size_t caqr_mixed_ws(int m, int n, int b, const ca_tree_t *tree, int nl, int slices) {
   const int bk = b < n ? b : n;
-  return align256(qr_panel_ws_bytes(nl)) +
+  return 2 * align256(qr_panel_ws_bytes(nl)) +
          tree_tc_ws_bytes(m, bk, n - bk > 0 ? n - bk : 1, tree->leaf_rows, nl, slices);
 }
 
@@ -293,7 +362,7 @@ int ca_caqr_workspace(int m, int n, int b, const ca_tree_t *tree, size_t *qtree_
   if (rc == -5 || rc == -6) rc = (rc == -5) ? -3 : -4;
   if (rc != CA_OK) return rc;
   *qtree_bytes = q;
-  *work_bytes = qr_panel_ws_bytes(nl);
+  *work_bytes = 2 * align256(qr_panel_ws_bytes(nl));  // two copies for look-ahead
   return CA_OK;
 }
 
@@ -361,7 +430,7 @@ int caqr_factor(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, 
   if (n > 0 && !A) return -3;
   if (!dev_info) return -11;
   if (n > 0 && (!qtree || qtree_bytes < qneed)) return CA_ERR_WORKSPACE;
-  if (n > 0 && (!work || lwork < qr_panel_ws_bytes(nl))) return CA_ERR_WORKSPACE;
+  if (n > 0 && (!work || lwork < 2 * align256(qr_panel_ws_bytes(nl)))) return CA_ERR_WORKSPACE;
   return caqr_run(m, n, A, lda, b, tree, qtree, work, nl, nullptr, 0, 0, dev_info, stream);
 }
 
@@ -592,7 +661,7 @@ int caqr_factor_mixed(int m, int n, double *A, int lda, int b, const ca_tree_t *
   if (!dev_info) return -13;
   if (n > 0 && (!qtree || qtree_bytes < qneed)) return CA_ERR_WORKSPACE;
   if (n > 0 && (!work || lwork < caqr_mixed_ws(m, n, b, tree, nl, slices))) return CA_ERR_WORKSPACE;
-  char *tcws = n > 0 ? (char *)work + align256(qr_panel_ws_bytes(nl)) : nullptr;
+  char *tcws = n > 0 ? (char *)work + 2 * align256(qr_panel_ws_bytes(nl)) : nullptr;
   return caqr_run(m, n, A, lda, b, tree, qtree, work, nl, tcws, slices, exact, dev_info, stream);
 }
 
