@@ -74,6 +74,7 @@ typedef struct {
 #define CA_ERR_UNSUPPORTED -1002 /* valid shape this build cannot run        */
 #define CA_ERR_LAUNCH -1003      /* a kernel launch failed (CUDA error)      */
 #define CA_ERR_TREE -1004        /* malformed tree                           */
+#define CA_ERR_BATCH_ITEM -1005  /* an item of a batch is invalid            */
 
 #define CA_STATUS_NONFINITE 1
 
@@ -277,11 +278,62 @@ int calu_gesv_mixed(int n, int nrhs, const double *A, int lda, int b, const ca_t
                     int *iters, double *berr, int *dev_info, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batched factorizations: many small matrices of uneven shapes, each with   */
+/* its own panel width and tree, in one persistent launch                    */
+/* ------------------------------------------------------------------------ */
+
+#define CA_BATCH_CALU 0
+#define CA_BATCH_CAQR 1
+#define CA_DTYPE_F64 0
+#define CA_DTYPE_F32 1
+
+/* One matrix of a batch.  All pointers are device pointers owned by the
+ * caller; the element type (double or float) is the batch's dtype. */
+typedef struct {
+  int op;          /* CA_BATCH_CALU (calu_factor) or CA_BATCH_CAQR (caqr_factor) */
+  int m, n, lda;   /* column-major m x n, lda >= max(1, m); CAQR needs m >= n   */
+  void *A;         /* factored in place, same layout as calu_factor /           */
+                   /* caqr_factor                                               */
+  int *ipiv;       /* CALU: min(m, n) ints (1-based swap sequence)              */
+  void *qtree;     /* CAQR: the T blocks, layout of caqr_factor in elements of  */
+                   /* the batch's type (ca_caqr_workspace's qtree_bytes / 8     */
+                   /* elements)                                                 */
+  int *info;       /* 2 ints: [0] as calu_factor's dev_info[0] (first exactly   */
+                   /* zero U diagonal), [1] CA_STATUS_NONFINITE                 */
+  int b;           /* panel width, 1..128; at most 64 when n > b                */
+  ca_tree_t tree;  /* leaf_rows >= min(b, min(m, n))                            */
+} ca_batch_item_t;
+
+/* ca_batched_plan: validates the batch and writes the launch plan (host
+ * bytes: a header, then the items ordered by decreasing flop count, so the
+ * largest start first).  plan == NULL: sizes only.  *plan_bytes: bytes of
+ * the plan; *work_bytes: device workspace of ca_batched_factor.  The caller
+ * copies the plan bytes to device memory of the same size (any 16-byte
+ * aligned buffer) and keeps both copies until the factorization is done.
+ * Each item's numerical result is the one calu_factor / caqr_factor give for
+ * the same matrix, panel width and tree (Sec. 3.1 and 3.2), in the batch's
+ * precision.  Errors: -1 count < 0, -2 items NULL, -3 dtype,
+ * -5 / -6 size pointers NULL, CA_ERR_BATCH_ITEM for a malformed item,
+ * CA_ERR_UNSUPPORTED for an item whose tree node (leaf_rows, or
+ * fan-in x panel width rows) does not fit one CTA's shared memory. */
+int ca_batched_plan(int count, const ca_batch_item_t *items, int dtype, void *plan, size_t *plan_bytes,
+                    size_t *work_bytes);
+
+/* ca_batched_factor: one persistent launch (one CTA per SM; each CTA takes
+ * the next item from a device counter) that factors every item of the plan
+ * on `stream`; plan_host and plan_dev hold the same bytes.  Nothing is
+ * allocated and nothing waits on the host, so the call can be captured in a
+ * CUDA graph (make one call before capturing).  Errors: -1 plan_host not a
+ * plan, -2 plan_dev NULL, CA_ERR_WORKSPACE, CA_ERR_LAUNCH. */
+int ca_batched_factor(const void *plan_host, const void *plan_dev, void *work, size_t lwork,
+                      cudaStream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Instrumentation (no counterpart in the paper): launch counts and device   */
 /* time per kernel class, measured with CUDA events recorded on the stream   */
 /* each kernel is launched on.  Classes: 0 tslu_node, 1 laswp, 2 lu_finish,  */
 /* 3 trsm_u12, 4 gemm_fp64, 5 tsqr_node, 6 tree_apply, 7 solve,              */
-/* 8 split_bf16, 9 gemm_tc, 10 refine.                                        */
+/* 8 split_bf16, 9 gemm_tc, 10 refine, 11 batched.                           */
 /* ------------------------------------------------------------------------ */
 
 /* on = 1: create a pool of 2 * max_launches events (here, not during a

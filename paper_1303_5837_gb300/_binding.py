@@ -24,7 +24,12 @@ CA_ERR_WORKSPACE = -1001
 CA_ERR_UNSUPPORTED = -1002
 CA_ERR_LAUNCH = -1003
 CA_ERR_TREE = -1004
+CA_ERR_BATCH_ITEM = -1005
 CA_STATUS_NONFINITE = 1
+CA_BATCH_CALU = 0
+CA_BATCH_CAQR = 1
+CA_DTYPE_F64 = 0
+CA_DTYPE_F32 = 1
 
 
 class CaError(RuntimeError):
@@ -39,6 +44,21 @@ class ca_tree_t(ctypes.Structure):
         ("nlevels", ctypes.c_int),
         ("fan_in", ctypes.c_int * MAX_LEVELS),
         ("style", ctypes.c_int * MAX_LEVELS),
+    ]
+
+
+class ca_batch_item_t(ctypes.Structure):
+    _fields_ = [
+        ("op", ctypes.c_int),
+        ("m", ctypes.c_int),
+        ("n", ctypes.c_int),
+        ("lda", ctypes.c_int),
+        ("A", ctypes.c_void_p),
+        ("ipiv", ctypes.c_void_p),
+        ("qtree", ctypes.c_void_p),
+        ("info", ctypes.c_void_p),
+        ("b", ctypes.c_int),
+        ("tree", ca_tree_t),
     ]
 
 
@@ -64,9 +84,9 @@ SYMBOLS = ("ca_strerror", "ca_calu_workspace", "ca_caqr_workspace", "ca_geqrs_wo
            "ca_prof_enable", "ca_prof_read", "ca_launch_count", "ca_kernel_class_name",
            "ca_gemm_mixed_workspace", "ca_gemm_minus_mixed", "ca_calu_mixed_workspace",
            "calu_factor_mixed", "ca_gesv_mixed_workspace", "calu_gesv_mixed", "ca_caqr_mixed_workspace",
-           "caqr_factor_mixed")
+           "caqr_factor_mixed", "ca_batched_plan", "ca_batched_factor")
 KERNEL_CLASSES = ("tslu_node", "laswp", "lu_finish", "trsm_u12", "gemm_fp64", "tsqr_node",
-                  "tree_apply", "solve", "split_bf16", "gemm_tc", "refine")
+                  "tree_apply", "solve", "split_bf16", "gemm_tc", "refine", "batched")
 
 
 def lib_path() -> str:
@@ -107,6 +127,8 @@ def load(build_if_missing: bool = True):
                                   ctypes.c_double, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double), P, P]
     L.ca_caqr_mixed_workspace.argtypes = [I, I, I, T, I, I, PS, PS]
     L.caqr_factor_mixed.argtypes = [I, I, P, I, I, T, I, I, P, S, P, S, P, P]
+    L.ca_batched_plan.argtypes = [I, ctypes.POINTER(ca_batch_item_t), I, P, PS, PS]
+    L.ca_batched_factor.argtypes = [P, P, P, S, P]
     L.ca_prof_enable.argtypes = [I, I]
     L.ca_prof_read.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)]
@@ -424,3 +446,112 @@ def caqr_factor_mixed(A: torch.Tensor, b: int, tree: ca_tree_t, slices: int = 7,
                                   _ptr(dev_info), _stream(stream))
     _check("caqr_factor_mixed", rc)
     return qtree, dev_info
+
+
+# ---------------------------------------------------------------------------
+# batched factorizations
+# ---------------------------------------------------------------------------
+
+def ca_batched_plan(items, dtype: int):
+    """Host plan of a batch: (plan bytes as a ctypes buffer, work bytes).
+    ``items`` is a sequence of ca_batch_item_t."""
+    arr = (ca_batch_item_t * max(1, len(items)))(*items)
+    pb = ctypes.c_size_t(0)
+    wb = ctypes.c_size_t(0)
+    L = load()
+    _check("ca_batched_plan", L.ca_batched_plan(len(items), arr, dtype, None, ctypes.byref(pb), ctypes.byref(wb)))
+    plan = ctypes.create_string_buffer(pb.value)
+    _check("ca_batched_plan", L.ca_batched_plan(len(items), arr, dtype, plan, ctypes.byref(pb), ctypes.byref(wb)))
+    return plan, wb.value
+
+
+def ca_batched_factor(plan_host, plan_dev: torch.Tensor, work: torch.Tensor, stream=None):
+    rc = load().ca_batched_factor(ctypes.cast(plan_host, ctypes.c_void_p), _ptr(plan_dev), _ptr(work),
+                                  work.numel() * work.element_size(), _stream(stream))
+    _check("ca_batched_factor", rc)
+
+
+class BatchedFactor:
+    """Many CALU / CAQR factorizations in one persistent launch.
+
+    ``mats``: 2-D column-major CUDA tensors, all float64 or all float32,
+    factored in place.  ``ops[i]`` is "lu" or "qr"; ``bs[i]`` the panel width;
+    ``trees[i]`` a ca_tree_t.  After ``run()``: ``ipiv(i)`` (LU), ``qtree(i)``
+    (QR, the caqr_factor layout in the batch's type) and ``info(i)``.
+    ``graph()`` captures the launch in a CUDA graph and returns it."""
+
+    def __init__(self, mats, ops, bs, trees):
+        if not mats:
+            raise ValueError("empty batch")
+        dt = mats[0].dtype
+        if dt not in (torch.float64, torch.float32):
+            raise TypeError("float64 or float32 matrices")
+        self.dtype = CA_DTYPE_F64 if dt == torch.float64 else CA_DTYPE_F32
+        dev = mats[0].device
+        self.mats = list(mats)
+        self.ops = list(ops)
+        esz = 8 if dt == torch.float64 else 4
+        ipiv_off, q_off = [], []
+        ni, nq = 0, 0
+        shapes = []
+        for A, op, b, tree in zip(mats, ops, bs, trees):
+            if A.dim() != 2 or A.dtype != dt or not A.is_cuda:
+                raise TypeError("every matrix must be a 2-D CUDA tensor of the batch's dtype")
+            m, n = A.shape
+            if m > 0 and n > 0 and A.stride(0) != 1:
+                raise ValueError("matrices must be column-major")
+            lda = max(A.stride(1) if n > 1 else max(1, m), max(1, m))
+            shapes.append((m, n, lda))
+            ipiv_off.append(ni)
+            q_off.append(nq)
+            if op == "lu":
+                ni += max(1, min(m, n))
+            elif op == "qr":
+                qb, _ = ca_caqr_workspace(m, n, b, tree) if n > 0 else (0, 0)
+                nq += qb // 8
+            else:
+                raise ValueError("op must be 'lu' or 'qr'")
+        self.ipiv_all = torch.zeros(max(1, ni), dtype=torch.int32, device=dev)
+        self.qtree_all = torch.zeros(max(1, nq), dtype=dt, device=dev)
+        self.info_all = torch.zeros(2 * len(mats), dtype=torch.int32, device=dev)
+        self._ipiv_off, self._q_off = ipiv_off, q_off
+        items = []
+        for i, (A, op, b, tree) in enumerate(zip(mats, ops, bs, trees)):
+            m, n, lda = shapes[i]
+            it = ca_batch_item_t()
+            it.op = CA_BATCH_CALU if op == "lu" else CA_BATCH_CAQR
+            it.m, it.n, it.lda = m, n, lda
+            it.A = A.data_ptr() if A.numel() > 0 else None
+            it.ipiv = self.ipiv_all.data_ptr() + 4 * ipiv_off[i] if op == "lu" else None
+            it.qtree = self.qtree_all.data_ptr() + esz * q_off[i] if op == "qr" else None
+            it.info = self.info_all.data_ptr() + 8 * i
+            it.b = int(b)
+            it.tree = tree
+            items.append(it)
+        self.plan_host, wbytes = ca_batched_plan(items, self.dtype)
+        raw = torch.frombuffer(bytearray(self.plan_host.raw), dtype=torch.uint8)
+        self.plan_dev = raw.to(dev)
+        self.work = torch.empty(max(1, (wbytes + 7) // 8), dtype=torch.float64, device=dev)
+
+    def run(self, stream=None):
+        ca_batched_factor(self.plan_host, self.plan_dev, self.work, stream)
+
+    def graph(self):
+        """A CUDA graph of the launch (replay with .replay())."""
+        self.run()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run()
+        return g
+
+    def ipiv(self, i: int) -> torch.Tensor:
+        m, n = self.mats[i].shape
+        return self.ipiv_all[self._ipiv_off[i]: self._ipiv_off[i] + min(m, n)]
+
+    def qtree(self, i: int) -> torch.Tensor:
+        nxt = self._q_off[i + 1] if i + 1 < len(self._q_off) else self.qtree_all.numel()
+        return self.qtree_all[self._q_off[i]: nxt]
+
+    def info(self, i: int) -> torch.Tensor:
+        return self.info_all[2 * i: 2 * i + 2]

@@ -1,0 +1,965 @@
+// batched.cu -- many small, uneven CALU / CAQR factorizations in one
+// persistent launch.
+//
+// One CTA factors one whole matrix at a time: it takes the next item of an
+// LPT-ordered list (largest flop count first) from a device counter, runs the
+// item's CALU or CAQR panel loop with the item's own panel width and tree,
+// and moves on.  Every tree node lives in the CTA's shared memory; the
+// trailing updates run from global memory (L2-resident for these sizes)
+// through shared-memory tiles.  The numerics are those of calu_factor /
+// caqr_factor: the same tree (Sec. 3.1 / 3.2), GEPP with the first-maximum
+// rule at every node, LAPACK larfg / larft Householder conventions and the
+// same tree storage of Y and T, in FP64 or FP32.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <vector>
+
+#include "ca_internal.cuh"
+
+namespace cagb {
+namespace {
+
+constexpr int kBT = 256;  // threads per CTA
+constexpr int kBW = kBT / 32;
+constexpr int kBMaxRows = 1024;  // rows of a node tile
+constexpr int kBMaxB = 128;      // widest panel
+constexpr int kBMultiB = 64;     // widest panel when a trailing update follows
+constexpr int kTl = 64;          // tile of the trailing updates (rows and columns)
+constexpr int kTs = kTl + 1;     // odd stride of those tiles
+constexpr int kGk = 32;          // k chunk of the Schur-complement tile
+constexpr unsigned kPlanMagic = 0x43414231u;
+
+struct BatchHeader {
+  unsigned magic;
+  int count, dtype, ctas;
+  int smem_region;  // bytes of the phase region (after the fixed part)
+  int pad;
+  size_t slot_bytes;
+  size_t work_bytes;
+  double flops;
+};
+constexpr size_t kHeaderBytes = 256;
+
+template <class T>
+struct Num;
+template <>
+struct Num<double> {
+  static __device__ __forceinline__ unsigned long long key(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  }
+  static __device__ __forceinline__ bool bad(double x) { return not_finite(x); }
+  static __device__ __forceinline__ double root(double x) { return sqrt(x); }
+};
+template <>
+struct Num<float> {
+  static __device__ __forceinline__ unsigned long long key(float x) {
+    return (unsigned long long)(__float_as_uint(x) & 0x7fffffffu);
+  }
+  static __device__ __forceinline__ bool bad(float x) {
+    return (__float_as_uint(x) & 0x7f800000u) == 0x7f800000u;
+  }
+  static __device__ __forceinline__ float root(float x) { return sqrtf(x); }
+};
+
+template <class T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Fixed part of shared memory (the phase region follows it).
+template <class T>
+struct Fixed {
+  Plan plan;
+  int prow[kBMaxRows];  // panel row of each node row
+  int fz[kBMaxRows];    // merge rows: child-local index t (zeros left of column t)
+  int sel[kBMaxB], rev_top[kBMaxB], top_c[kBMaxB], far_c[kBMaxB];
+  int perm_src[2 * kBMaxB], perm_dst[2 * kBMaxB];
+  int iscal[16];
+  ArgMax wbest[kBW];
+  T tau[kBMaxB], w[kBMaxB], z[kBMaxB];
+  T red[kBW];
+  T scal[8];
+  int item, nperm, info0, status;
+};
+
+__host__ __device__ inline size_t fixed_bytes(int dtype) {
+  return ((dtype == CA_DTYPE_F32 ? sizeof(Fixed<float>) : sizeof(Fixed<double>)) + 15) & ~size_t(15);
+}
+
+__host__ __device__ inline int odd_ld(int rows) { return rows | 1; }
+
+// ---------------------------------------------------------------------------
+// GEPP on the node tile (rows x bk, ld), rows permuted physically with their
+// labels in F.prow; first maximum of |a| in the current order.  Returns the
+// number of steps, min(rows, bk).
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ int node_gepp(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool root, int kb) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int kmax = min(rows, bk);
+  for (int j = 0; j < kmax; ++j) {
+    ArgMax best{0ull, INT_MAX};
+    const T *cj = tile + (size_t)j * ld;
+    for (int p = j + tid; p < rows; p += kBT) best = argmax_better(best, ArgMax{Num<T>::key(cj[p]), p});
+    best = warp_argmax(best);
+    if (lane == 0) F.wbest[warp] = best;
+    __syncthreads();
+    if (tid == 0) {
+      ArgMax bb = F.wbest[0];
+      for (int q = 1; q < kBW; ++q) bb = argmax_better(bb, F.wbest[q]);
+      F.iscal[0] = bb.pos;
+      F.iscal[1] = (bb.key == 0ull);
+      if (bb.key == 0ull && root && F.info0 == 0) F.info0 = kb + j + 1;
+    }
+    __syncthreads();
+    if (F.iscal[1]) continue;  // zero column: no swap, no update
+    const int p = F.iscal[0];
+    if (p != j) {
+      for (int k = tid; k < bk; k += kBT) {
+        T t = tile[p + (size_t)k * ld];
+        tile[p + (size_t)k * ld] = tile[j + (size_t)k * ld];
+        tile[j + (size_t)k * ld] = t;
+      }
+      if (tid == 0) {
+        int t = F.prow[p];
+        F.prow[p] = F.prow[j];
+        F.prow[j] = t;
+      }
+      __syncthreads();
+    }
+    const T rinv = T(1) / tile[j + (size_t)j * ld];
+    T *cjw = tile + (size_t)j * ld;
+    for (int q = j + 1 + tid; q < rows; q += kBT) cjw[q] *= rinv;
+    __syncthreads();
+    for (int k = j + 1 + warp; k < bk; k += kBW) {
+      const T u = tile[j + (size_t)k * ld];
+      T *ck = tile + (size_t)k * ld;
+      for (int q = j + 1 + lane; q < rows; q += 32) ck[q] = fma(-cjw[q], u, ck[q]);
+    }
+    __syncthreads();
+  }
+  return kmax;
+}
+
+// Loads the node rows F.prow[0..rows) of panel columns 0..bk-1 into the tile;
+// merge rows skip (zero) the entries left of F.fz (use_fz).
+template <class T>
+__device__ void load_rows(const T *P, int lda, int rows, int bk, T *tile, int ld, Fixed<T> &F, bool use_fz) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool bad = false;
+  for (int k = warp; k < bk; k += kBW) {
+    const T *col = P + (size_t)k * lda;
+    for (int p = lane; p < rows; p += 32) {
+      T v = T(0);
+      if (!use_fz || k >= F.fz[p]) v = col[F.prow[p]];
+      bad |= Num<T>::bad(v);
+      tile[p + (size_t)k * ld] = v;
+    }
+  }
+  if (bad) atomicOr(&F.status, CA_STATUS_NONFINITE);
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// CALU of one matrix
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ void cta_calu(const ca_batch_item_t &it, Fixed<T> &F, T *R, int region_elems, char *slot) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T *A = (T *)it.A;
+  const int lda = it.lda, m = it.m, n = it.n, b = it.b, L = it.tree.leaf_rows;
+  const int K = min(m, n);
+  const int nlmax = (m + L - 1) / L;
+  int *cand[2] = {(int *)slot, (int *)slot + (size_t)nlmax * b};
+  int *ncand[2] = {cand[1] + (size_t)nlmax * b, cand[1] + (size_t)nlmax * b + nlmax};
+  T *lu11 = (T *)(((uintptr_t)(ncand[1] + nlmax) + 15) & ~(uintptr_t)15);
+  for (int kb = 0; kb < K; kb += b) {
+    const int bk = min(b, K - kb), mk = m - kb;
+    T *P = A + kb + (size_t)kb * lda;
+    const int nl = (mk + L - 1) / L;
+    if (tid == 0) build_plan(nl, it.tree, F.plan);
+    __syncthreads();
+    const int nrounds = F.plan.nrounds;
+    // ---- tournament: leaves ----
+    for (int j = 0; j < nl; ++j) {
+      const int r0 = j * L, rows = min(L, mk - r0), ld = odd_ld(rows);
+      for (int p = tid; p < rows; p += kBT) F.prow[p] = r0 + p;
+      __syncthreads();
+      load_rows(P, lda, rows, bk, R, ld, F, false);
+      const int km = node_gepp(R, ld, rows, bk, F, nrounds == 0, kb);
+      for (int p = tid; p < km; p += kBT) cand[0][(size_t)j * b + p] = F.prow[p];
+      if (tid == 0) ncand[0][j] = km;
+      if (nrounds == 0)
+        for (int k = warp; k < bk; k += kBW)
+          for (int p = lane; p < bk; p += 32) lu11[p + (size_t)k * b] = R[p + (size_t)k * ld];
+      __syncthreads();
+    }
+    // ---- tournament: merge rounds ----
+    int buf = 0;
+    for (int r = 0; r < nrounds; ++r) {
+      const RoundDesc rd = F.plan.r[r];
+      const bool last = (r == nrounds - 1);
+      const int *cin = cand[buf], *nin = ncand[buf];
+      int *cout = cand[buf ^ 1], *nout = ncand[buf ^ 1];
+      for (int o = 0; o < rd.n_out; ++o) {
+        int start, cnt, midx;
+        round_node(rd, o, start, cnt, midx);
+        if (cnt == 1) {
+          const int c = nin[start];
+          for (int p = tid; p < c; p += kBT) cout[(size_t)o * b + p] = cin[(size_t)start * b + p];
+          if (tid == 0) nout[o] = c;
+          __syncthreads();
+          continue;
+        }
+        int rows = 0;
+        for (int ch = 0; ch < cnt; ++ch) rows += nin[start + ch];
+        for (int p = tid; p < rows; p += kBT) {
+          int off = 0, ch = 0;
+          while (p >= off + nin[start + ch]) off += nin[start + ch++];
+          F.prow[p] = cin[(size_t)(start + ch) * b + (p - off)];
+        }
+        __syncthreads();
+        const int ld = odd_ld(rows);
+        load_rows(P, lda, rows, bk, R, ld, F, false);
+        const int km = node_gepp(R, ld, rows, bk, F, last, kb);
+        for (int p = tid; p < km; p += kBT) cout[(size_t)o * b + p] = F.prow[p];
+        if (tid == 0) nout[o] = km;
+        if (last)
+          for (int k = warp; k < bk; k += kBW)
+            for (int p = lane; p < bk; p += 32) lu11[p + (size_t)k * b] = R[p + (size_t)k * ld];
+        __syncthreads();
+      }
+      buf ^= 1;
+    }
+    // ---- LAPACK swap sequence from the root's selection ----
+    // (the root's labels are in F.prow[0..bk) after the last node)
+    if (tid == 0) {
+      for (int t = 0; t < bk; ++t) {
+        F.sel[t] = F.prow[t];
+        F.rev_top[t] = t;
+        F.top_c[t] = t;
+        F.far_c[t] = F.sel[t];
+      }
+      for (int i = 0; i < bk; ++i) {
+        const int lab = F.sel[i];
+        int pp, fslot = -1;
+        if (lab < bk) {
+          const int rr = F.rev_top[lab];
+          if (rr >= 0) {
+            pp = rr;
+          } else {
+            fslot = -rr - 1;
+            pp = F.sel[fslot];
+          }
+        } else {
+          pp = lab;
+          fslot = i;
+        }
+        it.ipiv[kb + i] = kb + pp + 1;
+        if (pp == i) continue;
+        const int ci = F.top_c[i];
+        F.top_c[i] = lab;
+        if (pp < bk) {
+          F.top_c[pp] = ci;
+          F.rev_top[ci] = pp;
+        } else {
+          F.far_c[fslot] = ci;
+          F.rev_top[ci] = -(fslot + 1);
+        }
+        if (lab < bk) F.rev_top[lab] = i;
+      }
+      int np = 0;
+      for (int t = 0; t < bk; ++t)
+        if (F.top_c[t] != t) {
+          F.perm_dst[np] = t;
+          F.perm_src[np] = F.top_c[t];
+          ++np;
+        }
+      for (int t = 0; t < bk; ++t)
+        if (F.sel[t] >= bk) {
+          F.perm_dst[np] = F.sel[t];
+          F.perm_src[np] = F.far_c[t];
+          ++np;
+        }
+      F.nperm = np;
+    }
+    __syncthreads();
+    // ---- swap rows at left and right (all n columns) ----
+    {
+      const int np = F.nperm;
+      for (int c = warp; c < n; c += kBW) {
+        T *col = A + kb + (size_t)c * lda;
+        T v[2 * kBMaxB / 32];
+#pragma unroll
+        for (int t = 0; t < 2 * kBMaxB / 32; ++t) {
+          const int i = lane + 32 * t;
+          if (i < np) v[t] = col[F.perm_src[i]];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 2 * kBMaxB / 32; ++t) {
+          const int i = lane + 32 * t;
+          if (i < np) col[F.perm_dst[i]] = v[t];
+        }
+      }
+    }
+    __syncthreads();
+    // ---- L11 \ U11 in place; L21 = A21 U11^-1 ----
+    {
+      T *U = R;                        // bk x bk, ld bk
+      T *rdg = U + (size_t)bk * bk;    // reciprocals of U's diagonal
+      T *Tt = rdg + bk;                // rt x bk, ld rt|1
+      int rt = (region_elems - bk * bk - bk) / bk - 1;  // the tile's ld is rt + 1
+      rt = min(rt, kBT) & ~31;
+      const int ldt = rt | 1;
+      for (int k = warp; k < bk; k += kBW)
+        for (int p = lane; p < bk; p += 32) {
+          const T v = lu11[p + (size_t)k * b];
+          P[p + (size_t)k * lda] = v;
+          U[p + (size_t)k * bk] = v;
+        }
+      __syncthreads();
+      for (int p = tid; p < bk; p += kBT) rdg[p] = T(1) / U[p + (size_t)p * bk];
+      __syncthreads();
+      for (int r0 = bk; r0 < mk; r0 += rt) {
+        const int rows = min(rt, mk - r0);
+        for (int k = warp; k < bk; k += kBW)
+          for (int p = lane; p < rows; p += 32) Tt[p + (size_t)k * ldt] = P[r0 + p + (size_t)k * lda];
+        __syncthreads();
+        if (tid < rows) {
+          T *x = Tt + tid;
+          for (int j = 0; j < bk; ++j) {
+            const T xj = x[(size_t)j * ldt] * rdg[j];
+            x[(size_t)j * ldt] = xj;
+            for (int k = j + 1; k < bk; ++k) x[(size_t)k * ldt] = fma(-xj, U[j + (size_t)k * bk], x[(size_t)k * ldt]);
+          }
+        }
+        __syncthreads();
+        for (int k = warp; k < bk; k += kBW)
+          for (int p = lane; p < rows; p += 32) P[r0 + p + (size_t)k * lda] = Tt[p + (size_t)k * ldt];
+        __syncthreads();
+      }
+    }
+    const int nt = n - kb - bk;
+    if (nt <= 0) continue;
+    T *A12 = P + (size_t)bk * lda;
+    // ---- U12 = L11^-1 A12 (unit lower) ----
+    {
+      T *Ls = R;                       // bk x bk, ld bk
+      T *Ts = Ls + (size_t)bk * bk;    // bk x ct, row stride ct
+      int ct = (region_elems - bk * bk) / bk;
+      ct = min(ct, kBT) & ~31;
+      for (int k = warp; k < bk; k += kBW)
+        for (int p = lane; p < bk; p += 32) Ls[p + (size_t)k * bk] = lu11[p + (size_t)k * b];
+      __syncthreads();
+      for (int c0 = 0; c0 < nt; c0 += ct) {
+        const int cols = min(ct, nt - c0);
+        for (int c = warp; c < cols; c += kBW)
+          for (int p = lane; p < bk; p += 32) Ts[(size_t)p * ct + c] = A12[p + (size_t)(c0 + c) * lda];
+        __syncthreads();
+        if (tid < cols) {
+          T *x = Ts + tid;
+          for (int i = 1; i < bk; ++i) {
+            T s = x[(size_t)i * ct];
+            for (int j = 0; j < i; ++j) s = fma(-Ls[i + (size_t)j * bk], x[(size_t)j * ct], s);
+            x[(size_t)i * ct] = s;
+          }
+        }
+        __syncthreads();
+        for (int c = warp; c < cols; c += kBW)
+          for (int p = lane; p < bk; p += 32) A12[p + (size_t)(c0 + c) * lda] = Ts[(size_t)p * ct + c];
+        __syncthreads();
+      }
+    }
+    // ---- A22 -= L21 U12 (64 x 64 tiles, k in chunks of 32) ----
+    {
+      const int mr = mk - bk;
+      const T *L21 = P + bk;
+      T *A22 = A12 + bk;
+      T *As = R;                     // kGk x kTl, As[k * kTl + r]
+      T *Bs = As + kGk * kTl;        // kGk x kTl, Bs[k * kTl + c]
+      const int tx = tid & 15, ty = tid >> 4;
+      for (int c0 = 0; c0 < nt; c0 += kTl)
+        for (int r0 = 0; r0 < mr; r0 += kTl) {
+          T acc[4][4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+          for (int k0 = 0; k0 < bk; k0 += kGk) {
+            const int kc = min(kGk, bk - k0);
+            for (int e = tid; e < kGk * kTl; e += kBT) {
+              const int r = e & (kTl - 1), k = e / kTl;
+              As[e] = (k < kc && r0 + r < mr) ? L21[r0 + r + (size_t)(k0 + k) * lda] : T(0);
+            }
+            for (int e = tid; e < kGk * kTl; e += kBT) {
+              const int k = e % kGk, c = e / kGk;
+              Bs[k * kTl + c] = (k < kc && c0 + c < nt) ? A12[k0 + k + (size_t)(c0 + c) * lda] : T(0);
+            }
+            __syncthreads();
+            for (int k = 0; k < kc; ++k) {
+              T a[4], bb[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) a[i] = As[k * kTl + tx + 16 * i];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) bb[j] = Bs[k * kTl + ty + 16 * j];
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+            }
+            __syncthreads();
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int c = c0 + ty + 16 * j;
+            if (c >= nt) continue;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int r = r0 + tx + 16 * i;
+              if (r < mr) A22[r + (size_t)c * lda] -= acc[i][j];
+            }
+          }
+        }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR of the node tile (rows x bk, ld); merge rows are zero left
+// of F.fz (skipped).  tau to F.tau; T (larft, forward columnwise) to Tg
+// (b x b, ld b, zero outside the top-left kmax x kmax).  Returns kmax.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ int node_qr(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool use_fz, T *Tg, int b) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int kmax = min(rows, bk);
+  for (int j = 0; j < kmax; ++j) {
+    T *cj = tile + (size_t)j * ld;
+    T ss = T(0);
+    for (int p = j + 1 + tid; p < rows; p += kBT)
+      if (!use_fz || F.fz[p] <= j) ss = fma(cj[p], cj[p], ss);
+    ss = wsum(ss);
+    if (lane == 0) F.red[warp] = ss;
+    __syncthreads();
+    if (tid == 0) {
+      T xn2 = T(0);
+      for (int q = 0; q < kBW; ++q) xn2 += F.red[q];
+      const T alpha = cj[j];
+      if (xn2 == T(0)) {
+        F.scal[4] = T(1);
+        F.tau[j] = T(0);
+      } else {
+        const T nrm = Num<T>::root(fma(alpha, alpha, xn2));
+        const T beta = (alpha >= T(0)) ? -nrm : nrm;
+        F.scal[1] = beta;
+        F.tau[j] = (beta - alpha) / beta;
+        F.scal[3] = T(1) / (alpha - beta);
+        F.scal[4] = T(0);
+      }
+    }
+    __syncthreads();
+    if (F.scal[4] != T(0)) continue;
+    const T scal = F.scal[3], tj = F.tau[j];
+    for (int p = j + 1 + tid; p < rows; p += kBT)
+      if (!use_fz || F.fz[p] <= j) cj[p] *= scal;
+    __syncthreads();
+    if (tid == 0) cj[j] = F.scal[1];
+    // w_q = tau v^T A(:, q), then A(:, q) -= v w_q; one warp per column q
+    for (int q = j + 1 + warp; q < bk; q += kBW) {
+      T *cq = tile + (size_t)q * ld;
+      T acc = (lane == 0) ? cq[j] : T(0);
+      for (int p = j + 1 + lane; p < rows; p += 32)
+        if (!use_fz || F.fz[p] <= j) acc = fma(cj[p], cq[p], acc);
+      const T wq = tj * wsum(acc);
+      if (lane == 0) cq[j] -= wq;
+      for (int p = j + 1 + lane; p < rows; p += 32)
+        if (!use_fz || F.fz[p] <= j) cq[p] = fma(-cj[p], wq, cq[p]);
+    }
+    __syncthreads();
+  }
+  // T: zero the block, then column by column
+  for (int e = tid; e < b * b; e += kBT) Tg[e] = T(0);
+  __syncthreads();
+  for (int jj = 0; jj < kmax; ++jj) {
+    // z_q = v_q^T v_jj for q < jj (rows >= jj; v_jj(jj) = 1)
+    for (int q = warp; q < jj; q += kBW) {
+      const T *cq = tile + (size_t)q * ld;
+      const T *cjj = tile + (size_t)jj * ld;
+      T acc = (lane == 0) ? cq[jj] : T(0);
+      for (int p = jj + 1 + lane; p < rows; p += 32) acc = fma(cq[p], cjj[p], acc);
+      acc = wsum(acc);
+      if (lane == 0) F.z[q] = acc;
+    }
+    __syncthreads();
+    const T tj = F.tau[jj];
+    for (int i = tid; i < jj; i += kBT) {
+      T s = T(0);
+      if (tj != T(0))
+        for (int q = i; q < jj; ++q) s = fma(Tg[i + (size_t)q * b], F.z[q], s);
+      Tg[i + (size_t)jj * b] = -tj * s;
+    }
+    if (tid == 0) Tg[jj + (size_t)jj * b] = tj;
+    __syncthreads();
+  }
+  return kmax;
+}
+
+// Node rows of merge `o` (children start..start+cnt-1 with R rows at
+// top[], counts c[]): F.prow, F.fz; returns the row count, sets F.iscal[8] to
+// the first child's count.
+template <class T>
+__device__ int merge_rows(const int *top, const int *c, int start, int cnt, Fixed<T> &F) {
+  const int tid = threadIdx.x;
+  int rows = 0;
+  for (int ch = 0; ch < cnt; ++ch) rows += c[start + ch];
+  for (int p = tid; p < rows; p += kBT) {
+    int off = 0, ch = 0;
+    while (p >= off + c[start + ch]) off += c[start + ch++];
+    F.prow[p] = top[start + ch] + (p - off);
+    F.fz[p] = p - off;
+  }
+  if (tid == 0) F.iscal[8] = c[start];
+  __syncthreads();
+  return rows;
+}
+
+// C <- Q_node^T C for the node rows F.prow[0..rows) (leaf: Y unit lower
+// trapezoid stored in those rows; merge: identity on the first child's rows,
+// stored upper trapezoids on the others), nref reflectors, T block Tg.
+template <class T>
+__device__ void node_apply(const T *P, int lda, T *C, int nt, int rows, int nref, bool leaf, const T *Tg, int b,
+                           Fixed<T> &F, T *R) {
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  T *Ys = R;                     // kTl rows x nref, Ys[r * kTs + k]
+  T *CW = Ys + kTl * kTs;        // C chunk Cs[r * kTs + c], then W'[k * kTs + c]
+  T *Ts = CW + kTl * kTs;        // nref x nref, ld kTl
+  const int c0row = F.iscal[8];
+  for (int e = tid; e < kTl * kTl; e += kBT) {
+    const int i = e & (kTl - 1), k = e / kTl;
+    Ts[e] = (i < nref && k < nref) ? Tg[i + (size_t)k * b] : T(0);
+  }
+  auto yval = [&](int p, int k) -> T {
+    if (k >= nref) return T(0);
+    if (leaf) {
+      if (p == k) return T(1);
+      return p > k ? P[F.prow[p] + (size_t)k * lda] : T(0);
+    }
+    if (p < c0row) return p == k ? T(1) : T(0);
+    return k >= F.fz[p] ? P[F.prow[p] + (size_t)k * lda] : T(0);
+  };
+  for (int c0 = 0; c0 < nt; c0 += kTl) {
+    const int cols = min(kTl, nt - c0);
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    // W = Y^T C (thread: k = tx + 16 i, c = ty + 16 j)
+    for (int p0 = 0; p0 < rows; p0 += kTl) {
+      const int pr = min(kTl, rows - p0);
+      __syncthreads();
+      for (int e = tid; e < kTl * kTl; e += kBT) {
+        const int r = e & (kTl - 1), k = e / kTl;
+        Ys[r * kTs + k] = (r < pr) ? yval(p0 + r, k) : T(0);
+      }
+      for (int e = tid; e < kTl * kTl; e += kBT) {
+        const int r = e & (kTl - 1), c = e / kTl;
+        CW[r * kTs + c] = (r < pr && c < cols) ? C[F.prow[p0 + r] + (size_t)(c0 + c) * lda] : T(0);
+      }
+      __syncthreads();
+      for (int r = 0; r < pr; ++r) {
+        T y[4], cc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) y[i] = Ys[r * kTs + tx + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cc[j] = CW[r * kTs + ty + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(y[i], cc[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) CW[(tx + 16 * i) * kTs + ty + 16 * j] = acc[i][j];
+    __syncthreads();
+    // W' = T^T W
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = tx + 16 * i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        T s = T(0);
+        for (int q = 0; q <= k && q < nref; ++q) s = fma(Ts[q + k * kTl], CW[q * kTs + ty + 16 * j], s);
+        acc[i][j] = s;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) CW[(tx + 16 * i) * kTs + ty + 16 * j] = acc[i][j];
+    // C -= Y W' (thread: r = tx + 16 i, c = ty + 16 j)
+    for (int p0 = 0; p0 < rows; p0 += kTl) {
+      const int pr = min(kTl, rows - p0);
+      __syncthreads();
+      for (int e = tid; e < kTl * kTl; e += kBT) {
+        const int r = e & (kTl - 1), k = e / kTl;
+        Ys[r * kTs + k] = (r < pr) ? yval(p0 + r, k) : T(0);
+      }
+      __syncthreads();
+      T o[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[i][j] = T(0);
+      for (int k = 0; k < nref; ++k) {
+        T y[4], ww[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) y[i] = Ys[(tx + 16 * i) * kTs + k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ww[j] = CW[k * kTs + ty + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) o[i][j] = fma(y[i], ww[j], o[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = tx + 16 * i;
+        if (r >= pr) continue;
+        T *crow = C + F.prow[p0 + r];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = ty + 16 * j;
+          if (c < cols) crow[(size_t)(c0 + c) * lda] -= o[i][j];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CAQR of one matrix
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ void cta_caqr(const ca_batch_item_t &it, Fixed<T> &F, T *R, char *slot) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T *A = (T *)it.A;
+  T *qtree = (T *)it.qtree;
+  const int lda = it.lda, m = it.m, n = it.n, b = it.b, L = it.tree.leaf_rows;
+  const int nlmax = (m + L - 1) / L;
+  int *top[2] = {(int *)slot, (int *)slot + nlmax};
+  int *cc[2] = {(int *)slot + 2 * nlmax, (int *)slot + 3 * nlmax};
+  size_t off = 0;
+  for (int kb = 0; kb < n; kb += b) {
+    const int bk = min(b, n - kb), mk = m - kb;
+    T *P = A + kb + (size_t)kb * lda;
+    T *Tp = qtree + off;
+    const int nl = (mk + L - 1) / L;
+    if (tid == 0) build_plan(nl, it.tree, F.plan);
+    __syncthreads();
+    const int nrounds = F.plan.nrounds, nmerges = F.plan.nmerges;
+    // ---- TSQR: leaves ----
+    for (int j = 0; j < nl; ++j) {
+      const int r0 = j * L, rows = min(L, mk - r0), ld = odd_ld(rows);
+      for (int p = tid; p < rows; p += kBT) F.prow[p] = r0 + p;
+      __syncthreads();
+      load_rows(P, lda, rows, bk, R, ld, F, false);
+      const int km = node_qr(R, ld, rows, bk, F, false, Tp + (size_t)j * b * b, b);
+      for (int k = warp; k < bk; k += kBW)
+        for (int p = lane; p < rows; p += 32) P[r0 + p + (size_t)k * lda] = R[p + (size_t)k * ld];
+      if (tid == 0) {
+        top[0][j] = r0;
+        cc[0][j] = km;
+      }
+      __syncthreads();
+    }
+    // ---- TSQR: merge rounds ----
+    int buf = 0;
+    for (int r = 0; r < nrounds; ++r) {
+      const RoundDesc rd = F.plan.r[r];
+      for (int o = 0; o < rd.n_out; ++o) {
+        int start, cnt, midx;
+        round_node(rd, o, start, cnt, midx);
+        if (cnt == 1) {
+          if (tid == 0) {
+            top[buf ^ 1][o] = top[buf][start];
+            cc[buf ^ 1][o] = cc[buf][start];
+          }
+          __syncthreads();
+          continue;
+        }
+        const int rows = merge_rows(top[buf], cc[buf], start, cnt, F);
+        const int ld = odd_ld(rows);
+        load_rows(P, lda, rows, bk, R, ld, F, true);
+        const int km = node_qr(R, ld, rows, bk, F, true, Tp + (size_t)(nl + midx) * b * b, b);
+        for (int k = warp; k < bk; k += kBW)
+          for (int p = lane; p < rows; p += 32)
+            if (k >= F.fz[p]) P[F.prow[p] + (size_t)k * lda] = R[p + (size_t)k * ld];
+        if (tid == 0) {
+          top[buf ^ 1][o] = top[buf][start];
+          cc[buf ^ 1][o] = km;
+        }
+        __syncthreads();
+      }
+      buf ^= 1;
+    }
+    // ---- tree update of the trailing columns ----
+    const int nt = n - kb - bk;
+    if (nt > 0) {
+      T *C = P + (size_t)bk * lda;
+      for (int j = 0; j < nl; ++j) {
+        const int r0 = j * L, rows = min(L, mk - r0);
+        for (int p = tid; p < rows; p += kBT) F.prow[p] = r0 + p;
+        __syncthreads();
+        node_apply(P, lda, C, nt, rows, min(rows, bk), true, Tp + (size_t)j * b * b, b, F, R);
+        if (tid == 0) {
+          top[0][j] = r0;
+          cc[0][j] = min(rows, bk);
+        }
+        __syncthreads();
+      }
+      buf = 0;
+      for (int r = 0; r < nrounds; ++r) {
+        const RoundDesc rd = F.plan.r[r];
+        for (int o = 0; o < rd.n_out; ++o) {
+          int start, cnt, midx;
+          round_node(rd, o, start, cnt, midx);
+          if (cnt == 1) {
+            if (tid == 0) {
+              top[buf ^ 1][o] = top[buf][start];
+              cc[buf ^ 1][o] = cc[buf][start];
+            }
+            __syncthreads();
+            continue;
+          }
+          const int rows = merge_rows(top[buf], cc[buf], start, cnt, F);
+          const int km = min(rows, bk);
+          node_apply(P, lda, C, nt, rows, km, false, Tp + (size_t)(nl + midx) * b * b, b, F, R);
+          if (tid == 0) {
+            top[buf ^ 1][o] = top[buf][start];
+            cc[buf ^ 1][o] = km;
+          }
+          __syncthreads();
+        }
+        buf ^= 1;
+      }
+    }
+    off += (size_t)(nl + nmerges) * b * b;
+  }
+}
+
+struct BatchArgs {
+  const ca_batch_item_t *items;
+  int count;
+  int region_elems;
+  char *slots;
+  size_t slot_bytes;
+  int *counter;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kBT, 1) batched_kernel(BatchArgs a) {
+  extern __shared__ __align__(16) char smem_raw[];
+  Fixed<T> &F = *reinterpret_cast<Fixed<T> *>(smem_raw);
+  T *R = reinterpret_cast<T *>(smem_raw + ((sizeof(Fixed<T>) + 15) & ~size_t(15)));
+  char *slot = a.slots + (size_t)blockIdx.x * a.slot_bytes;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      F.item = atomicAdd(a.counter, 1);
+      F.info0 = 0;
+      F.status = 0;
+    }
+    __syncthreads();
+    const int idx = F.item;
+    if (idx >= a.count) return;
+    const ca_batch_item_t it = a.items[idx];
+    if (it.op == CA_BATCH_CALU)
+      cta_calu<T>(it, F, R, a.region_elems, slot);
+    else
+      cta_caqr<T>(it, F, R, slot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      it.info[0] = F.info0;
+      it.info[1] = F.status;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+int tree_ok(const ca_tree_t &t, int b) {
+  if (t.nlevels < 1 || t.nlevels > CA_MAX_LEVELS) return 0;
+  if (t.leaf_rows < b || t.leaf_rows < 1) return 0;
+  for (int l = 0; l < t.nlevels; ++l) {
+    if (t.style[l] != CA_TREE_BINARY && t.style[l] != CA_TREE_FLAT) return 0;
+    if (l < t.nlevels - 1 && t.fan_in[l] < 1) return 0;
+  }
+  return 1;
+}
+
+double item_flops(const ca_batch_item_t &it) {
+  const double m = it.m, n = it.n;
+  const double k = m < n ? m : n;
+  if (it.op == CA_BATCH_CALU) {
+    // m n k - (m + n) k^2 / 2 + k^3 / 3 multiply-adds, x 2 (LAPACK getrf count)
+    return m * n * k - (m + n) * k * k / 2.0 + k * k * k / 3.0;
+  }
+  return 2.0 * m * n * n - 2.0 * n * n * n / 3.0;
+}
+
+// Largest phase-region need (elements) of one item, and its slot bytes;
+// returns 0 if the item cannot run here.
+int item_needs(const ca_batch_item_t &it, size_t esz, size_t region_cap, size_t *elems, size_t *slot) {
+  const int K = it.m < it.n ? it.m : it.n;
+  const int b = it.b;
+  const int bk = b < K ? b : K;
+  const int L = it.tree.leaf_rows;
+  const int nlmax = (it.m + L - 1) / L;
+  size_t need = 0;
+  // node tiles of the first panel (the largest); later panels have fewer rows
+  Plan p;
+  if (!build_plan(nlmax, it.tree, p)) return 0;
+  int rows = L < it.m ? L : it.m;
+  for (int r = 0; r < p.nrounds; ++r) rows = std::max(rows, p.r[r].max_cnt * bk);
+  if (rows > kBMaxRows) return 0;
+  need = std::max(need, (size_t)odd_ld(rows) * bk);
+  const bool multi = it.n > bk;  // a trailing update follows the first panel
+  if (multi && bk > kBMultiB) return 0;
+  if (it.op == CA_BATCH_CALU) {
+    need = std::max(need, (size_t)bk * bk + bk + 33 * (size_t)bk);  // L21 with 32-row tiles at least
+    if (multi) {
+      need = std::max(need, (size_t)bk * bk + 32 * (size_t)bk);
+      need = std::max(need, (size_t)2 * kGk * kTl);
+    }
+    *slot = align256((size_t)4 * (2 * (size_t)nlmax * b + 2 * nlmax) + 16) + (size_t)b * b * esz;
+  } else {
+    if (multi) need = std::max(need, (size_t)2 * kTl * kTs + (size_t)kTl * kTl);
+    *slot = (size_t)4 * 4 * nlmax;
+  }
+  if (need * esz > region_cap) return 0;
+  *elems = need;
+  return 1;
+}
+
+}  // namespace
+}  // namespace cagb
+
+using namespace cagb;
+
+extern "C" {
+
+int ca_batched_plan(int count, const ca_batch_item_t *items, int dtype, void *plan, size_t *plan_bytes,
+                    size_t *work_bytes) {
+  if (count < 0) return -1;
+  if (count > 0 && !items) return -2;
+  if (dtype != CA_DTYPE_F64 && dtype != CA_DTYPE_F32) return -3;
+  if (!plan_bytes) return -5;
+  if (!work_bytes) return -6;
+  const size_t esz = dtype == CA_DTYPE_F64 ? 8 : 4;
+  const size_t pb = kHeaderBytes + (size_t)count * sizeof(ca_batch_item_t);
+  const size_t fixed = fixed_bytes(dtype);
+  const size_t cap = 227 * 1024 - fixed - 1024;
+  size_t region = 0, slot = 256;
+  double flops = 0.0;
+  for (int i = 0; i < count; ++i) {
+    const ca_batch_item_t &it = items[i];
+    if (it.op != CA_BATCH_CALU && it.op != CA_BATCH_CAQR) return CA_ERR_BATCH_ITEM;
+    if (it.m < 0 || it.n < 0 || it.lda < (it.m > 1 ? it.m : 1) || it.b < 1 || it.b > kBMaxB)
+      return CA_ERR_BATCH_ITEM;
+    if (it.op == CA_BATCH_CAQR && it.n > it.m) return CA_ERR_BATCH_ITEM;
+    if (!tree_ok(it.tree, it.b < (it.m < it.n ? it.m : it.n) ? it.b : (it.m < it.n ? it.m : it.n)))
+      return CA_ERR_BATCH_ITEM;
+    if (!it.info) return CA_ERR_BATCH_ITEM;
+    const int K = it.m < it.n ? it.m : it.n;
+    if (K == 0) continue;
+    if (!it.A) return CA_ERR_BATCH_ITEM;
+    if (it.op == CA_BATCH_CALU && !it.ipiv) return CA_ERR_BATCH_ITEM;
+    if (it.op == CA_BATCH_CAQR && !it.qtree) return CA_ERR_BATCH_ITEM;
+    size_t e = 0, s = 0;
+    if (!item_needs(it, esz, cap, &e, &s)) return CA_ERR_UNSUPPORTED;
+    region = std::max(region, e * esz);
+    slot = std::max(slot, align256(s));
+    flops += item_flops(it);
+  }
+  // room for full 256-row / 256-column solve tiles when it fits
+  region = std::max(region, std::min(cap, (size_t)(kBMultiB * kBMultiB + kBMultiB + (kBT + 1) * kBMultiB) * esz));
+  region = (region + 15) & ~size_t(15);
+  // one CTA per SM of the current device (sized for 152 SMs when no device
+  // is visible: the plan is host data and may be made without a GPU)
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    (void)cudaGetLastError();
+    sms = 152;
+  }
+  const int ctas = count < sms ? (count > 0 ? count : 1) : sms;
+  *plan_bytes = pb;
+  *work_bytes = 256 + (size_t)ctas * slot;
+  if (!plan) return CA_OK;
+  BatchHeader h = {};
+  h.magic = kPlanMagic;
+  h.count = count;
+  h.dtype = dtype;
+  h.ctas = ctas;
+  h.smem_region = (int)region;
+  h.slot_bytes = slot;
+  h.work_bytes = *work_bytes;
+  h.flops = flops;
+  std::memset(plan, 0, kHeaderBytes);
+  std::memcpy(plan, &h, sizeof(h));
+  // LPT order: largest flop count first (ties by input position)
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return item_flops(items[x]) > item_flops(items[y]); });
+  ca_batch_item_t *dst = (ca_batch_item_t *)((char *)plan + kHeaderBytes);
+  for (int i = 0; i < count; ++i) dst[i] = items[order[i]];
+  return CA_OK;
+}
+
+int ca_batched_factor(const void *plan_host, const void *plan_dev, void *work, size_t lwork, cudaStream_t stream) {
+  if (!plan_host) return -1;
+  BatchHeader h;
+  std::memcpy(&h, plan_host, sizeof(h));
+  if (h.magic != kPlanMagic) return -1;
+  if (!plan_dev) return -2;
+  if (h.count == 0) return CA_OK;
+  if (!work || lwork < h.work_bytes) return CA_ERR_WORKSPACE;
+  const size_t smem = fixed_bytes(h.dtype) + (size_t)h.smem_region;
+  BatchArgs a;
+  a.items = (const ca_batch_item_t *)((const char *)plan_dev + kHeaderBytes);
+  a.count = h.count;
+  a.region_elems = (int)(h.smem_region / (h.dtype == CA_DTYPE_F64 ? 8 : 4));
+  a.counter = (int *)work;
+  a.slots = (char *)work + 256;
+  a.slot_bytes = h.slot_bytes;
+  if (cudaMemsetAsync(work, 0, 4, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  cudaError_t e;
+  {
+    ProfScope ps(kClsBatched, stream, h.flops);
+    if (h.dtype == CA_DTYPE_F64) {
+      e = cudaFuncSetAttribute(batched_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) batched_kernel<double><<<h.ctas, kBT, smem, stream>>>(a);
+    } else {
+      e = cudaFuncSetAttribute(batched_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) batched_kernel<float><<<h.ctas, kBT, smem, stream>>>(a);
+    }
+  }
+  if (e != cudaSuccess) return CA_ERR_LAUNCH;
+  return cudaGetLastError() == cudaSuccess ? CA_OK : CA_ERR_LAUNCH;
+}
+
+}  // extern "C"

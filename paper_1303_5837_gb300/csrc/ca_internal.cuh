@@ -52,7 +52,72 @@ __host__ __device__ inline void round_node(const RoundDesc &rd, int o, int &star
 }
 
 // Builds the plan for `nleaves` leaves; returns false for a malformed tree.
-bool build_plan(int nleaves, const ca_tree_t &t, Plan &p);
+// Per level, groups of fan_in consecutive nodes; binary style pairs
+// neighbours until one node is left in each group, flat style merges a group
+// at once; the last level takes every remaining node.
+__host__ __device__ inline bool build_plan(int nleaves, const ca_tree_t &t, Plan &p) {
+  p.nleaves = nleaves;
+  p.nrounds = 0;
+  p.nmerges = 0;
+  if (nleaves < 1 || t.nlevels < 1 || t.nlevels > CA_MAX_LEVELS) return false;
+  int cur = nleaves;
+  for (int l = 0; l < t.nlevels; ++l) {
+    int f = (l == t.nlevels - 1) ? cur : t.fan_in[l];
+    if (f < 1) return false;
+    int ngroups = (cur + f - 1) / f;
+    int s = (ngroups == 1) ? cur : f;
+    int s_last = cur - (ngroups - 1) * f;
+    if (t.style[l] == CA_TREE_FLAT) {
+      RoundDesc rd;
+      rd.n_in = cur;
+      rd.n_out = ngroups;
+      rd.ngroups = ngroups;
+      rd.s = s;
+      rd.s_last = s_last;
+      rd.w = s;
+      rd.h = 1;
+      rd.h_last = 1;
+      rd.mfull = s >= 2 ? 1 : 0;
+      rd.merge_base = p.nmerges;
+      rd.max_cnt = s > s_last ? s : s_last;
+      int merges = (ngroups - 1) * rd.mfull + (s_last >= 2 ? 1 : 0);
+      if (merges > 0) {
+        if (p.nrounds >= kMaxRounds) return false;
+        p.r[p.nrounds++] = rd;
+        p.nmerges += merges;
+      }
+    } else if (t.style[l] == CA_TREE_BINARY) {
+      int in = cur;
+      while (s > 1 || s_last > 1) {
+        RoundDesc rd;
+        rd.n_in = in;
+        rd.ngroups = ngroups;
+        rd.s = s;
+        rd.s_last = s_last;
+        rd.w = 2;
+        rd.h = (s + 1) / 2;
+        rd.h_last = (s_last + 1) / 2;
+        rd.n_out = (ngroups - 1) * rd.h + rd.h_last;
+        rd.mfull = s / 2;
+        rd.merge_base = p.nmerges;
+        rd.max_cnt = 2;
+        int merges = (ngroups - 1) * rd.mfull + s_last / 2;
+        if (merges > 0) {
+          if (p.nrounds >= kMaxRounds) return false;
+          p.r[p.nrounds++] = rd;
+          p.nmerges += merges;
+        }
+        in = rd.n_out;
+        s = rd.h;
+        s_last = rd.h_last;
+      }
+    } else {
+      return false;
+    }
+    cur = ngroups;
+  }
+  return cur == 1;
+}
 
 // ---------------------------------------------------------------------------
 // Argmax helpers: |x| compared through the bit pattern (an integer compare,
@@ -109,6 +174,7 @@ enum KernelClass {
   kClsSplit,
   kClsGemmTc,
   kClsRefine,
+  kClsBatched,
   kNumClasses
 };
 

@@ -75,3 +75,38 @@ def test_workspace_matches_tree_counts(lib):
                              (4096, 128, 64, 256, [(4, 0), (4, 0), (0, 1)])]:
         qb, _ = B.ca_caqr_workspace(m, n, b, B.make_tree(L, lv))
         assert qb == 8 * oracle.caqr_tcount(m, n, b, oracle.make_tree(L, lv))
+
+
+def test_batched_plan_checks_without_gpu(lib):
+    """The batched plan is host data: validation, sizes and the LPT order
+    need no GPU; a launch with a foreign buffer is refused before any work."""
+    from paper_1303_5837_gb300 import _binding as B
+    pb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+
+    def item(op=0, m=100, n=100, b=32, L=64, levels=((0, 0),)):
+        it = B.ca_batch_item_t()
+        it.op, it.m, it.n, it.lda, it.b = op, m, n, max(m, 1), b
+        it.A, it.ipiv, it.qtree, it.info = 256, 256, 256, 256
+        it.tree = B.make_tree(L, levels)
+        return it
+
+    def plan(items, dtype=B.CA_DTYPE_F64):
+        arr = (B.ca_batch_item_t * max(1, len(items)))(*items)
+        return lib.ca_batched_plan(len(items), arr, dtype, None, ctypes.byref(pb), ctypes.byref(wb))
+
+    assert lib.ca_batched_plan(-1, None, 0, None, ctypes.byref(pb), ctypes.byref(wb)) == -1
+    assert lib.ca_batched_plan(1, None, 0, None, ctypes.byref(pb), ctypes.byref(wb)) == -2
+    assert plan([item()], dtype=7) == -3
+    assert plan([item(op=5)]) == B.CA_ERR_BATCH_ITEM
+    assert plan([item(op=1, m=10, n=20)]) == B.CA_ERR_BATCH_ITEM         # QR needs m >= n
+    assert plan([item(L=16)]) == B.CA_ERR_BATCH_ITEM                      # leaf_rows < b
+    assert plan([item(b=96, L=128)]) == B.CA_ERR_UNSUPPORTED              # > 64 with an update
+    # FP64 binary merge of two 128-wide candidate sets (257 x 128) exceeds shared memory ...
+    assert plan([item(op=1, m=4096, n=128, b=128, L=128)]) == B.CA_ERR_UNSUPPORTED
+    # ... FP32 holds it
+    assert plan([item(op=1, m=4096, n=128, b=128, L=128)], dtype=B.CA_DTYPE_F32) == 0
+    assert plan([item(), item(op=1, m=3000, n=64, b=64, L=256)]) == 0
+    assert pb.value == 256 + 2 * ctypes.sizeof(B.ca_batch_item_t)
+    assert wb.value > 256
+    bogus = ctypes.create_string_buffer(256)
+    assert lib.ca_batched_factor(bogus, None, None, 0, None) == -1
