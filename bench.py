@@ -60,6 +60,11 @@ def parse():
     p.add_argument("--serve-duration", type=float, default=3.0)
     p.add_argument("--serve-nmax", type=int, default=2048)
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--batch-count", type=int, default=4096, help="matrices of the batched workload")
+    p.add_argument("--batch-steps", type=int, default=3)
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--only-batch", default="", choices=["", "f64", "f32"],
+                   help="diagnostic: run only the batched workload in this precision")
     return p.parse_args()
 
 
@@ -224,6 +229,12 @@ def run_ours(a, rank: int, world: int, local: int):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     ca.load()
+    if a.only_batch:
+        out = batched_run(a, ca, torch, torch.float64 if a.only_batch == "f64" else torch.float32, dev, rank,
+                          world)
+        if rank == 0:
+            print(json.dumps({"batched": {a.only_batch: out}}), flush=True)
+        return
     n, b, nrhs = a.n, a.b, a.nrhs
     tree = ca.make_tree(a.leaf, TREE_LEVELS)
 
@@ -312,6 +323,13 @@ def run_ours(a, rank: int, world: int, local: int):
     if not a.no_serve and world == 1:
         serving = serving_run(a)
 
+    # ---- batched: many uneven matrices in one persistent graph-captured launch
+    batched = None
+    if not a.no_batch:
+        batched = {}
+        for tname, tdt in (("f64", torch.float64), ("f32", torch.float32)):
+            batched[tname] = batched_run(a, ca, torch, tdt, dev, rank, world)
+
     # ---- end to end through the public API with host buffers --------------
     e2e = None
     if a.e2e_steps > 0:
@@ -370,6 +388,7 @@ def run_ours(a, rank: int, world: int, local: int):
         "check": {"x_rel_err_calu": err_lu, "x_rel_err_caqr": err_qr},
         "lu_forms": lu_forms,
         "serving": serving,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
 
@@ -491,6 +510,67 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
                                        "update on the tensor cores"}
     for k, v in kernels_of.items():
         out[k]["kernels"] = v
+    return out
+
+
+BATCH_TABLES = {"f64": os.path.join(ROOT, "paper_1303_5837_gb300", "tuned_batch_f64.json"),
+                "f32": os.path.join(ROOT, "paper_1303_5837_gb300", "tuned_batch_f32.json")}
+
+
+def batched_run(a, ca, torch, dtype, dev, rank, world):
+    """The batched workload: a.batch_count matrices (half square with n in
+    [32, 512], half tall with m in [256, 8192] and n in {16, 32, 64, 128}),
+    each factored by CALU and by CAQR, all in one persistent launch replayed
+    from a CUDA graph; tile and tree shapes from the tuned table.  Inputs are
+    seeded N(0, 1) drawn on the device (11 GB in FP64, larger than L2) and
+    restored from a pristine copy before every (untimed) replay."""
+    from paper_1303_5837_gb300 import tune
+    tname = "f64" if dtype == torch.float64 else "f32"
+    esz = 8 if dtype == torch.float64 else 4
+    table = tune.load_table(BATCH_TABLES[tname])
+    shapes, ops, bs, trees = tune.batch_items(2026 + rank, a.batch_count, table, esz)
+    offs, tot = [], 0
+    for m, n in shapes:
+        offs.append(tot)
+        tot += (m * n + 31) // 32 * 32          # 256-byte aligned starts
+    flat = torch.empty(tot, dtype=dtype, device=dev)
+    flat.normal_(generator=torch.Generator(device=dev).manual_seed(99 + rank))
+    for i in range(1, len(shapes), 2):          # the CAQR item factors the CALU item's matrix
+        m, n = shapes[i]
+        flat[offs[i]: offs[i] + m * n].copy_(flat[offs[i - 1]: offs[i - 1] + m * n])
+    pristine = flat.clone()
+    views = [flat[o: o + m * n].view(n, m).t() for o, (m, n) in zip(offs, shapes)]
+    bf = ca.BatchedFactor(views, ops, bs, [ca.make_tree(L, lv) for L, lv in trees])
+    graph = bf.graph()
+    flops = sum(tune.item_flops(op, m, n) for op, (m, n) in zip(ops, shapes))
+    st = torch.cuda.current_stream()
+    for _ in range(2):
+        flat.copy_(pristine)
+        graph.replay()
+    torch.cuda.synchronize()
+    bad = int((bf.info_all != 0).sum())
+    barrier(world)
+    times = []
+    for _ in range(a.batch_steps):
+        flat.copy_(pristine)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        graph.replay()
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = allreduce_max(statistics.median(times), world)
+    gflops = world * flops / (ms / 1e3) / 1e9
+    out = {"matrices": a.batch_count, "items": len(shapes), "ms": ms, "gflops": gflops,
+           "gflop_per_step": flops / 1e9, "launches_per_step": 1, "graph": True,
+           "tuned": table is not None, "nonzero_info": bad, "bytes": tot * esz,
+           "form": "ca_batched_factor: one CTA per matrix, LPT work queue, CALU + CAQR of every matrix"}
+    if dtype == torch.float64:
+        out["roofline"] = {"bound": "alu", "achieved": gflops / world, "peak": FP64_PEAK_GFLOPS,
+                           "unit": "GFLOP/s", "frac": gflops / world / FP64_PEAK_GFLOPS}
+    del views, bf, graph, flat, pristine
+    torch.cuda.empty_cache()
     return out
 
 

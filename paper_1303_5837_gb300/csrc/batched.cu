@@ -91,6 +91,27 @@ __host__ __device__ inline size_t fixed_bytes(int dtype) {
 
 __host__ __device__ inline int odd_ld(int rows) { return rows | 1; }
 
+// Element-wise copy of `total` elements, ld(e) -> st(e, v): each thread
+// issues the loads of kU elements before any of their stores, so that the
+// latencies of the global loads overlap.
+constexpr int kU = 8;
+template <class T, class Ld, class St>
+__device__ __forceinline__ void stage(int total, Ld ld, St st) {
+  for (int base = threadIdx.x; base < total; base += kBT * kU) {
+    T v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = base + u * kBT;
+      v[u] = (e < total) ? ld(e) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = base + u * kBT;
+      if (e < total) st(e, v[u]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // GEPP on the node tile (rows x bk, ld), rows permuted physically with their
 // labels in F.prow; first maximum of |a| in the current order.  Returns the
@@ -113,6 +134,7 @@ __device__ int node_gepp(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool ro
       F.iscal[0] = bb.pos;
       F.iscal[1] = (bb.key == 0ull);
       if (bb.key == 0ull && root && F.info0 == 0) F.info0 = kb + j + 1;
+      if (bb.key != 0ull) F.scal[0] = T(1) / cj[bb.pos];
     }
     __syncthreads();
     if (F.iscal[1]) continue;  // zero column: no swap, no update
@@ -130,7 +152,7 @@ __device__ int node_gepp(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool ro
       }
       __syncthreads();
     }
-    const T rinv = T(1) / tile[j + (size_t)j * ld];
+    const T rinv = F.scal[0];
     T *cjw = tile + (size_t)j * ld;
     for (int q = j + 1 + tid; q < rows; q += kBT) cjw[q] *= rinv;
     __syncthreads();
@@ -148,17 +170,18 @@ __device__ int node_gepp(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool ro
 // merge rows skip (zero) the entries left of F.fz (use_fz).
 template <class T>
 __device__ void load_rows(const T *P, int lda, int rows, int bk, T *tile, int ld, Fixed<T> &F, bool use_fz) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   bool bad = false;
-  for (int k = warp; k < bk; k += kBW) {
-    const T *col = P + (size_t)k * lda;
-    for (int p = lane; p < rows; p += 32) {
-      T v = T(0);
-      if (!use_fz || k >= F.fz[p]) v = col[F.prow[p]];
-      bad |= Num<T>::bad(v);
-      tile[p + (size_t)k * ld] = v;
-    }
-  }
+  stage<T>(
+      rows * bk,
+      [&](int e) -> T {
+        const int k = e / rows, p = e - k * rows;
+        return (!use_fz || k >= F.fz[p]) ? P[F.prow[p] + (size_t)k * lda] : T(0);
+      },
+      [&](int e, T v) {
+        const int k = e / rows, p = e - k * rows;
+        bad |= Num<T>::bad(v);
+        tile[p + (size_t)k * ld] = v;
+      });
   if (bad) atomicOr(&F.status, CA_STATUS_NONFINITE);
   __syncthreads();
 }
@@ -326,8 +349,16 @@ __device__ void cta_calu(const ca_batch_item_t &it, Fixed<T> &F, T *R, int regio
       __syncthreads();
       for (int r0 = bk; r0 < mk; r0 += rt) {
         const int rows = min(rt, mk - r0);
-        for (int k = warp; k < bk; k += kBW)
-          for (int p = lane; p < rows; p += 32) Tt[p + (size_t)k * ldt] = P[r0 + p + (size_t)k * lda];
+        stage<T>(
+            rows * bk,
+            [&](int e) -> T {
+              const int k = e / rows, p = e - k * rows;
+              return P[r0 + p + (size_t)k * lda];
+            },
+            [&](int e, T v) {
+              const int k = e / rows, p = e - k * rows;
+              Tt[p + (size_t)k * ldt] = v;
+            });
         __syncthreads();
         if (tid < rows) {
           T *x = Tt + tid;
@@ -357,8 +388,16 @@ __device__ void cta_calu(const ca_batch_item_t &it, Fixed<T> &F, T *R, int regio
       __syncthreads();
       for (int c0 = 0; c0 < nt; c0 += ct) {
         const int cols = min(ct, nt - c0);
-        for (int c = warp; c < cols; c += kBW)
-          for (int p = lane; p < bk; p += 32) Ts[(size_t)p * ct + c] = A12[p + (size_t)(c0 + c) * lda];
+        stage<T>(
+            cols * bk,
+            [&](int e) -> T {
+              const int c = e / bk, p = e - c * bk;
+              return A12[p + (size_t)(c0 + c) * lda];
+            },
+            [&](int e, T v) {
+              const int c = e / bk, p = e - c * bk;
+              Ts[(size_t)p * ct + c] = v;
+            });
         __syncthreads();
         if (tid < cols) {
           T *x = Ts + tid;
@@ -391,14 +430,25 @@ __device__ void cta_calu(const ca_batch_item_t &it, Fixed<T> &F, T *R, int regio
             for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
           for (int k0 = 0; k0 < bk; k0 += kGk) {
             const int kc = min(kGk, bk - k0);
-            for (int e = tid; e < kGk * kTl; e += kBT) {
-              const int r = e & (kTl - 1), k = e / kTl;
-              As[e] = (k < kc && r0 + r < mr) ? L21[r0 + r + (size_t)(k0 + k) * lda] : T(0);
-            }
-            for (int e = tid; e < kGk * kTl; e += kBT) {
-              const int k = e % kGk, c = e / kGk;
-              Bs[k * kTl + c] = (k < kc && c0 + c < nt) ? A12[k0 + k + (size_t)(c0 + c) * lda] : T(0);
-            }
+            stage<T>(
+                2 * kGk * kTl,
+                [&](int e) -> T {
+                  if (e < kGk * kTl) {
+                    const int r = e & (kTl - 1), k = e / kTl;
+                    return (k < kc && r0 + r < mr) ? L21[r0 + r + (size_t)(k0 + k) * lda] : T(0);
+                  }
+                  e -= kGk * kTl;
+                  const int k = e % kGk, c = e / kGk;
+                  return (k < kc && c0 + c < nt) ? A12[k0 + k + (size_t)(c0 + c) * lda] : T(0);
+                },
+                [&](int e, T v) {
+                  if (e < kGk * kTl) {
+                    As[e] = v;
+                  } else {
+                    e -= kGk * kTl;
+                    Bs[(e % kGk) * kTl + e / kGk] = v;
+                  }
+                });
             __syncthreads();
             for (int k = 0; k < kc; ++k) {
               T a[4], bb[4];
@@ -544,14 +594,14 @@ __device__ void node_apply(const T *P, int lda, T *C, int nt, int rows, int nref
     const int i = e & (kTl - 1), k = e / kTl;
     Ts[e] = (i < nref && k < nref) ? Tg[i + (size_t)k * b] : T(0);
   }
+  // Y(p, k): leaf rows hold the unit lower trapezoid; merge rows: identity
+  // on the first child, stored upper trapezoids (k >= child-local row) on
+  // the others
   auto yval = [&](int p, int k) -> T {
-    if (k >= nref) return T(0);
-    if (leaf) {
-      if (p == k) return T(1);
-      return p > k ? P[F.prow[p] + (size_t)k * lda] : T(0);
-    }
-    if (p < c0row) return p == k ? T(1) : T(0);
-    return k >= F.fz[p] ? P[F.prow[p] + (size_t)k * lda] : T(0);
+    const bool stored = k < nref && (leaf ? p > k : (p >= c0row && k >= F.fz[p]));
+    T v = stored ? P[F.prow[p] + (size_t)k * lda] : T(0);
+    if (p == k && (leaf || p < c0row)) v = T(1);
+    return v;
   };
   for (int c0 = 0; c0 < nt; c0 += kTl) {
     const int cols = min(kTl, nt - c0);
@@ -564,14 +614,20 @@ __device__ void node_apply(const T *P, int lda, T *C, int nt, int rows, int nref
     for (int p0 = 0; p0 < rows; p0 += kTl) {
       const int pr = min(kTl, rows - p0);
       __syncthreads();
-      for (int e = tid; e < kTl * kTl; e += kBT) {
-        const int r = e & (kTl - 1), k = e / kTl;
-        Ys[r * kTs + k] = (r < pr) ? yval(p0 + r, k) : T(0);
-      }
-      for (int e = tid; e < kTl * kTl; e += kBT) {
-        const int r = e & (kTl - 1), c = e / kTl;
-        CW[r * kTs + c] = (r < pr && c < cols) ? C[F.prow[p0 + r] + (size_t)(c0 + c) * lda] : T(0);
-      }
+      stage<T>(
+          2 * kTl * kTl,
+          [&](int e) -> T {
+            const int h = e >> 12, f = e & (kTl * kTl - 1);
+            const int r = f & (kTl - 1), q = f >> 6;
+            if (r >= pr) return T(0);
+            if (h == 0) return yval(p0 + r, q);
+            return q < cols ? C[F.prow[p0 + r] + (size_t)(c0 + q) * lda] : T(0);
+          },
+          [&](int e, T v) {
+            const int h = e >> 12, f = e & (kTl * kTl - 1);
+            const int r = f & (kTl - 1), q = f >> 6;
+            (h == 0 ? Ys : CW)[r * kTs + q] = v;
+          });
       __syncthreads();
       for (int r = 0; r < pr; ++r) {
         T y[4], cc[4];
@@ -611,10 +667,9 @@ __device__ void node_apply(const T *P, int lda, T *C, int nt, int rows, int nref
     for (int p0 = 0; p0 < rows; p0 += kTl) {
       const int pr = min(kTl, rows - p0);
       __syncthreads();
-      for (int e = tid; e < kTl * kTl; e += kBT) {
-        const int r = e & (kTl - 1), k = e / kTl;
-        Ys[r * kTs + k] = (r < pr) ? yval(p0 + r, k) : T(0);
-      }
+      stage<T>(
+          kTl * kTl, [&](int e) -> T { return (e & (kTl - 1)) < pr ? yval(p0 + (e & (kTl - 1)), e >> 6) : T(0); },
+          [&](int e, T v) { Ys[(e & (kTl - 1)) * kTs + (e >> 6)] = v; });
       __syncthreads();
       T o[4][4];
 #pragma unroll

@@ -51,24 +51,59 @@ def batch_matrices(shapes, seed: int):
     return [inputs.gaussian(m, n, seed * 100003 + i) for i, (m, n) in enumerate(shapes)]
 
 
-def batch_workload(seed: int, count: int, table=None, esz: int = 8):
-    """The batch: `count` matrices from ``batch_shapes``, each factored by
-    CALU and by CAQR (2 * count items).  Returns (host matrices, ops, panel
-    widths, trees as (leaf_rows, levels)); shapes from ``table`` (class ->
-    (b, leaf_rows, tree name)) or the untuned defaults."""
-    shapes = batch_shapes(seed, count)
-    base = batch_matrices(shapes, seed)
-    mats, ops, bs, trees = [], [], [], []
-    for A in base:
-        m, n = A.shape
+def batch_items(seed: int, count: int, table=None, esz: int = 8):
+    """Items of the batch: `count` matrices from ``batch_shapes``, each
+    factored by CALU and by CAQR (2 * count items).  Returns (shapes, ops,
+    panel widths, trees as (leaf_rows, levels)); shapes from ``table``
+    (class -> (b, leaf_rows, tree name)) or the untuned defaults."""
+    shapes, ops, bs, trees = [], [], [], []
+    for m, n in batch_shapes(seed, count):
         for op in ("lu", "qr"):
             cfg = (table or {}).get(class_of(op, m, n)) or default_config(op, m, n, esz)
             b, L, name = cfg
-            mats.append(A.copy(order="F"))
+            shapes.append((m, n))
             ops.append(op)
             bs.append(int(b))
             trees.append((int(L), TREES[name]))
+    return shapes, ops, bs, trees
+
+
+def batch_workload(seed: int, count: int, table=None, esz: int = 8):
+    """``batch_items`` with host matrices (seeded iid N(0, 1); the CALU and
+    the CAQR item of a matrix get the same values)."""
+    shapes, ops, bs, trees = batch_items(seed, count, table, esz)
+    base = batch_matrices(shapes[::2], seed)
+    mats = [base[i // 2].copy(order="F") for i in range(len(shapes))]
     return mats, ops, bs, trees
+
+
+def item_flops(op: str, m: int, n: int) -> float:
+    """Standard flop counts: LU m n^2 - n^3 / 3 (m >= n), QR 2 m n^2 - 2 n^3 / 3."""
+    if op == "lu":
+        k = min(m, n)
+        return m * n * k - (m + n) * k * k / 2.0 + k ** 3 / 3.0
+    return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+
+
+def load_table(path: str):
+    """Tuned table from JSON ({"op,n,ratio": [b, leaf_rows, tree]})."""
+    import json
+    import os
+    if not os.path.exists(path):
+        return None
+    raw = json.load(open(path))
+    out = {}
+    for k, v in raw.get("table", {}).items():
+        op, nb, ratio = k.split(",")
+        out[(op, int(nb), int(ratio))] = (int(v[0]), int(v[1]), str(v[2]))
+    return out
+
+
+def save_table(path: str, table: dict, meta: dict):
+    import json
+    raw = {"meta": meta, "table": {f"{k[0]},{k[1]},{k[2]}": list(v) for k, v in sorted(table.items())}}
+    with open(path, "w") as f:
+        json.dump(raw, f, indent=1, sort_keys=True)
 
 
 def _node_fits(m: int, n: int, b: int, L: int, levels, esz: int) -> bool:
@@ -152,8 +187,8 @@ class Tuner:
             op = cls[0]
             idx = g.choice(len(members), min(self.sample, len(members)), replace=False)
             samp = [members[i] for i in idx]
-            mats = [torch.from_numpy(np.ascontiguousarray(A.T)).to("cuda", self.dtype).t()
-                    for A in batch_matrices(samp, seed + 7)]
+            gen = torch.Generator(device="cuda").manual_seed(seed + 7)
+            mats = [torch.randn(n, m, dtype=self.dtype, device="cuda", generator=gen).t() for m, n in samp]
             pristine = [A.clone() for A in mats]
             # candidates valid for every sampled shape
             common = None
@@ -186,3 +221,34 @@ class Tuner:
                 self.table[cls] = best
                 self.trials[cls] = results
         return self.table
+
+
+def main(argv=None):
+    """Tune the batch of ``batch_items`` on the current GPU and write the
+    table (python -m paper_1303_5837_gb300.tune --dtype f64 --out FILE)."""
+    import argparse
+    import time
+
+    import torch
+    p = argparse.ArgumentParser()
+    p.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    p.add_argument("--count", type=int, default=4096)
+    p.add_argument("--seed", type=int, default=2026)
+    p.add_argument("--sample", type=int, default=304)
+    p.add_argument("--out", required=True)
+    a = p.parse_args(argv)
+    dt = torch.float64 if a.dtype == "f64" else torch.float32
+    shapes, ops, _, _ = batch_items(a.seed, a.count)
+    t0 = time.time()
+    tu = Tuner(torch, dt, sample=a.sample)
+    table = tu.tune(ops, shapes, seed=a.seed)
+    meta = {"dtype": a.dtype, "count": a.count, "seed": a.seed, "sample": a.sample,
+            "seconds": time.time() - t0, "device": torch.cuda.get_device_name(),
+            "trials": {f"{k[0]},{k[1]},{k[2]}": {f"{b},{L},{t}": ms for (b, L, t), ms in v.items()}
+                       for k, v in tu.trials.items()}}
+    save_table(a.out, table, meta)
+    print(f"tuned {len(table)} classes in {meta['seconds']:.1f} s -> {a.out}")
+
+
+if __name__ == "__main__":
+    main()
