@@ -1,4 +1,5 @@
-"""CPU oracle for tree-based LU (CALU) and QR (CAQR / TSQR) in FP64.
+"""CPU oracle for tree-based LU (CALU) and QR (CAQR / TSQR) in FP64 (and the
+same code built for FP32, used for the FP32 form of the batched path).
 
 TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this package; only
 ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
@@ -22,8 +23,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ca_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libca_oracle.so")
+_LIB32 = os.path.join(_HERE, "_build", "libca_oracle_f32.so")
 _lock = threading.Lock()
 _lib = None
+_lib32 = None
 
 MAXLEV = 8
 BINARY = 0
@@ -40,22 +43,29 @@ class _Tree(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile ``ca_oracle.c`` into ``oracle/_build/libca_oracle.so``."""
+    """Compile ``ca_oracle.c`` into ``oracle/_build/libca_oracle.so`` (FP64)
+    and ``libca_oracle_f32.so`` (the same source with ORA_REAL=float)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-shared",
-           "-fPIC", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
+    for lib, extra in ((_LIB, []), (_LIB32, ["-DORA_REAL=float"])):
+        if (not force and os.path.exists(lib)
+                and os.path.getmtime(lib) >= os.path.getmtime(_SRC)):
+            continue
+        tmp = lib + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-shared",
+               "-fPIC", *extra, "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, lib)
     return _LIB
 
 
-def _load():
-    global _lib
+def _load(dtype=np.float64):
+    global _lib, _lib32
     with _lock:
+        if np.dtype(dtype) == np.float32:
+            if _lib32 is None:
+                build()
+                _lib32 = _declare(ctypes.CDLL(_LIB32))
+            return _lib32
         if _lib is None:
             alt = os.environ.get("CA_ORACLE_LIB")  # a planted-mistake build (tests only)
             if alt:
@@ -63,21 +73,25 @@ def _load():
             else:
                 build()
                 lib = ctypes.CDLL(_LIB)
-            P = ctypes.c_void_p
-            I = ctypes.c_int
-            lib.ora_tree_counts.argtypes = [I, P, P, P]
-            lib.ora_getf2.argtypes = [I, I, P, I, P, P]
-            lib.ora_tslu_select.argtypes = [I, I, P, I, P, P, P]
-            lib.ora_calu.argtypes = [I, I, P, I, I, P, P, P]
-            lib.ora_getrs.argtypes = [I, I, P, I, P, P, I]
-            lib.ora_geqrt.argtypes = [I, I, P, I, P, I]
-            lib.ora_caqr_tcount.argtypes = [I, I, I, P]
-            lib.ora_caqr_tcount.restype = ctypes.c_longlong
-            lib.ora_caqr.argtypes = [I, I, P, I, I, P, P]
-            lib.ora_geqrs.argtypes = [I, I, I, P, I, I, P, P, P, I]
-            lib.ora_caqr_apply_qt.argtypes = [I, I, P, I, I, P, P, P, I, I]
-            _lib = lib
+            _lib = _declare(lib)
     return _lib
+
+
+def _declare(lib):
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    lib.ora_tree_counts.argtypes = [I, P, P, P]
+    lib.ora_getf2.argtypes = [I, I, P, I, P, P]
+    lib.ora_tslu_select.argtypes = [I, I, P, I, P, P, P]
+    lib.ora_calu.argtypes = [I, I, P, I, I, P, P, P]
+    lib.ora_getrs.argtypes = [I, I, P, I, P, P, I]
+    lib.ora_geqrt.argtypes = [I, I, P, I, P, I]
+    lib.ora_caqr_tcount.argtypes = [I, I, I, P]
+    lib.ora_caqr_tcount.restype = ctypes.c_longlong
+    lib.ora_caqr.argtypes = [I, I, P, I, I, P, P]
+    lib.ora_geqrs.argtypes = [I, I, I, P, I, I, P, P, P, I]
+    lib.ora_caqr_apply_qt.argtypes = [I, I, P, I, I, P, P, P, I, I]
+    return lib
 
 
 def make_tree(leaf_rows: int, levels=((0, BINARY),)) -> dict:
@@ -144,10 +158,15 @@ def tslu_select(P, tree: dict):
     return sel[:k], nt.value
 
 
-def calu(A, b: int, tree: dict):
-    """CALU with tournament pivoting.  Returns (LU, ipiv 1-based, info, nearties)."""
-    lib = _load()
-    A = _f64(A)
+def _arr(a, dtype) -> np.ndarray:
+    return np.asfortranarray(np.array(a, dtype=dtype, copy=True))
+
+
+def calu(A, b: int, tree: dict, dtype=np.float64):
+    """CALU with tournament pivoting.  Returns (LU, ipiv 1-based, info, nearties).
+    dtype float32: the FP32 build (every operation and pivot decision in FP32)."""
+    lib = _load(dtype)
+    A = _arr(A, dtype)
     m, n = A.shape
     ipiv = np.zeros(max(1, min(m, n)), dtype=np.int32)
     nt = ctypes.c_long(0)
@@ -190,12 +209,13 @@ def caqr_tcount(m: int, n: int, b: int, tree: dict) -> int:
     return int(c)
 
 
-def caqr(A, b: int, tree: dict):
-    """CAQR (TSQR panels + tree update).  Returns (QR factors, T storage)."""
-    lib = _load()
-    A = _f64(A)
+def caqr(A, b: int, tree: dict, dtype=np.float64):
+    """CAQR (TSQR panels + tree update).  Returns (QR factors, T storage).
+    dtype float32: the FP32 build."""
+    lib = _load(dtype)
+    A = _arr(A, dtype)
     m, n = A.shape
-    T = np.zeros(max(1, caqr_tcount(m, n, b, tree)), dtype=np.float64)
+    T = np.zeros(max(1, caqr_tcount(m, n, b, tree)), dtype=dtype)
     t = _ctree(tree)
     rc = lib.ora_caqr(m, n, _ptr(A), max(1, m), b, ctypes.byref(t), _ptr(T))
     if rc:

@@ -1,6 +1,8 @@
 /*
  * ca_oracle.c -- plain, slow CPU reference for tree-based LU (CALU, tournament
- * pivoting) and QR (CAQR, TSQR) in IEEE FP64.
+ * pivoting) and QR (CAQR, TSQR) in IEEE FP64 (the default build) or IEEE
+ * FP32 (built with -DORA_REAL=float, for the FP32 form of the batched path,
+ * so that pivot decisions are taken in the precision the kernel uses).
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the correctness oracle for the GPU
  * library.  Only the test-suite, the smoke check and the CPU-baseline leg of
@@ -47,6 +49,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifndef ORA_REAL
+#define ORA_REAL double
+#endif
+typedef ORA_REAL real;
+
 #define ORA_MAXLEV 8
 #define ORA_BINARY 0
 #define ORA_FLAT 1
@@ -62,7 +69,7 @@ typedef struct {
 
 /* near-tie threshold: a runner-up within this relative distance of the
  * selected maximum is counted (pivot choice then depends on rounding). */
-#define ORA_NEARTIE 1e-10
+#define ORA_NEARTIE (sizeof(real) == 4 ? 1e-4 : 1e-10)
 
 /* ------------------------------------------------------------------------ */
 /* Reduction tree                                                           */
@@ -196,24 +203,24 @@ int ora_tree_counts(int m, const ora_tree *t, int *nleaves, int *nmerges) {
  * position i; rows are physically swapped, so after the call perm[0..k) are
  * the labels of the selected pivot rows in selection order, k = min(r, c).
  * Returns the 1-based first step with an exactly zero pivot column, else 0. */
-static int gepp_block(int r, int c, double *W, int ldw, int *perm, long *nearties) {
+static int gepp_block(int r, int c, real *W, int ldw, int *perm, long *nearties) {
   int info = 0;
   int k = r < c ? r : c;
   for (int j = 0; j < k; ++j) {
     int p = j;
-    double amax = fabs(AT(W, ldw, j, j));
+    real amax = fabs(AT(W, ldw, j, j));
     for (int i = j + 1; i < r; ++i) {
-      double a = fabs(AT(W, ldw, i, j));
+      real a = fabs(AT(W, ldw, i, j));
       if (a > amax) {
         amax = a;
         p = i;
       }
     }
     if (nearties && amax > 0.0) {
-      double second = -1.0;
+      real second = -1.0;
       for (int i = j; i < r; ++i) {
         if (i == p) continue;
-        double a = fabs(AT(W, ldw, i, j));
+        real a = fabs(AT(W, ldw, i, j));
         if (a > second) second = a;
       }
       if (second >= amax * (1.0 - ORA_NEARTIE)) (*nearties)++;
@@ -221,7 +228,7 @@ static int gepp_block(int r, int c, double *W, int ldw, int *perm, long *neartie
     if (AT(W, ldw, p, j) != 0.0) {
       if (p != j) {
         for (int q = 0; q < c; ++q) {
-          double tmp = AT(W, ldw, j, q);
+          real tmp = AT(W, ldw, j, q);
           AT(W, ldw, j, q) = AT(W, ldw, p, q);
           AT(W, ldw, p, q) = tmp;
         }
@@ -229,10 +236,10 @@ static int gepp_block(int r, int c, double *W, int ldw, int *perm, long *neartie
         perm[j] = perm[p];
         perm[p] = ti;
       }
-      double piv = AT(W, ldw, j, j);
+      real piv = AT(W, ldw, j, j);
       for (int i = j + 1; i < r; ++i) AT(W, ldw, i, j) = AT(W, ldw, i, j) / piv;
       for (int q = j + 1; q < c; ++q) {
-        double u = AT(W, ldw, j, q);
+        real u = AT(W, ldw, j, q);
         for (int i = j + 1; i < r; ++i) AT(W, ldw, i, q) = AT(W, ldw, i, q) - AT(W, ldw, i, j) * u;
       }
     } else if (info == 0) {
@@ -244,7 +251,7 @@ static int gepp_block(int r, int c, double *W, int ldw, int *perm, long *neartie
 
 /* Public: GEPP of an m x n matrix in place; ipiv is the 1-based LAPACK swap
  * sequence of length min(m, n).  Returns info (0 or first zero pivot). */
-int ora_getf2(int m, int n, double *A, int lda, int *ipiv, long *nearties) {
+int ora_getf2(int m, int n, real *A, int lda, int *ipiv, long *nearties) {
   int k = m < n ? m : n;
   int *perm = (int *)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
   int *pos = (int *)malloc(sizeof(int) * (size_t)(m > 0 ? m : 1));
@@ -282,7 +289,7 @@ int ora_getf2(int m, int n, double *A, int lda, int *ipiv, long *nearties) {
  * yields min(rows, b) candidate rows; every merge stacks its children's
  * candidate rows (original values, child order, each child in its selection
  * order) and GEPP picks min(sum, b) of them (Sec. 3.2, reduction steps). */
-int ora_tslu_select(int m, int b, const double *P, int ldp, const ora_tree *t, int *sel,
+int ora_tslu_select(int m, int b, const real *P, int ldp, const ora_tree *t, int *sel,
                     long *nearties) {
   if (m < 1 || b < 1 || t->leaf_rows < b) return -1;
   int L = t->leaf_rows;
@@ -299,7 +306,7 @@ int ora_tslu_select(int m, int b, const double *P, int ldp, const ora_tree *t, i
   for (int r = 0; r < plan.nrounds; ++r)
     for (int o = 0; o < plan.r[r].nout; ++o)
       if ((size_t)plan.r[r].cnt[o] * b > wmax) wmax = (size_t)plan.r[r].cnt[o] * b;
-  double *W = (double *)malloc(sizeof(double) * wmax * (size_t)b);
+  real *W = (real *)malloc(sizeof(real) * wmax * (size_t)b);
   int *perm = (int *)malloc(sizeof(int) * wmax);
   if (!cand || !ncand || !W || !perm) return -1000;
 
@@ -375,7 +382,7 @@ int ora_tslu_select(int m, int b, const double *P, int ldp, const ora_tree *t, i
  * bk = min(b, min(m, n) - kb).  ipiv gets min(m, n) 1-based row swaps.
  * Returns info: 0, or 1 + the first column whose U diagonal is exactly zero;
  * negative on a bad argument. */
-int ora_calu(int m, int n, double *A, int lda, int b, const ora_tree *t, int *ipiv,
+int ora_calu(int m, int n, real *A, int lda, int b, const ora_tree *t, int *ipiv,
              long *nearties) {
   if (m < 0 || n < 0 || lda < (m > 1 ? m : 1) || b < 1 || t->leaf_rows < b) return -1;
   int K = m < n ? m : n;
@@ -387,7 +394,7 @@ int ora_calu(int m, int n, double *A, int lda, int b, const ora_tree *t, int *ip
   for (int kb = 0; kb < K; kb += b) {
     int bk = (K - kb < b) ? K - kb : b;
     int mk = m - kb;
-    double *P = &AT(A, lda, kb, kb);
+    real *P = &AT(A, lda, kb, kb);
     /* 1. tournament pivoting on the panel */
     int k = ora_tslu_select(mk, bk, P, lda, t, sel, nearties);
     if (k != bk) {
@@ -405,7 +412,7 @@ int ora_calu(int m, int n, double *A, int lda, int b, const ora_tree *t, int *ip
       ipiv[kb + i] = kb + p + 1;
       if (p != i) {
         for (int q = 0; q < n; ++q) {
-          double tmp = AT(A, lda, kb + i, q);
+          real tmp = AT(A, lda, kb + i, q);
           AT(A, lda, kb + i, q) = AT(A, lda, kb + p, q);
           AT(A, lda, kb + p, q) = tmp;
         }
@@ -419,14 +426,14 @@ int ora_calu(int m, int n, double *A, int lda, int b, const ora_tree *t, int *ip
     /* 3. L11 U11: LU without pivoting of the selected rows, in their order
      *    (the root's GEPP factors of the same rows) */
     for (int j = 0; j < bk; ++j) {
-      double piv = AT(A, lda, kb + j, kb + j);
+      real piv = AT(A, lda, kb + j, kb + j);
       if (piv == 0.0) {
         if (info == 0) info = kb + j + 1;
         continue;
       }
       for (int i = j + 1; i < bk; ++i) AT(A, lda, kb + i, kb + j) = AT(A, lda, kb + i, kb + j) / piv;
       for (int q = j + 1; q < bk; ++q) {
-        double u = AT(A, lda, kb + j, kb + q);
+        real u = AT(A, lda, kb + j, kb + q);
         for (int i = j + 1; i < bk; ++i)
           AT(A, lda, kb + i, kb + q) = AT(A, lda, kb + i, kb + q) - AT(A, lda, kb + i, kb + j) * u;
       }
@@ -434,21 +441,21 @@ int ora_calu(int m, int n, double *A, int lda, int b, const ora_tree *t, int *ip
     /* 4. block column of L: L21 = A21 U11^{-1} (row-wise substitution) */
     for (int i = kb + bk; i < m; ++i)
       for (int j = 0; j < bk; ++j) {
-        double s = AT(A, lda, i, kb + j);
+        real s = AT(A, lda, i, kb + j);
         for (int l = 0; l < j; ++l) s = s - AT(A, lda, i, kb + l) * AT(A, lda, kb + l, kb + j);
         AT(A, lda, i, kb + j) = s / AT(A, lda, kb + j, kb + j);
       }
     /* 5. block row of U: U12 = L11^{-1} A12 (unit lower substitution) */
     for (int q = kb + bk; q < n; ++q)
       for (int i = 0; i < bk; ++i) {
-        double s = AT(A, lda, kb + i, q);
+        real s = AT(A, lda, kb + i, q);
         for (int l = 0; l < i; ++l) s = s - AT(A, lda, kb + i, kb + l) * AT(A, lda, kb + l, q);
         AT(A, lda, kb + i, q) = s;
       }
     /* 6. Schur complement: A22 -= L21 U12 */
     for (int q = kb + bk; q < n; ++q)
       for (int i = kb + bk; i < m; ++i) {
-        double s = AT(A, lda, i, q);
+        real s = AT(A, lda, i, q);
         for (int l = 0; l < bk; ++l) s = s - AT(A, lda, i, kb + l) * AT(A, lda, kb + l, q);
         AT(A, lda, i, q) = s;
       }
@@ -461,24 +468,24 @@ int ora_calu(int m, int n, double *A, int lda, int b, const ora_tree *t, int *ip
 
 /* Solve A x = B from the CALU (or getf2) factors: row swaps, unit-lower
  * forward substitution, upper back substitution.  B is n x nrhs, in place. */
-int ora_getrs(int n, int nrhs, const double *LU, int lda, const int *ipiv, double *B, int ldb) {
+int ora_getrs(int n, int nrhs, const real *LU, int lda, const int *ipiv, real *B, int ldb) {
   for (int c = 0; c < nrhs; ++c) {
-    double *x = &AT(B, ldb, 0, c);
+    real *x = &AT(B, ldb, 0, c);
     for (int i = 0; i < n; ++i) {
       int p = ipiv[i] - 1;
       if (p != i) {
-        double tmp = x[i];
+        real tmp = x[i];
         x[i] = x[p];
         x[p] = tmp;
       }
     }
     for (int i = 0; i < n; ++i) {
-      double s = x[i];
+      real s = x[i];
       for (int l = 0; l < i; ++l) s = s - AT(LU, lda, i, l) * x[l];
       x[i] = s;
     }
     for (int i = n - 1; i >= 0; --i) {
-      double s = x[i];
+      real s = x[i];
       for (int l = i + 1; l < n; ++l) s = s - AT(LU, lda, i, l) * x[l];
       x[i] = s / AT(LU, lda, i, i);
     }
@@ -493,26 +500,26 @@ int ora_getrs(int n, int nrhs, const double *LU, int lda, const int *ipiv, doubl
 /* Unblocked Householder QR of the r x c block W (ld ldw) in place, LAPACK
  * geqr2 layout: R on and above the diagonal, v below it (unit diagonal
  * implied).  tau[0..min(r,c)). */
-static void geqr2(int r, int c, double *W, int ldw, double *tau) {
+static void geqr2(int r, int c, real *W, int ldw, real *tau) {
   int k = r < c ? r : c;
   for (int j = 0; j < k; ++j) {
-    double alpha = AT(W, ldw, j, j);
-    double xn2 = 0.0;
+    real alpha = AT(W, ldw, j, j);
+    real xn2 = 0.0;
     for (int i = j + 1; i < r; ++i) xn2 = xn2 + AT(W, ldw, i, j) * AT(W, ldw, i, j);
     if (xn2 == 0.0) {
       tau[j] = 0.0;
       continue;
     }
-    double nrm = sqrt(alpha * alpha + xn2);
-    double beta = (alpha >= 0.0) ? -nrm : nrm;
-    double tj = (beta - alpha) / beta;
-    double scal = 1.0 / (alpha - beta);
+    real nrm = sqrt(alpha * alpha + xn2);
+    real beta = (alpha >= 0.0) ? -nrm : nrm;
+    real tj = (beta - alpha) / beta;
+    real scal = (real)1 / (alpha - beta);
     for (int i = j + 1; i < r; ++i) AT(W, ldw, i, j) = AT(W, ldw, i, j) * scal;
     AT(W, ldw, j, j) = beta;
     tau[j] = tj;
     /* apply H_j = I - tau v v^T to the columns on the right */
     for (int q = j + 1; q < c; ++q) {
-      double w = AT(W, ldw, j, q);
+      real w = AT(W, ldw, j, q);
       for (int i = j + 1; i < r; ++i) w = w + AT(W, ldw, i, j) * AT(W, ldw, i, q);
       w = tj * w;
       AT(W, ldw, j, q) = AT(W, ldw, j, q) - w;
@@ -523,7 +530,7 @@ static void geqr2(int r, int c, double *W, int ldw, double *tau) {
 
 /* LAPACK larft (forward, columnwise): T (k x k, ld ldt) upper triangular with
  * H_0 H_1 ... H_{k-1} = I - V T V^T, V the r x k unit lower trapezoid in W. */
-static void larft(int r, int k, const double *V, int ldv, const double *tau, double *T, int ldt) {
+static void larft(int r, int k, const real *V, int ldv, const real *tau, real *T, int ldt) {
   for (int j = 0; j < k; ++j) {
     for (int i = 0; i < k; ++i) AT(T, ldt, i, j) = 0.0;
   }
@@ -533,13 +540,13 @@ static void larft(int r, int k, const double *V, int ldv, const double *tau, dou
     /* z = V(:, 0:j)^T v_j */
     for (int i = 0; i < j; ++i) {
       /* v_j has 1 at row j and V(row, j) below; V(:, i) has 1 at row i */
-      double s = AT(V, ldv, j, i); /* row j of v_i times the unit of v_j */
+      real s = AT(V, ldv, j, i); /* row j of v_i times the unit of v_j */
       for (int q = j + 1; q < r; ++q) s = s + AT(V, ldv, q, i) * AT(V, ldv, q, j);
       AT(T, ldt, i, j) = -tau[j] * s;
     }
     /* T(0:j, j) = T(0:j, 0:j) * z  (upper triangular times vector) */
     for (int i = 0; i < j; ++i) {
-      double s = 0.0;
+      real s = 0.0;
       for (int q = i; q < j; ++q) s = s + AT(T, ldt, i, q) * AT(T, ldt, q, j);
       AT(T, ldt, i, j) = s;
     }
@@ -548,24 +555,24 @@ static void larft(int r, int k, const double *V, int ldv, const double *tau, dou
 
 /* Apply Q^T = I - Y T^T Y^T to C (r x nc, ld ldc); Y is r x k dense (the unit
  * diagonal and the zeros are stored explicitly), T is k x k. */
-static void apply_qt_dense(int r, int k, const double *Y, int ldy, const double *T, int ldt,
-                           double *C, int ldc, int nc, double *Wk /* k x nc */) {
+static void apply_qt_dense(int r, int k, const real *Y, int ldy, const real *T, int ldt,
+                           real *C, int ldc, int nc, real *Wk /* k x nc */) {
   for (int q = 0; q < nc; ++q)
     for (int j = 0; j < k; ++j) {
-      double s = 0.0;
+      real s = 0.0;
       for (int i = 0; i < r; ++i) s = s + AT(Y, ldy, i, j) * AT(C, ldc, i, q);
       AT(Wk, k, j, q) = s;
     }
   /* W <- T^T W (T upper, so T^T lower): process rows from the bottom */
   for (int q = 0; q < nc; ++q)
     for (int j = k - 1; j >= 0; --j) {
-      double s = 0.0;
+      real s = 0.0;
       for (int l = 0; l <= j; ++l) s = s + AT(T, ldt, l, j) * AT(Wk, k, l, q);
       AT(Wk, k, j, q) = s;
     }
   for (int q = 0; q < nc; ++q)
     for (int i = 0; i < r; ++i) {
-      double s = AT(C, ldc, i, q);
+      real s = AT(C, ldc, i, q);
       for (int j = 0; j < k; ++j) s = s - AT(Y, ldy, i, j) * AT(Wk, k, j, q);
       AT(C, ldc, i, q) = s;
     }
@@ -573,9 +580,9 @@ static void apply_qt_dense(int r, int k, const double *Y, int ldy, const double 
 
 /* Public: Householder QR of an m x n block in place (geqr2) plus its T
  * (larft), k = min(m, n); T is k x k with ld ldt. */
-int ora_geqrt(int m, int n, double *A, int lda, double *T, int ldt) {
+int ora_geqrt(int m, int n, real *A, int lda, real *T, int ldt) {
   int k = m < n ? m : n;
-  double *tau = (double *)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+  real *tau = (real *)malloc(sizeof(real) * (size_t)(k > 0 ? k : 1));
   if (!tau) return -1000;
   geqr2(m, n, A, lda, tau);
   larft(m, k, A, lda, tau, T, ldt);
@@ -603,8 +610,8 @@ int ora_geqrt(int m, int n, double *A, int lda, double *T, int ldt) {
 /* Stack the R rows of the children [s, s+cnt) of one merge: child ch owns
  * panel rows top[ch] .. top[ch] + c[ch] - 1.  Fills S (rows x bk, ld rows)
  * with the upper trapezoids (zeros below each child's diagonal). */
-static void stack_r(const double *P, int ldp, int bk, const int *top, const int *c, int s,
-                    int cnt, double *S, int rows) {
+static void stack_r(const real *P, int ldp, int bk, const int *top, const int *c, int s,
+                    int cnt, real *S, int rows) {
   int at = 0;
   for (int ch = s; ch < s + cnt; ++ch) {
     for (int i = 0; i < c[ch]; ++i) {
@@ -616,13 +623,13 @@ static void stack_r(const double *P, int ldp, int bk, const int *top, const int 
 
 /* Dense stacked Y of one merge from the stored blocks: identity for the
  * first child, the stored upper trapezoid for the others. */
-static void stack_y(const double *P, int ldp, int bk, const int *top, const int *c, int s, int cnt,
-                    double *Y, int rows) {
+static void stack_y(const real *P, int ldp, int bk, const int *top, const int *c, int s, int cnt,
+                    real *Y, int rows) {
   int at = 0;
   for (int ch = s; ch < s + cnt; ++ch) {
     for (int i = 0; i < c[ch]; ++i)
       for (int q = 0; q < bk; ++q) {
-        double v;
+        real v;
         if (ch == s)
           v = (q == i) ? 1.0 : 0.0;
         else
@@ -635,7 +642,7 @@ static void stack_y(const double *P, int ldp, int bk, const int *top, const int 
 
 /* TSQR of one panel (mk x bk at P, ld ldp) with the tree; T blocks of size
  * b x b go to Tp (leaves then merges). */
-static int tsqr_panel(int mk, int bk, int b, double *P, int ldp, const ora_tree *t, double *Tp) {
+static int tsqr_panel(int mk, int bk, int b, real *P, int ldp, const ora_tree *t, real *Tp) {
   int L = t->leaf_rows;
   int nl = (mk + L - 1) / L;
   ora_plan plan;
@@ -651,15 +658,15 @@ static int tsqr_panel(int mk, int bk, int b, double *P, int ldp, const ora_tree 
   for (int r = 0; r < plan.nrounds; ++r)
     for (int o = 0; o < plan.r[r].nout; ++o)
       if (plan.r[r].cnt[o] > maxcnt) maxcnt = plan.r[r].cnt[o];
-  double *S = (double *)malloc(sizeof(double) * (size_t)maxcnt * bk * bk);
-  double *tau = (double *)malloc(sizeof(double) * (size_t)bk);
+  real *S = (real *)malloc(sizeof(real) * (size_t)maxcnt * bk * bk);
+  real *tau = (real *)malloc(sizeof(real) * (size_t)bk);
   if (!top || !c || !ntop || !nc || !S || !tau) return -1000;
   size_t bb = (size_t)b * b;
   for (int j = 0; j < nl; ++j) {
     int r0 = j * L;
     int rows = (mk - r0 < L) ? mk - r0 : L;
-    double *Tj = Tp + (size_t)j * bb;
-    memset(Tj, 0, sizeof(double) * bb);
+    real *Tj = Tp + (size_t)j * bb;
+    memset(Tj, 0, sizeof(real) * bb);
     ora_geqrt(rows, bk, &AT(P, ldp, r0, 0), ldp, Tj, b);
     top[j] = r0;
     c[j] = rows < bk ? rows : bk;
@@ -679,8 +686,8 @@ static int tsqr_panel(int mk, int bk, int b, double *P, int ldp, const ora_tree 
       stack_r(P, ldp, bk, top, c, s, cnt, S, rows);
       geqr2(rows, bk, S, rows, tau);
       int kk = rows < bk ? rows : bk;
-      double *Tn = Tp + (size_t)node * bb;
-      memset(Tn, 0, sizeof(double) * bb);
+      real *Tn = Tp + (size_t)node * bb;
+      memset(Tn, 0, sizeof(real) * bb);
       larft(rows, kk, S, rows, tau, Tn, b);
       /* new R into the first child's rows; Y blocks into the others */
       int at = 0;
@@ -711,8 +718,8 @@ static int tsqr_panel(int mk, int bk, int b, double *P, int ldp, const ora_tree 
 /* Apply the Q^T of one factored panel (mk rows, width bk, factors at P) to
  * the mk x nc block C: leaves first (UPFACT), then merges bottom-up
  * (UPELIM).  Tp holds the panel's T blocks (b x b each). */
-static int apply_panel_qt(int mk, int bk, int b, const double *P, int ldp, const ora_tree *t,
-                          const double *Tp, double *C, int ldc, int ncols) {
+static int apply_panel_qt(int mk, int bk, int b, const real *P, int ldp, const ora_tree *t,
+                          const real *Tp, real *C, int ldc, int ncols) {
   if (ncols <= 0) return 0;
   int L = t->leaf_rows;
   int nl = (mk + L - 1) / L;
@@ -726,9 +733,9 @@ static int apply_panel_qt(int mk, int bk, int b, const double *P, int ldp, const
     for (int o = 0; o < plan.r[r].nout; ++o)
       if (plan.r[r].cnt[o] > maxcnt) maxcnt = plan.r[r].cnt[o];
   size_t ymax = (size_t)(L > maxcnt * bk ? L : maxcnt * bk);
-  double *Y = (double *)malloc(sizeof(double) * ymax * bk);
-  double *Cs = (double *)malloc(sizeof(double) * ymax * (size_t)ncols);
-  double *Wk = (double *)malloc(sizeof(double) * (size_t)bk * ncols);
+  real *Y = (real *)malloc(sizeof(real) * ymax * bk);
+  real *Cs = (real *)malloc(sizeof(real) * ymax * (size_t)ncols);
+  real *Wk = (real *)malloc(sizeof(real) * (size_t)bk * ncols);
   int *top = (int *)malloc(sizeof(int) * (size_t)nl);
   int *c = (int *)malloc(sizeof(int) * (size_t)nl);
   int *ntop = (int *)malloc(sizeof(int) * (size_t)nl);
@@ -811,13 +818,13 @@ long long ora_caqr_tcount(int m, int n, int b, const ora_tree *t) {
  * tree; T receives ora_caqr_tcount doubles.  Per panel: TSQR, then the
  * trailing columns are updated by the leaves' and merges' Q^T (Algorithm
  * ML-CAQR with one level: UPFACT then UPELIM). */
-int ora_caqr(int m, int n, double *A, int lda, int b, const ora_tree *t, double *T) {
+int ora_caqr(int m, int n, real *A, int lda, int b, const ora_tree *t, real *T) {
   if (m < n || n < 0 || lda < (m > 1 ? m : 1) || b < 1 || t->leaf_rows < b) return -1;
   size_t off = 0;
   for (int kb = 0; kb < n; kb += b) {
     int bk = (n - kb < b) ? n - kb : b;
     int mk = m - kb;
-    double *P = &AT(A, lda, kb, kb);
+    real *P = &AT(A, lda, kb, kb);
     int used = tsqr_panel(mk, bk, b, P, lda, t, T + off);
     if (used < 0) return used;
     int rc = apply_panel_qt(mk, bk, b, P, lda, t, T + off, &AT(A, lda, kb, kb + bk), lda, n - kb - bk);
@@ -829,8 +836,8 @@ int ora_caqr(int m, int n, double *A, int lda, int b, const ora_tree *t, double 
 
 /* Public: least-squares solve from the CAQR factors: B (m x nrhs) <- Q^T B
  * panel by panel, then x = R^{-1} (Q^T B)[0:n] in B's top n rows. */
-int ora_geqrs(int m, int n, int nrhs, const double *QR, int lda, int b, const ora_tree *t,
-              const double *T, double *B, int ldb) {
+int ora_geqrs(int m, int n, int nrhs, const real *QR, int lda, int b, const ora_tree *t,
+              const real *T, real *B, int ldb) {
   if (m < n || b < 1 || t->leaf_rows < b) return -1;
   size_t off = 0;
   for (int kb = 0; kb < n; kb += b) {
@@ -845,7 +852,7 @@ int ora_geqrs(int m, int n, int nrhs, const double *QR, int lda, int b, const or
   }
   for (int c = 0; c < nrhs; ++c)
     for (int i = n - 1; i >= 0; --i) {
-      double s = AT(B, ldb, i, c);
+      real s = AT(B, ldb, i, c);
       for (int l = i + 1; l < n; ++l) s = s - AT(QR, lda, i, l) * AT(B, ldb, l, c);
       AT(B, ldb, i, c) = s / AT(QR, lda, i, i);
     }
@@ -854,8 +861,8 @@ int ora_geqrs(int m, int n, int nrhs, const double *QR, int lda, int b, const or
 
 /* Public: apply Q^T of a CAQR factorization to C (m x nc) without the solve
  * (used by the tests to rebuild Q). */
-int ora_caqr_apply_qt(int m, int n, const double *QR, int lda, int b, const ora_tree *t,
-                      const double *T, double *C, int ldc, int nc) {
+int ora_caqr_apply_qt(int m, int n, const real *QR, int lda, int b, const ora_tree *t,
+                      const real *T, real *C, int ldc, int nc) {
   size_t off = 0;
   for (int kb = 0; kb < n; kb += b) {
     int bk = (n - kb < b) ? n - kb : b;

@@ -485,7 +485,8 @@ __device__ void cta_calu(const ca_batch_item_t &it, Fixed<T> &F, T *R, int regio
 // (b x b, ld b, zero outside the top-left kmax x kmax).  Returns kmax.
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ int node_qr(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool use_fz, T *Tg, int b) {
+__device__ int node_qr(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool use_fz, T *Tg, int b,
+                       int region_elems) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int kmax = min(rows, bk);
   for (int j = 0; j < kmax; ++j) {
@@ -532,11 +533,19 @@ __device__ int node_qr(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool use_
     }
     __syncthreads();
   }
-  // T: zero the block, then column by column
-  for (int e = tid; e < b * b; e += kBT) Tg[e] = T(0);
-  __syncthreads();
-  for (int jj = 0; jj < kmax; ++jj) {
-    // z_q = v_q^T v_jj for q < jj (rows >= jj; v_jj(jj) = 1)
+  // T (larft, forward columnwise): column jj = -tau_jj T(0:jj, 0:jj) z with
+  // z_q = v_q^T v_jj; built in shared memory after the tile when it fits
+  // (odd leading dimension), else in place in Tg
+  const int kk = kmax;
+  const int ldw = kk | 1;
+  const bool in_smem = (size_t)ld * bk + (size_t)ldw * kk <= (size_t)region_elems;
+  T *Tw = in_smem ? tile + (size_t)ld * bk : Tg;
+  const int ldt = in_smem ? ldw : b;
+  if (!in_smem) {
+    for (int e = tid; e < b * b; e += kBT) Tg[e] = T(0);
+    __syncthreads();
+  }
+  for (int jj = 0; jj < kk; ++jj) {
     for (int q = warp; q < jj; q += kBW) {
       const T *cq = tile + (size_t)q * ld;
       const T *cjj = tile + (size_t)jj * ld;
@@ -547,13 +556,20 @@ __device__ int node_qr(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool use_
     }
     __syncthreads();
     const T tj = F.tau[jj];
-    for (int i = tid; i < jj; i += kBT) {
-      T s = T(0);
-      if (tj != T(0))
-        for (int q = i; q < jj; ++q) s = fma(Tg[i + (size_t)q * b], F.z[q], s);
-      Tg[i + (size_t)jj * b] = -tj * s;
+    for (int i = warp; i < jj; i += kBW) {
+      T acc = T(0);
+      for (int q = i + lane; q < jj; q += 32) acc = fma(Tw[i + (size_t)q * ldt], F.z[q], acc);
+      acc = wsum(acc);
+      if (lane == 0) Tw[i + (size_t)jj * ldt] = -tj * acc;
     }
-    if (tid == 0) Tg[jj + (size_t)jj * b] = tj;
+    if (tid == 0) Tw[jj + (size_t)jj * ldt] = tj;
+    __syncthreads();
+  }
+  if (in_smem) {
+    for (int e = tid; e < b * b; e += kBT) {
+      const int i = e % b, k = e / b;
+      Tg[e] = (k < kk && i <= k) ? Tw[i + (size_t)k * ldw] : T(0);
+    }
     __syncthreads();
   }
   return kmax;
@@ -580,61 +596,74 @@ __device__ int merge_rows(const int *top, const int *c, int start, int cnt, Fixe
 
 // C <- Q_node^T C for the node rows F.prow[0..rows) (leaf: Y unit lower
 // trapezoid stored in those rows; merge: identity on the first child's rows,
-// stored upper trapezoids on the others), nref reflectors, T block Tg.
-template <class T>
-__device__ void node_apply(const T *P, int lda, T *C, int nt, int rows, int nref, bool leaf, const T *Tg, int b,
-                           Fixed<T> &F, T *R) {
+// stored upper trapezoids on the others), nref <= TK reflectors, T block Tg.
+// Tile: TK reflectors x TC columns of C; thread (tx, ty) holds W(k, c) for
+// k = tx + TX i, c = ty + TY j (i, j < 4).  W = Y^T C over row chunks of kRw,
+// W' = T^T W, C -= Y W' over row chunks of TK.
+constexpr int kRw = 64;
+
+template <class T, int TK>
+__device__ void node_apply_t(const T *P, int lda, T *C, int nt, int rows, int nref, bool leaf, const T *Tg, int b,
+                             Fixed<T> &F, T *R) {
+  constexpr int TX = TK / 4, TY = kBT / TX, TC = 4 * TY;
+  constexpr int SK = TK + 1, SC = TC + 1;  // odd strides
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
-  T *Ys = R;                     // kTl rows x nref, Ys[r * kTs + k]
-  T *CW = Ys + kTl * kTs;        // C chunk Cs[r * kTs + c], then W'[k * kTs + c]
-  T *Ts = CW + kTl * kTs;        // nref x nref, ld kTl
+  const int tx = tid % TX, ty = tid / TX;
+  T *Ys = R;                     // row chunk x TK, Ys[r * SK + k]
+  T *CW = Ys + kRw * SK;         // C chunk Cs[r * SC + c], then W'[k * SC + c]
+  T *Ts = CW + kRw * SC;         // T transposed: Ts[k * SK + i] = T(i, k)
   const int c0row = F.iscal[8];
-  for (int e = tid; e < kTl * kTl; e += kBT) {
-    const int i = e & (kTl - 1), k = e / kTl;
-    Ts[e] = (i < nref && k < nref) ? Tg[i + (size_t)k * b] : T(0);
+  for (int e = tid; e < TK * TK; e += kBT) {
+    const int i = e % TK, k = e / TK;
+    Ts[k * SK + i] = (i < nref && k < nref) ? Tg[i + (size_t)k * b] : T(0);
   }
-  // Y(p, k): leaf rows hold the unit lower trapezoid; merge rows: identity
-  // on the first child, stored upper trapezoids (k >= child-local row) on
-  // the others
+  // merges: the first child's block of Y is the identity, so its rows enter
+  // W = C_0 + sum_i Y_i^T C_i and C_0 -= W' directly
+  const int pstart = leaf ? 0 : c0row;
+  // Y(p, k): leaf rows hold the unit lower trapezoid; merge rows past the
+  // first child hold stored upper trapezoids (k >= child-local row)
   auto yval = [&](int p, int k) -> T {
-    const bool stored = k < nref && (leaf ? p > k : (p >= c0row && k >= F.fz[p]));
+    const bool stored = k < nref && (leaf ? p > k : k >= F.fz[p]);
     T v = stored ? P[F.prow[p] + (size_t)k * lda] : T(0);
-    if (p == k && (leaf || p < c0row)) v = T(1);
+    if (leaf && p == k) v = T(1);
     return v;
   };
-  for (int c0 = 0; c0 < nt; c0 += kTl) {
-    const int cols = min(kTl, nt - c0);
+  for (int c0 = 0; c0 < nt; c0 += TC) {
+    const int cols = min(TC, nt - c0);
     T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-    // W = Y^T C (thread: k = tx + 16 i, c = ty + 16 j)
-    for (int p0 = 0; p0 < rows; p0 += kTl) {
-      const int pr = min(kTl, rows - p0);
+      for (int j = 0; j < 4; ++j) {
+        const int k = tx + TX * i, c = ty + TY * j;
+        acc[i][j] = (!leaf && k < c0row && c < cols) ? C[F.prow[k] + (size_t)(c0 + c) * lda] : T(0);
+      }
+    // W = Y^T C
+    for (int p0 = pstart; p0 < rows; p0 += kRw) {
+      const int pr = min(kRw, rows - p0);
       __syncthreads();
       stage<T>(
-          2 * kTl * kTl,
+          kRw * (TK + TC),
           [&](int e) -> T {
-            const int h = e >> 12, f = e & (kTl * kTl - 1);
-            const int r = f & (kTl - 1), q = f >> 6;
+            const int r = e % kRw, q = e / kRw;
             if (r >= pr) return T(0);
-            if (h == 0) return yval(p0 + r, q);
-            return q < cols ? C[F.prow[p0 + r] + (size_t)(c0 + q) * lda] : T(0);
+            if (q < TK) return yval(p0 + r, q);
+            return q - TK < cols ? C[F.prow[p0 + r] + (size_t)(c0 + q - TK) * lda] : T(0);
           },
           [&](int e, T v) {
-            const int h = e >> 12, f = e & (kTl * kTl - 1);
-            const int r = f & (kTl - 1), q = f >> 6;
-            (h == 0 ? Ys : CW)[r * kTs + q] = v;
+            const int r = e % kRw, q = e / kRw;
+            if (q < TK)
+              Ys[r * SK + q] = v;
+            else
+              CW[r * SC + q - TK] = v;
           });
       __syncthreads();
       for (int r = 0; r < pr; ++r) {
         T y[4], cc[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) y[i] = Ys[r * kTs + tx + 16 * i];
+        for (int i = 0; i < 4; ++i) y[i] = Ys[r * SK + tx + TX * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cc[j] = CW[r * kTs + ty + 16 * j];
+        for (int j = 0; j < 4; ++j) cc[j] = CW[r * SC + ty + TY * j];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -645,31 +674,40 @@ __device__ void node_apply(const T *P, int lda, T *C, int nt, int rows, int nref
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) CW[(tx + 16 * i) * kTs + ty + 16 * j] = acc[i][j];
+      for (int j = 0; j < 4; ++j) CW[(tx + TX * i) * SC + ty + TY * j] = acc[i][j];
     __syncthreads();
     // W' = T^T W
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int k = tx + 16 * i;
+      const int k = tx + TX * i;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        T s = T(0);
-        for (int q = 0; q <= k && q < nref; ++q) s = fma(Ts[q + k * kTl], CW[q * kTs + ty + 16 * j], s);
-        acc[i][j] = s;
+        T sum = T(0);
+        for (int q = 0; q <= k && q < nref; ++q) sum = fma(Ts[k * SK + q], CW[q * SC + ty + TY * j], sum);
+        acc[i][j] = sum;
       }
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) CW[(tx + 16 * i) * kTs + ty + 16 * j] = acc[i][j];
-    // C -= Y W' (thread: r = tx + 16 i, c = ty + 16 j)
-    for (int p0 = 0; p0 < rows; p0 += kTl) {
-      const int pr = min(kTl, rows - p0);
+      for (int j = 0; j < 4; ++j) CW[(tx + TX * i) * SC + ty + TY * j] = acc[i][j];
+    if (!leaf) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = tx + TX * i, c = ty + TY * j;
+          if (k < c0row && c < cols) C[F.prow[k] + (size_t)(c0 + c) * lda] -= acc[i][j];
+        }
+    }
+    // C -= Y W' (thread: r = tx + TX i, c = ty + TY j; row chunks of TK)
+    for (int p0 = pstart; p0 < rows; p0 += TK) {
+      const int pr = min(TK, rows - p0);
       __syncthreads();
       stage<T>(
-          kTl * kTl, [&](int e) -> T { return (e & (kTl - 1)) < pr ? yval(p0 + (e & (kTl - 1)), e >> 6) : T(0); },
-          [&](int e, T v) { Ys[(e & (kTl - 1)) * kTs + (e >> 6)] = v; });
+          TK * TK, [&](int e) -> T { return (e % TK) < pr ? yval(p0 + e % TK, e / TK) : T(0); },
+          [&](int e, T v) { Ys[(e % TK) * SK + e / TK] = v; });
       __syncthreads();
       T o[4][4];
 #pragma unroll
@@ -679,9 +717,9 @@ __device__ void node_apply(const T *P, int lda, T *C, int nt, int rows, int nref
       for (int k = 0; k < nref; ++k) {
         T y[4], ww[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) y[i] = Ys[(tx + 16 * i) * kTs + k];
+        for (int i = 0; i < 4; ++i) y[i] = Ys[(tx + TX * i) * SK + k];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) ww[j] = CW[k * kTs + ty + 16 * j];
+        for (int j = 0; j < 4; ++j) ww[j] = CW[k * SC + ty + TY * j];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -689,12 +727,12 @@ __device__ void node_apply(const T *P, int lda, T *C, int nt, int rows, int nref
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int r = tx + 16 * i;
+        const int r = tx + TX * i;
         if (r >= pr) continue;
         T *crow = C + F.prow[p0 + r];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int c = ty + 16 * j;
+          const int c = ty + TY * j;
           if (c < cols) crow[(size_t)(c0 + c) * lda] -= o[i][j];
         }
       }
@@ -703,11 +741,20 @@ __device__ void node_apply(const T *P, int lda, T *C, int nt, int rows, int nref
   }
 }
 
+template <class T>
+__device__ void node_apply(const T *P, int lda, T *C, int nt, int rows, int nref, bool leaf, const T *Tg, int b,
+                           Fixed<T> &F, T *R) {
+  if (nref <= 32)
+    node_apply_t<T, 32>(P, lda, C, nt, rows, nref, leaf, Tg, b, F, R);
+  else
+    node_apply_t<T, 64>(P, lda, C, nt, rows, nref, leaf, Tg, b, F, R);
+}
+
 // ---------------------------------------------------------------------------
 // CAQR of one matrix
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ void cta_caqr(const ca_batch_item_t &it, Fixed<T> &F, T *R, char *slot) {
+__device__ void cta_caqr(const ca_batch_item_t &it, Fixed<T> &F, T *R, int region_elems, char *slot) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   T *A = (T *)it.A;
   T *qtree = (T *)it.qtree;
@@ -730,7 +777,7 @@ __device__ void cta_caqr(const ca_batch_item_t &it, Fixed<T> &F, T *R, char *slo
       for (int p = tid; p < rows; p += kBT) F.prow[p] = r0 + p;
       __syncthreads();
       load_rows(P, lda, rows, bk, R, ld, F, false);
-      const int km = node_qr(R, ld, rows, bk, F, false, Tp + (size_t)j * b * b, b);
+      const int km = node_qr(R, ld, rows, bk, F, false, Tp + (size_t)j * b * b, b, region_elems);
       for (int k = warp; k < bk; k += kBW)
         for (int p = lane; p < rows; p += 32) P[r0 + p + (size_t)k * lda] = R[p + (size_t)k * ld];
       if (tid == 0) {
@@ -757,7 +804,7 @@ __device__ void cta_caqr(const ca_batch_item_t &it, Fixed<T> &F, T *R, char *slo
         const int rows = merge_rows(top[buf], cc[buf], start, cnt, F);
         const int ld = odd_ld(rows);
         load_rows(P, lda, rows, bk, R, ld, F, true);
-        const int km = node_qr(R, ld, rows, bk, F, true, Tp + (size_t)(nl + midx) * b * b, b);
+        const int km = node_qr(R, ld, rows, bk, F, true, Tp + (size_t)(nl + midx) * b * b, b, region_elems);
         for (int k = warp; k < bk; k += kBW)
           for (int p = lane; p < rows; p += 32)
             if (k >= F.fz[p]) P[F.prow[p] + (size_t)k * lda] = R[p + (size_t)k * ld];
@@ -842,7 +889,7 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BatchArgs a) {
     if (it.op == CA_BATCH_CALU)
       cta_calu<T>(it, F, R, a.region_elems, slot);
     else
-      cta_caqr<T>(it, F, R, slot);
+      cta_caqr<T>(it, F, R, a.region_elems, slot);
     __syncthreads();
     if (threadIdx.x == 0) {
       it.info[0] = F.info0;
@@ -869,8 +916,9 @@ double item_flops(const ca_batch_item_t &it) {
   const double m = it.m, n = it.n;
   const double k = m < n ? m : n;
   if (it.op == CA_BATCH_CALU) {
-    // m n k - (m + n) k^2 / 2 + k^3 / 3 multiply-adds, x 2 (LAPACK getrf count)
-    return m * n * k - (m + n) * k * k / 2.0 + k * k * k / 3.0;
+    // LAPACK getrf count: m n k - (m + n) k^2 / 2 + k^3 / 3 multiply-adds
+    // (m n^2 - n^3 / 3 flops for m >= n)
+    return 2.0 * (m * n * k - (m + n) * k * k / 2.0 + k * k * k / 3.0);
   }
   return 2.0 * m * n * n - 2.0 * n * n * n / 3.0;
 }
@@ -901,7 +949,7 @@ int item_needs(const ca_batch_item_t &it, size_t esz, size_t region_cap, size_t 
     }
     *slot = align256((size_t)4 * (2 * (size_t)nlmax * b + 2 * nlmax) + 16) + (size_t)b * b * esz;
   } else {
-    if (multi) need = std::max(need, (size_t)2 * kTl * kTs + (size_t)kTl * kTl);
+    if (multi) need = std::max(need, (size_t)3 * kTl * kTs);  // node_apply_t<T, 64>: 3 x 64 x 65 (the larger)
     *slot = (size_t)4 * 4 * nlmax;
   }
   if (need * esz > region_cap) return 0;

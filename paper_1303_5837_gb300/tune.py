@@ -81,7 +81,7 @@ def item_flops(op: str, m: int, n: int) -> float:
     """Standard flop counts: LU m n^2 - n^3 / 3 (m >= n), QR 2 m n^2 - 2 n^3 / 3."""
     if op == "lu":
         k = min(m, n)
-        return m * n * k - (m + n) * k * k / 2.0 + k ** 3 / 3.0
+        return 2.0 * (m * n * k - (m + n) * k * k / 2.0 + k ** 3 / 3.0)
     return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
 
 
@@ -132,7 +132,7 @@ def candidates(op: str, m: int, n: int, esz: int = 8):
     k = min(m, n)
     bs = sorted({b for b in (16, 32, 64) if b <= max(16, k)} | ({k} if k <= 128 else set()))
     for b in bs:
-        for L in (64, 128, 256):
+        for L in (64, 128, 256, 512):
             if L < min(b, k):
                 continue
             for name, lv in TREES.items():

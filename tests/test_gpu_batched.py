@@ -204,3 +204,40 @@ def test_batched_benchmark_mix(ca):
             R = torch.triu(F[:n])
             res = torch.linalg.norm(R.T @ R - A0.T @ A0) / torch.linalg.norm(A0) ** 2
         assert float(res) < 1e-13, (i, ops[i], m, n, float(res))
+
+
+CASES32 = CASES + [("qr", 4096, 128, 128, 128, [(0, BIN)]), ("lu", 4096, 128, 128, 128, [(0, BIN)])]
+
+
+def test_batched_fp32_matches_fp32_oracle(ca):
+    """FP32 batch against the FP32 build of the oracle (pivot decisions in
+    FP32 on both sides): pivots exactly wherever the oracle saw no near tie
+    (runner-up within 1e-4), factors and T within 1e-4 relative."""
+    hosts = [inputs.gaussian(c[1], c[2], 700 + i) for i, c in enumerate(CASES32)]
+    devs = [to_dev(A, torch.float32) for A in hosts]
+    bf = ca.BatchedFactor(devs, [c[0] for c in CASES32], [c[3] for c in CASES32],
+                          [ca.make_tree(c[4], c[5]) for c in CASES32])
+    bf.run()
+    torch.cuda.synchronize()
+    compared = 0
+    for i, (op, m, n, b, L, lv) in enumerate(CASES32):
+        got = devs[i].cpu().numpy()
+        if op == "lu":
+            LU_o, ipiv_o, info_o, nt = oracle.calu(hosts[i], b, oracle.make_tree(L, lv), dtype=np.float32)
+            if nt:
+                # a near tie decides a pivot by rounding: the GPU's own pivots
+                # must still give a valid factorization
+                perm, Lf, U = oracle.lu_unpack(got.astype(np.float64), bf.ipiv(i).cpu().numpy())
+                A64 = hosts[i]
+                assert np.linalg.norm(A64[perm] - Lf @ U) / np.linalg.norm(A64) < 1e-5, (op, m, n)
+                continue
+            compared += 1
+            assert np.array_equal(bf.ipiv(i).cpu().numpy(), ipiv_o), (op, m, n)
+            assert rel(got, LU_o) < 1e-4, (op, m, n, rel(got, LU_o))
+        else:
+            QR_o, T_o = oracle.caqr(hosts[i], b, oracle.make_tree(L, lv), dtype=np.float32)
+            compared += 1
+            assert rel(got, QR_o) < 1e-4, (op, m, n, rel(got, QR_o))
+            assert rel(bf.qtree(i).cpu().numpy()[: T_o.size], T_o) < 1e-4, (op, m, n)
+        assert bf.info(i).cpu().tolist() == [0, 0]
+    assert compared >= len(CASES32) - 8

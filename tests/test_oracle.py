@@ -354,3 +354,42 @@ def test_golden_tournament_example():
     tree = oracle.make_tree(g["leaf_rows"], [tuple(x) for x in g["levels"]])
     sel, _ = oracle.tslu_select(A, tree)
     assert sel.tolist() == g["selected"]
+
+
+# ---------------------------------------------------------------------------
+# the FP32 build of the oracle (same source, ORA_REAL=float): pinned to the
+# FP64 build, which is pinned above.  Where FP32 takes no near-tie decision,
+# its pivots must be the FP64 pivots and its factors the FP64 factors to FP32
+# accuracy; R of a QR is unique, so it must agree to FP32 accuracy anyway.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("m,n,b,L,levels", [(96, 96, 16, 32, [(0, 0)]), (300, 40, 40, 64, [(2, 1), (0, 0)]),
+                                            (200, 200, 32, 64, [(0, 1)])])
+def test_fp32_oracle_agrees_with_fp64(m, n, b, L, levels):
+    tree = oracle.make_tree(L, levels)
+    checked = 0
+    for seed in range(6):
+        A = inputs.gaussian(m, n, 4000 + seed)
+        LU64, ip64, _, _ = oracle.calu(A, b, tree)
+        LU32, ip32, _, nt32 = oracle.calu(A, b, tree, dtype=np.float32)
+        assert LU32.dtype == np.float32
+        if nt32 == 0:
+            checked += 1
+            assert np.array_equal(ip32, ip64)
+            assert np.linalg.norm(LU32 - LU64) / np.linalg.norm(LU64) < 2e-5
+        QR64, T64 = oracle.caqr(A, b, tree)
+        QR32, T32 = oracle.caqr(A, b, tree, dtype=np.float32)
+        k = min(m, n)
+        R64, R32 = np.triu(QR64[:k]), np.triu(QR32[:k])
+        assert np.linalg.norm(R32 - R64) / np.linalg.norm(R64) < 2e-5
+        assert np.linalg.norm(T32 - T64) / np.linalg.norm(T64) < 2e-5
+    assert checked >= 2
+
+
+def test_fp32_oracle_is_single_precision():
+    """Sums below FP32 resolution vanish in the FP32 build and not in FP64
+    (the build really computes in float): GEPP of [[1, 1], [1, 1 + 2^-30]]."""
+    A = np.array([[1.0, 1.0], [1.0, 1.0 + 2.0 ** -30]])
+    LU64, _, info64, _ = oracle.calu(A, 2, oracle.make_tree(2))
+    LU32, _, info32, _ = oracle.calu(A, 2, oracle.make_tree(2), dtype=np.float32)
+    assert LU64[1, 1] == 2.0 ** -30 and info64 == 0
+    assert LU32[1, 1] == 0.0 and info32 == 2

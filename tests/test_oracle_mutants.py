@@ -27,7 +27,7 @@ MUTANTS = {
                             "s = s - AT(A, lda, kb + l, kb + i) * AT(A, lda, kb + l, q);"),
     "schur_wrong_index": ("for (int l = 0; l < bk; ++l) s = s - AT(A, lda, i, kb + l) * AT(A, lda, kb + l, q);",
                           "for (int l = 1; l < bk; ++l) s = s - AT(A, lda, i, kb + l) * AT(A, lda, kb + l, q);"),
-    "householder_beta_sign": ("double beta = (alpha >= 0.0) ? -nrm : nrm;", "double beta = (alpha >= 0.0) ? nrm : -nrm;"),
+    "householder_beta_sign": ("real beta = (alpha >= 0.0) ? -nrm : nrm;", "real beta = (alpha >= 0.0) ? nrm : -nrm;"),
     "larft_missing_tau": ("AT(T, ldt, i, j) = -tau[j] * s;", "AT(T, ldt, i, j) = -s;"),
     "apply_t_not_transposed": ("for (int l = 0; l <= j; ++l) s = s + AT(T, ldt, l, j) * AT(Wk, k, l, q);",
                                "for (int l = 0; l <= j; ++l) s = s + AT(T, ldt, j, l) * AT(Wk, k, l, q);"),
