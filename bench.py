@@ -63,7 +63,7 @@ def parse():
     p.add_argument("--batch-count", type=int, default=4096, help="matrices of the batched workload")
     p.add_argument("--batch-steps", type=int, default=3)
     p.add_argument("--no-batch", action="store_true")
-    p.add_argument("--only-batch", default="", choices=["", "f64", "f32"],
+    p.add_argument("--only-batch", default="", choices=["", "f64", "f32", "ops"],
                    help="diagnostic: run only the batched workload in this precision")
     return p.parse_args()
 
@@ -230,6 +230,9 @@ def run_ours(a, rank: int, world: int, local: int):
     torch.cuda.set_device(dev)
     ca.load()
     if a.only_batch:
+        if a.only_batch == "ops":
+            print(json.dumps({"batched": {"operators": operator_diagnostics(a, ca, torch, dev)}}), flush=True)
+            return
         out = batched_run(a, ca, torch, torch.float64 if a.only_batch == "f64" else torch.float32, dev, rank,
                           world)
         if rank == 0:
@@ -329,6 +332,8 @@ def run_ours(a, rank: int, world: int, local: int):
         batched = {}
         for tname, tdt in (("f64", torch.float64), ("f32", torch.float32)):
             batched[tname] = batched_run(a, ca, torch, tdt, dev, rank, world)
+        if rank == 0:
+            batched["operators"] = operator_diagnostics(a, ca, torch, dev)
 
     # ---- end to end through the public API with host buffers --------------
     e2e = None
@@ -510,6 +515,53 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
                                        "update on the tensor cores"}
     for k, v in kernels_of.items():
         out[k]["kernels"] = v
+    return out
+
+
+OPERATOR_FORMS = [  # (name, panel width, leaf rows, levels, reduction operator)
+    ("gepp", 32, 4096, [(0, 0)], []),
+    ("calu", 64, 128, [(0, 0)], []),
+    ("2d_ml_calu_depth1", 64, 128, [(0, 0)], [(16, 32)]),
+    ("2d_ml_calu_depth2", 64, 256, [(0, 0)], [(32, 64), (8, 16)]),
+]
+
+
+def operator_diagnostics(a, ca, torch, dev, count=64, n=512):
+    """Stability of the reduction operators on `count` seeded N(0, 1)
+    matrices of order n, each form one batched launch: growth max|U| / max|A|,
+    normwise backward error ||P A - L U||_F / ||A||_F and max |L| (median and
+    worst over the sample), and the launch time.  GEPP is CALU with one leaf
+    holding every row (blocked GEPP)."""
+    gen = torch.Generator(device=dev).manual_seed(4242)
+    A0 = [torch.randn(n, n, dtype=torch.float64, device=dev, generator=gen).t() for _ in range(count)]
+    out = {"matrices": count, "n": n}
+    for name, b, L, lv, op in OPERATOR_FORMS:
+        mats = [A.clone() for A in A0]
+        bf = ca.BatchedFactor(mats, ["lu"] * count, [b] * count, [ca.make_tree(L, lv, op)] * count)
+        bf.run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        for M, A in zip(mats, A0):
+            M.copy_(A)
+        e0.record()
+        bf.run()
+        e1.record()
+        e1.synchronize()
+        growth, berr, lmax = [], [], []
+        for i, (F, A) in enumerate(zip(mats, A0)):
+            Lf = torch.tril(F, -1) + torch.eye(n, dtype=F.dtype, device=dev)
+            U = torch.triu(F)
+            perm = torch.arange(n, device=dev)
+            for j, p in enumerate(bf.ipiv(i).cpu().tolist()):
+                perm[[j, p - 1]] = perm[[p - 1, j]]
+            growth.append(float(U.abs().max() / A.abs().max()))
+            berr.append(float(torch.linalg.norm(A[perm] - Lf @ U) / torch.linalg.norm(A)))
+            lmax.append(float(Lf.abs().max()))
+        out[name] = {"b": b, "leaf_rows": L, "operator": op, "ms": e0.elapsed_time(e1),
+                     "growth_median": statistics.median(growth), "growth_max": max(growth),
+                     "berr_median": statistics.median(berr), "berr_max": max(berr),
+                     "lmax_max": max(lmax), "nonzero_info": int((bf.info_all != 0).sum())}
     return out
 
 

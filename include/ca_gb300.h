@@ -66,6 +66,19 @@ typedef struct {
   int fan_in[CA_MAX_LEVELS];  /* nodes per group at each level (>= 2 except  */
                               /* the last level, whose value is ignored)     */
   int style[CA_MAX_LEVELS];   /* CA_TREE_BINARY or CA_TREE_FLAT              */
+  /* Reduction operator of the tournament's nodes (LU only).  0: GEPP (the
+   * CALU base case).  1 or 2: the 2D multilevel CALU reduction (Algorithm
+   * 2D-ML-CALU, Sec. 3.2): every node -- a leaf, or the stacked candidate
+   * sets of a reduction step -- is factored by CALU of the level below with
+   * panel width op_b[0] over leaves of op_leaf_rows[0] rows and a binary
+   * tree; its own nodes use GEPP (depth 1) or, at depth 2, CALU with
+   * op_b[1] and op_leaf_rows[1] and GEPP below that.  The node's pivot rows
+   * are the first rows of that factorization.  Zero-initialize for GEPP.
+   * Only the batched entry points (CALU items) accept depth > 0; the others
+   * return CA_ERR_UNSUPPORTED. */
+  int op_depth;
+  int op_b[2];                /* 1 <= op_b[d] <= op_leaf_rows[d]              */
+  int op_leaf_rows[2];
 } ca_tree_t;
 
 /* return codes (negative small values -i name a bad argument i) */

@@ -39,6 +39,9 @@ class _Tree(ctypes.Structure):
         ("nlevels", ctypes.c_int),
         ("fan_in", ctypes.c_int * MAXLEV),
         ("style", ctypes.c_int * MAXLEV),
+        ("op_depth", ctypes.c_int),
+        ("op_b", ctypes.c_int * 2),
+        ("op_leaf_rows", ctypes.c_int * 2),
     ]
 
 
@@ -94,11 +97,15 @@ def _declare(lib):
     return lib
 
 
-def make_tree(leaf_rows: int, levels=((0, BINARY),)) -> dict:
+def make_tree(leaf_rows: int, levels=((0, BINARY),), op=()) -> dict:
     """A reduction tree: leaves of ``leaf_rows`` rows; ``levels`` is a list of
     (fan_in, style) from the bottom up; the last level merges all remaining
-    nodes whatever its fan_in says."""
-    return {"leaf_rows": int(leaf_rows), "levels": [(int(f), int(s)) for f, s in levels]}
+    nodes whatever its fan_in says.  ``op``: the reduction operator of the
+    tournament's nodes, () for GEPP, or up to two (b, leaf_rows) pairs from
+    the top down for the 2D multilevel CALU operator (each node factored by
+    CALU with that block size over a binary tree of such leaves)."""
+    return {"leaf_rows": int(leaf_rows), "levels": [(int(f), int(s)) for f, s in levels],
+            "op": [(int(b), int(L)) for b, L in op]}
 
 
 def _ctree(tree: dict) -> _Tree:
@@ -111,6 +118,13 @@ def _ctree(tree: dict) -> _Tree:
     for i, (f, s) in enumerate(lv):
         t.fan_in[i] = f
         t.style[i] = s
+    op = tree.get("op", [])
+    if len(op) > 2:
+        raise ValueError("operator depth 0..2")
+    t.op_depth = len(op)
+    for d, (b, L) in enumerate(op):
+        t.op_b[d] = b
+        t.op_leaf_rows[d] = L
     return t
 
 

@@ -63,6 +63,14 @@ typedef struct {
   int nlevels;
   int fan_in[ORA_MAXLEV];
   int style[ORA_MAXLEV];
+  /* reduction operator of the tournament's nodes (CALU only): 0 = GEPP;
+   * d = 1, 2: CALU of the node's rows with panel width op_b[0] over leaves
+   * of op_leaf_rows[0] rows and a binary tree, whose own nodes use the
+   * operator of depth d - 1 with (op_b[1], op_leaf_rows[1]) -- the 2D
+   * multilevel CALU reduction (Algorithm 2D-ML-CALU, Sec. 3.2) */
+  int op_depth;
+  int op_b[2];
+  int op_leaf_rows[2];
 } ora_tree;
 
 #define AT(M, ld, i, j) (M)[(size_t)(j) * (size_t)(ld) + (size_t)(i)]
@@ -280,6 +288,52 @@ int ora_getf2(int m, int n, real *A, int lda, int *ipiv, long *nearties) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* The reduction operator of a tournament node                              */
+/* ------------------------------------------------------------------------ */
+
+int ora_calu(int m, int n, real *A, int lda, int b, const ora_tree *t, int *ipiv, long *nearties);
+
+/* Valid operator spec: depth 0..2, each used level with 1 <= b <= leaf rows. */
+static int op_valid(const ora_tree *t) {
+  if (t->op_depth < 0 || t->op_depth > 2) return 0;
+  for (int d = 0; d < t->op_depth; ++d)
+    if (t->op_b[d] < 1 || t->op_leaf_rows[d] < t->op_b[d]) return 0;
+  return 1;
+}
+
+/* Factors the r x c node block W (ld ldw) in place with the tree's operator
+ * and permutes perm with its rows (as gepp_block does): GEPP at depth 0;
+ * otherwise CALU of the block (Algorithm 2D-ML-CALU: a node -- a leaf, or
+ * the stacked candidate sets of a reduction step -- is factored by the
+ * multilevel CALU of the level below, with that level's block size and a
+ * binary tree over its row blocks).  The first min(r, c) labels of perm are
+ * then the node's pivot rows in pivot order. */
+static int node_factor(int r, int c, real *W, int ldw, int *perm, const ora_tree *t, long *nearties) {
+  if (t->op_depth <= 0) return gepp_block(r, c, W, ldw, perm, nearties);
+  ora_tree in;
+  memset(&in, 0, sizeof in);
+  in.leaf_rows = t->op_leaf_rows[0];
+  in.nlevels = 1;
+  in.fan_in[0] = 0;
+  in.style[0] = ORA_BINARY;
+  in.op_depth = t->op_depth - 1;
+  in.op_b[0] = t->op_b[1];
+  in.op_leaf_rows[0] = t->op_leaf_rows[1];
+  int k = r < c ? r : c;
+  int *ipiv = (int *)malloc(sizeof(int) * (size_t)(k > 0 ? k : 1));
+  if (!ipiv) return -1000;
+  int info = ora_calu(r, c, W, ldw, t->op_b[0], &in, ipiv, nearties);
+  for (int i = 0; i < k && info >= 0; ++i) {
+    int sw = ipiv[i] - 1; /* the row swapped with row i */
+    int ti = perm[i];
+    perm[i] = perm[sw];
+    perm[sw] = ti;
+  }
+  free(ipiv);
+  return info;
+}
+
+/* ------------------------------------------------------------------------ */
 /* TSLU: tournament pivoting over the reduction tree                        */
 /* ------------------------------------------------------------------------ */
 
@@ -291,7 +345,7 @@ int ora_getf2(int m, int n, real *A, int lda, int *ipiv, long *nearties) {
  * order) and GEPP picks min(sum, b) of them (Sec. 3.2, reduction steps). */
 int ora_tslu_select(int m, int b, const real *P, int ldp, const ora_tree *t, int *sel,
                     long *nearties) {
-  if (m < 1 || b < 1 || t->leaf_rows < b) return -1;
+  if (m < 1 || b < 1 || t->leaf_rows < b || !op_valid(t)) return -1;
   int L = t->leaf_rows;
   int nl = (m + L - 1) / L;
   ora_plan plan;
@@ -316,7 +370,7 @@ int ora_tslu_select(int m, int b, const real *P, int ldp, const ora_tree *t, int
     for (int q = 0; q < b; ++q)
       for (int i = 0; i < rows; ++i) AT(W, rows, i, q) = AT(P, ldp, r0 + i, q);
     for (int i = 0; i < rows; ++i) perm[i] = r0 + i;
-    gepp_block(rows, b, W, rows, perm, nearties);
+    if (node_factor(rows, b, W, rows, perm, t, nearties) < 0) return -3;
     int c = rows < b ? rows : b;
     cand[j] = (int *)malloc(sizeof(int) * (size_t)c);
     memcpy(cand[j], perm, sizeof(int) * (size_t)c);
@@ -344,7 +398,7 @@ int ora_tslu_select(int m, int b, const real *P, int ldp, const ora_tree *t, int
           perm[at] = cand[ch][i];
           at++;
         }
-      gepp_block(rows, b, W, rows, perm, nearties);
+      if (node_factor(rows, b, W, rows, perm, t, nearties) < 0) return -3;
       int c = rows < b ? rows : b;
       nc[o] = (int *)malloc(sizeof(int) * (size_t)c);
       memcpy(nc[o], perm, sizeof(int) * (size_t)c);
@@ -384,7 +438,7 @@ int ora_tslu_select(int m, int b, const real *P, int ldp, const ora_tree *t, int
  * negative on a bad argument. */
 int ora_calu(int m, int n, real *A, int lda, int b, const ora_tree *t, int *ipiv,
              long *nearties) {
-  if (m < 0 || n < 0 || lda < (m > 1 ? m : 1) || b < 1 || t->leaf_rows < b) return -1;
+  if (m < 0 || n < 0 || lda < (m > 1 ? m : 1) || b < 1 || t->leaf_rows < b || !op_valid(t)) return -1;
   int K = m < n ? m : n;
   int info = 0;
   int *sel = (int *)malloc(sizeof(int) * (size_t)(b + 1));
@@ -819,7 +873,7 @@ long long ora_caqr_tcount(int m, int n, int b, const ora_tree *t) {
  * trailing columns are updated by the leaves' and merges' Q^T (Algorithm
  * ML-CAQR with one level: UPFACT then UPELIM). */
 int ora_caqr(int m, int n, real *A, int lda, int b, const ora_tree *t, real *T) {
-  if (m < n || n < 0 || lda < (m > 1 ? m : 1) || b < 1 || t->leaf_rows < b) return -1;
+  if (m < n || n < 0 || lda < (m > 1 ? m : 1) || b < 1 || t->leaf_rows < b || t->op_depth != 0) return -1;
   size_t off = 0;
   for (int kb = 0; kb < n; kb += b) {
     int bk = (n - kb < b) ? n - kb : b;
@@ -838,7 +892,7 @@ int ora_caqr(int m, int n, real *A, int lda, int b, const ora_tree *t, real *T) 
  * panel by panel, then x = R^{-1} (Q^T B)[0:n] in B's top n rows. */
 int ora_geqrs(int m, int n, int nrhs, const real *QR, int lda, int b, const ora_tree *t,
               const real *T, real *B, int ldb) {
-  if (m < n || b < 1 || t->leaf_rows < b) return -1;
+  if (m < n || b < 1 || t->leaf_rows < b || t->op_depth != 0) return -1;
   size_t off = 0;
   for (int kb = 0; kb < n; kb += b) {
     int bk = (n - kb < b) ? n - kb : b;

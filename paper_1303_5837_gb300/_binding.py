@@ -44,6 +44,9 @@ class ca_tree_t(ctypes.Structure):
         ("nlevels", ctypes.c_int),
         ("fan_in", ctypes.c_int * MAX_LEVELS),
         ("style", ctypes.c_int * MAX_LEVELS),
+        ("op_depth", ctypes.c_int),
+        ("op_b", ctypes.c_int * 2),
+        ("op_leaf_rows", ctypes.c_int * 2),
     ]
 
 
@@ -62,10 +65,19 @@ class ca_batch_item_t(ctypes.Structure):
     ]
 
 
-def make_tree(leaf_rows: int, levels=((0, BINARY),)) -> ca_tree_t:
+def make_tree(leaf_rows: int, levels=((0, BINARY),), op=()) -> ca_tree_t:
     """Reduction tree: leaves of ``leaf_rows`` rows, then ``levels`` as
-    (fan_in, style) pairs from the bottom up (the last level merges all)."""
+    (fan_in, style) pairs from the bottom up (the last level merges all).
+    ``op``: the nodes' reduction operator, () for GEPP or up to two
+    (b, leaf_rows) pairs for the 2D multilevel CALU operator (batched CALU)."""
     t = ca_tree_t()
+    op = list(op)
+    if len(op) > 2:
+        raise ValueError("operator depth 0..2")
+    t.op_depth = len(op)
+    for d, (ob, oL) in enumerate(op):
+        t.op_b[d] = int(ob)
+        t.op_leaf_rows[d] = int(oL)
     t.leaf_rows = int(leaf_rows)
     levels = list(levels)
     if not 1 <= len(levels) <= MAX_LEVELS:

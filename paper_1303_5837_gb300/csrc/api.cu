@@ -50,6 +50,7 @@ int lu_shape(int m, int n, int b, const ca_tree_t *tree, int *nl_max) {
   if (n < 0) return -2;
   if (b < 1) return -5;
   if (check_tree(tree, b)) return -6;
+  if (tree->op_depth != 0) return CA_ERR_UNSUPPORTED;  // the 2D operator runs in the batched path
   int K = m < n ? m : n;
   *nl_max = 1;
   if (K == 0) return CA_OK;
@@ -68,6 +69,7 @@ int qr_shape(int m, int n, int b, const ca_tree_t *tree, int *nl_max, size_t *qb
   if (n < 0 || n > m) return -2;
   if (b < 1) return -5;
   if (check_tree(tree, b)) return -6;
+  if (tree->op_depth != 0) return CA_ERR_UNSUPPORTED;  // no pivoting in QR
   *nl_max = 1;
   *qbytes = 0;
   if (n == 0) return CA_OK;
@@ -501,6 +503,7 @@ int calu_gesv_mixed(int n, int nrhs, const double *A, int lda, int b, const ca_t
   if (lda < (n > 1 ? n : 1)) return -4;
   if (b < 1) return -5;
   if (check_tree(tree, b)) return -6;
+  if (tree->op_depth != 0) return CA_ERR_UNSUPPORTED;
   if (slices < 1 || slices > 8) return -7;
   if (n > 0 && !LU) return -9;
   if (ldlu < (n > 1 ? n : 1)) return -10;

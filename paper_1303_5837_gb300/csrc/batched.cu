@@ -74,7 +74,9 @@ template <class T>
 struct Fixed {
   Plan plan;
   int prow[kBMaxRows];  // panel row of each node row
-  int fz[kBMaxRows];    // merge rows: child-local index t (zeros left of column t)
+  int fz[kBMaxRows];    // merge rows: child-local index t (zeros left of column t);
+                        // LU with the 2D operator: labels of the level-1 scratch rows
+  int lab2[kBMaxRows];  // labels of the level-2 scratch rows (2D operator)
   int sel[kBMaxB], rev_top[kBMaxB], top_c[kBMaxB], far_c[kBMaxB];
   int perm_src[2 * kBMaxB], perm_dst[2 * kBMaxB];
   int iscal[16];
@@ -114,11 +116,11 @@ __device__ __forceinline__ void stage(int total, Ld ld, St st) {
 
 // ---------------------------------------------------------------------------
 // GEPP on the node tile (rows x bk, ld), rows permuted physically with their
-// labels in F.prow; first maximum of |a| in the current order.  Returns the
+// labels lab[]; first maximum of |a| in the current order.  Returns the
 // number of steps, min(rows, bk).
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ int node_gepp(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool root, int kb) {
+__device__ int node_gepp(T *tile, int ld, int rows, int bk, int *lab, Fixed<T> &F, bool root, int kb) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int kmax = min(rows, bk);
   for (int j = 0; j < kmax; ++j) {
@@ -146,9 +148,9 @@ __device__ int node_gepp(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool ro
         tile[j + (size_t)k * ld] = t;
       }
       if (tid == 0) {
-        int t = F.prow[p];
-        F.prow[p] = F.prow[j];
-        F.prow[j] = t;
+        int t = lab[p];
+        lab[p] = lab[j];
+        lab[j] = t;
       }
       __syncthreads();
     }
@@ -164,6 +166,192 @@ __device__ int node_gepp(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool ro
     __syncthreads();
   }
   return kmax;
+}
+
+// ---------------------------------------------------------------------------
+// The 2D multilevel CALU reduction operator (Algorithm 2D-ML-CALU): a node
+// tile (rows x c, labels lab[]) is factored by CALU of the level below --
+// panels of op_b[level] columns; each panel's pivots chosen by a tournament
+// over leaves of op_leaf_rows[level] tile rows and a binary tree, whose
+// nodes (copies of the current rows in the scratch tile scr) are factored by
+// the operator one level further down (GEPP at the bottom); the chosen rows
+// swapped to the top (all c columns, labels with them), then eliminated
+// without further pivoting.  The first min(rows, c) labels are the node's
+// pivot rows in pivot order and the top of the tile holds L \ U of them.
+// wsi: the global candidate buffers of this level (and, after them, of the
+// levels below).
+// ---------------------------------------------------------------------------
+// one level's buffers: two candidate lists (nodes x panel width <= 2 x
+// kBMaxRows) and two count lists
+constexpr int kOpCandList = 2 * kBMaxRows;
+constexpr int kOpCand = 2 * kOpCandList + 2 * kBMaxRows;
+
+// Elimination steps j0 <= j < j1 of the tile without pivot search (zero
+// pivot: no scaling, no update; reported at the root).
+template <class T>
+__device__ void elim_nopiv(T *tile, int ld, int rows, int c, int j0, int j1, Fixed<T> &F, bool root, int kb) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = j0; j < j1; ++j) {
+    if (tid == 0) {
+      const T piv = tile[j + (size_t)j * ld];
+      F.iscal[1] = (piv == T(0));
+      if (piv == T(0) && root && F.info0 == 0) F.info0 = kb + j + 1;
+      if (piv != T(0)) F.scal[0] = T(1) / piv;
+    }
+    __syncthreads();
+    if (F.iscal[1]) continue;
+    const T rinv = F.scal[0];
+    T *cj = tile + (size_t)j * ld;
+    for (int q = j + 1 + tid; q < rows; q += kBT) cj[q] *= rinv;
+    __syncthreads();
+    for (int k = j + 1 + warp; k < c; k += kBW) {
+      const T u = tile[j + (size_t)k * ld];
+      T *ck = tile + (size_t)k * ld;
+      for (int q = j + 1 + lane; q < rows; q += 32) ck[q] = fma(-cj[q], u, ck[q]);
+    }
+    __syncthreads();
+  }
+}
+
+template <class T, int D>
+__device__ int node_factor(T *tile, int ld, int rows, int c, int *lab, Fixed<T> &F, bool root, int kb,
+                           const ca_tree_t &tr, int level, T *scr, int *wsi) {
+  if constexpr (D == 0) {
+    return node_gepp(tile, ld, rows, c, lab, F, root, kb);
+  } else {
+    const int tid = threadIdx.x;
+    const int b1 = tr.op_b[level], L1 = tr.op_leaf_rows[level];
+    int *slab = (level == 0) ? F.fz : F.lab2;  // labels of the scratch rows: tile positions
+    int *cand[2] = {wsi, wsi + kOpCandList};
+    int *ncand[2] = {wsi + 2 * kOpCandList, wsi + 2 * kOpCandList + kBMaxRows};
+    const int K = min(rows, c);
+    for (int k0 = 0; k0 < K; k0 += b1) {
+      const int c1 = min(b1, K - k0);
+      const int r1 = rows - k0;
+      const int nl1 = (r1 + L1 - 1) / L1;
+      // copies rows slab[0..rr) of tile columns k0..k0+c1 into the scratch tile
+      auto gather = [&](int rr, int ldS) {
+        for (int e = tid; e < rr * c1; e += kBT) {
+          const int q = e / rr, p = e - q * rr;
+          scr[p + (size_t)q * ldS] = tile[slab[p] + (size_t)(k0 + q) * ld];
+        }
+        __syncthreads();
+      };
+      // ---- tournament: leaves ----
+      for (int j = 0; j < nl1; ++j) {
+        const int rr = min(L1, r1 - j * L1), ldS = odd_ld(rr);
+        for (int p = tid; p < rr; p += kBT) slab[p] = k0 + j * L1 + p;
+        __syncthreads();
+        gather(rr, ldS);
+        const int km = node_factor<T, D - 1>(scr, ldS, rr, c1, slab, F, false, kb, tr, level + 1,
+                                             scr + (size_t)ldS * c1, wsi + kOpCand);
+        for (int p = tid; p < km; p += kBT) cand[0][j * c1 + p] = slab[p];
+        if (tid == 0) ncand[0][j] = km;
+        __syncthreads();
+      }
+      // ---- tournament: binary rounds ----
+      int cur = nl1, buf = 0;
+      while (cur > 1) {
+        const int nout = (cur + 1) / 2;
+        for (int o = 0; o < nout; ++o) {
+          if (2 * o + 1 >= cur) {
+            const int cc = ncand[buf][2 * o];
+            for (int p = tid; p < cc; p += kBT) cand[buf ^ 1][o * c1 + p] = cand[buf][2 * o * c1 + p];
+            if (tid == 0) ncand[buf ^ 1][o] = cc;
+            __syncthreads();
+            continue;
+          }
+          const int na = ncand[buf][2 * o], rr = na + ncand[buf][2 * o + 1], ldS = odd_ld(rr);
+          for (int p = tid; p < rr; p += kBT)
+            slab[p] = p < na ? cand[buf][2 * o * c1 + p] : cand[buf][(2 * o + 1) * c1 + p - na];
+          __syncthreads();
+          gather(rr, ldS);
+          const int km = node_factor<T, D - 1>(scr, ldS, rr, c1, slab, F, false, kb, tr, level + 1,
+                                               scr + (size_t)ldS * c1, wsi + kOpCand);
+          for (int p = tid; p < km; p += kBT) cand[buf ^ 1][o * c1 + p] = slab[p];
+          if (tid == 0) ncand[buf ^ 1][o] = km;
+          __syncthreads();
+        }
+        buf ^= 1;
+        cur = nout;
+      }
+      // ---- LAPACK swap sequence moving the chosen rows to k0.. (tid 0) ----
+      if (tid == 0) {
+        for (int t = 0; t < c1; ++t) {
+          F.sel[t] = cand[buf][t] - k0;
+          F.rev_top[t] = t;
+          F.top_c[t] = t;
+          F.far_c[t] = F.sel[t];
+        }
+        for (int i = 0; i < c1; ++i) {
+          const int lb = F.sel[i];
+          int pp, fslot = -1;
+          if (lb < c1) {
+            const int rv = F.rev_top[lb];
+            if (rv >= 0) {
+              pp = rv;
+            } else {
+              fslot = -rv - 1;
+              pp = F.sel[fslot];
+            }
+          } else {
+            pp = lb;
+            fslot = i;
+          }
+          F.perm_dst[i] = pp;
+          if (pp == i) continue;
+          const int ci = F.top_c[i];
+          F.top_c[i] = lb;
+          if (pp < c1) {
+            F.top_c[pp] = ci;
+            F.rev_top[ci] = pp;
+          } else {
+            F.far_c[fslot] = ci;
+            F.rev_top[ci] = -(fslot + 1);
+          }
+          if (lb < c1) F.rev_top[lb] = i;
+        }
+      }
+      __syncthreads();
+      // ---- apply the swaps to every column (in order), labels with them ----
+      for (int q = tid; q < c; q += kBT) {
+        T *col = tile + (size_t)q * ld + k0;
+        for (int i = 0; i < c1; ++i) {
+          const int pp = F.perm_dst[i];
+          if (pp != i) {
+            const T t = col[i];
+            col[i] = col[pp];
+            col[pp] = t;
+          }
+        }
+      }
+      if (tid == 0)
+        for (int i = 0; i < c1; ++i) {
+          const int pp = F.perm_dst[i];
+          if (pp != i) {
+            const int t = lab[k0 + i];
+            lab[k0 + i] = lab[k0 + pp];
+            lab[k0 + pp] = t;
+          }
+        }
+      __syncthreads();
+      // ---- eliminate the panel's columns without further pivoting ----
+      elim_nopiv(tile, ld, rows, c, k0, k0 + c1, F, root, kb);
+    }
+    return K;
+  }
+}
+
+// Node factorization with the tree's operator (GEPP, or the 2D operator of
+// depth 1 or 2); scr: shared scratch after the node tile, wsi: the slot's
+// candidate buffers of the operator.
+template <class T>
+__device__ int node_op(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool root, int kb, const ca_tree_t &tr,
+                       int *wsi) {
+  T *scr = tile + (size_t)ld * bk;
+  if (tr.op_depth == 1) return node_factor<T, 1>(tile, ld, rows, bk, F.prow, F, root, kb, tr, 0, scr, wsi);
+  if (tr.op_depth == 2) return node_factor<T, 2>(tile, ld, rows, bk, F.prow, F, root, kb, tr, 0, scr, wsi);
+  return node_gepp(tile, ld, rows, bk, F.prow, F, root, kb);
 }
 
 // Loads the node rows F.prow[0..rows) of panel columns 0..bk-1 into the tile;
@@ -199,6 +387,7 @@ __device__ void cta_calu(const ca_batch_item_t &it, Fixed<T> &F, T *R, int regio
   int *cand[2] = {(int *)slot, (int *)slot + (size_t)nlmax * b};
   int *ncand[2] = {cand[1] + (size_t)nlmax * b, cand[1] + (size_t)nlmax * b + nlmax};
   T *lu11 = (T *)(((uintptr_t)(ncand[1] + nlmax) + 15) & ~(uintptr_t)15);
+  int *wsi = (int *)(((uintptr_t)(lu11 + (size_t)b * b) + 15) & ~(uintptr_t)15);  // operator buffers
   for (int kb = 0; kb < K; kb += b) {
     const int bk = min(b, K - kb), mk = m - kb;
     T *P = A + kb + (size_t)kb * lda;
@@ -212,7 +401,7 @@ __device__ void cta_calu(const ca_batch_item_t &it, Fixed<T> &F, T *R, int regio
       for (int p = tid; p < rows; p += kBT) F.prow[p] = r0 + p;
       __syncthreads();
       load_rows(P, lda, rows, bk, R, ld, F, false);
-      const int km = node_gepp(R, ld, rows, bk, F, nrounds == 0, kb);
+      const int km = node_op(R, ld, rows, bk, F, nrounds == 0, kb, it.tree, wsi);
       for (int p = tid; p < km; p += kBT) cand[0][(size_t)j * b + p] = F.prow[p];
       if (tid == 0) ncand[0][j] = km;
       if (nrounds == 0)
@@ -247,7 +436,7 @@ __device__ void cta_calu(const ca_batch_item_t &it, Fixed<T> &F, T *R, int regio
         __syncthreads();
         const int ld = odd_ld(rows);
         load_rows(P, lda, rows, bk, R, ld, F, false);
-        const int km = node_gepp(R, ld, rows, bk, F, last, kb);
+        const int km = node_op(R, ld, rows, bk, F, last, kb, it.tree, wsi);
         for (int p = tid; p < km; p += kBT) cout[(size_t)o * b + p] = F.prow[p];
         if (tid == 0) nout[o] = km;
         if (last)
@@ -942,12 +1131,25 @@ int item_needs(const ca_batch_item_t &it, size_t esz, size_t region_cap, size_t 
   const bool multi = it.n > bk;  // a trailing update follows the first panel
   if (multi && bk > kBMultiB) return 0;
   if (it.op == CA_BATCH_CALU) {
+    // the 2D operator's scratch tiles after the node tile (level d: a leaf of
+    // op_leaf_rows[d] rows or a binary merge of two op_b[d]-row sets)
+    size_t scr = 0;
+    int pr = rows, pw = bk;
+    for (int d = 0; d < it.tree.op_depth; ++d) {
+      const int w = std::min(it.tree.op_b[d], pw);
+      const int r = std::min(std::max(it.tree.op_leaf_rows[d], 2 * w), pr);
+      scr += (size_t)odd_ld(r) * w;
+      pr = r;
+      pw = w;
+    }
+    need = std::max(need, (size_t)odd_ld(rows) * bk + scr);
     need = std::max(need, (size_t)bk * bk + bk + 33 * (size_t)bk);  // L21 with 32-row tiles at least
     if (multi) {
       need = std::max(need, (size_t)bk * bk + 32 * (size_t)bk);
       need = std::max(need, (size_t)2 * kGk * kTl);
     }
-    *slot = align256((size_t)4 * (2 * (size_t)nlmax * b + 2 * nlmax) + 16) + (size_t)b * b * esz;
+    *slot = align256((size_t)4 * (2 * (size_t)nlmax * b + 2 * nlmax) + 16) + (size_t)b * b * esz + 16 +
+            (size_t)4 * kOpCand * it.tree.op_depth;
   } else {
     if (multi) need = std::max(need, (size_t)3 * kTl * kTs);  // node_apply_t<T, 64>: 3 x 64 x 65 (the larger)
     *slot = (size_t)4 * 4 * nlmax;
@@ -991,6 +1193,12 @@ int ca_batched_plan(int count, const ca_batch_item_t *items, int dtype, void *pl
     if (!it.A) return CA_ERR_BATCH_ITEM;
     if (it.op == CA_BATCH_CALU && !it.ipiv) return CA_ERR_BATCH_ITEM;
     if (it.op == CA_BATCH_CAQR && !it.qtree) return CA_ERR_BATCH_ITEM;
+    if (it.op == CA_BATCH_CAQR && it.tree.op_depth != 0) return CA_ERR_BATCH_ITEM;  // no pivoting in QR
+    if (it.tree.op_depth < 0 || it.tree.op_depth > 2) return CA_ERR_BATCH_ITEM;
+    for (int d = 0; d < it.tree.op_depth; ++d)
+      if (it.tree.op_b[d] < 1 || it.tree.op_b[d] > kBMaxB || it.tree.op_leaf_rows[d] < it.tree.op_b[d] ||
+          it.tree.op_leaf_rows[d] > kBMaxRows)
+        return CA_ERR_BATCH_ITEM;
     size_t e = 0, s = 0;
     if (!item_needs(it, esz, cap, &e, &s)) return CA_ERR_UNSUPPORTED;
     region = std::max(region, e * esz);

@@ -56,22 +56,33 @@ def ipiv_from_order(order, k, n=None):
     return ipiv
 
 
-def _merge(panel, cands, b):
+def _merge(panel, cands, b, op=()):
+    """The node operator: GEPP (op empty), or exact CALU of the node's rows
+    with block op[0][0], leaves of op[0][1] rows, a binary tree, and the
+    operator op[1:] at its own nodes (the 2D multilevel CALU reduction)."""
     rows = [panel[i] for i in cands]
-    lab, _, tie = gepp(rows, b)
     k = min(len(rows), b)
+    if not op:
+        lab, _, tie = gepp(rows, b)
+    else:
+        (b1, L1), inner = op[0], op[1:]
+        ipiv, _, tie = calu(rows, b1, L1, [(0, 0)], inner)
+        lab = list(range(len(rows)))
+        for i, p in enumerate(ipiv):
+            lab[i], lab[p - 1] = lab[p - 1], lab[i]
     return [cands[l] for l in lab[:k]], tie
 
 
-def tournament(panel, b, leaf_rows, levels):
+def tournament(panel, b, leaf_rows, levels, op=()):
     """Rows selected by tournament pivoting; ``levels`` = [(fan_in, style)]
-    with style 0 = binary, 1 = flat.  Returns (selected rows, tie_seen)."""
+    with style 0 = binary, 1 = flat; ``op`` the node operator (see _merge).
+    Returns (selected rows, tie_seen)."""
     m = len(panel)
     tie = False
     nodes = []
     for r0 in range(0, m, leaf_rows):
         rows = list(range(r0, min(r0 + leaf_rows, m)))
-        sel, t = _merge(panel, rows, b)
+        sel, t = _merge(panel, rows, b, op)
         tie |= t
         nodes.append(sel)
     for li, (f, style) in enumerate(levels):
@@ -84,7 +95,7 @@ def tournament(panel, b, leaf_rows, levels):
                 if len(grp) == 1:
                     out.append(grp[0])
                 else:
-                    sel, t = _merge(panel, [i for c in grp for i in c], b)
+                    sel, t = _merge(panel, [i for c in grp for i in c], b, op)
                     tie |= t
                     out.append(sel)
             else:
@@ -93,7 +104,7 @@ def tournament(panel, b, leaf_rows, levels):
                     nxt = []
                     for i in range(0, len(cur), 2):
                         if i + 1 < len(cur):
-                            sel, t = _merge(panel, cur[i] + cur[i + 1], b)
+                            sel, t = _merge(panel, cur[i] + cur[i + 1], b, op)
                             tie |= t
                             nxt.append(sel)
                         else:
@@ -105,7 +116,7 @@ def tournament(panel, b, leaf_rows, levels):
     return nodes[0], tie
 
 
-def calu(A, b, leaf_rows, levels):
+def calu(A, b, leaf_rows, levels, op=()):
     """Exact CALU: returns (ipiv 1-based, LU rows in LAPACK layout, tie_seen)."""
     W = [list(r) for r in A]
     m = len(W)
@@ -116,7 +127,7 @@ def calu(A, b, leaf_rows, levels):
     for kb in range(0, K, b):
         bk = min(b, K - kb)
         panel = [row[kb:kb + bk] for row in W[kb:]]
-        sel, t = tournament(panel, bk, leaf_rows, levels)
+        sel, t = tournament(panel, bk, leaf_rows, levels, op)
         tie |= t
         piv = ipiv_from_order(sel, bk, m - kb)
         for i, p in enumerate(piv):

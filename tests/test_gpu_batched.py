@@ -241,3 +241,44 @@ def test_batched_fp32_matches_fp32_oracle(ca):
             assert rel(bf.qtree(i).cpu().numpy()[: T_o.size], T_o) < 1e-4, (op, m, n)
         assert bf.info(i).cpu().tolist() == [0, 0]
     assert compared >= len(CASES32) - 8
+
+
+# (m, n, b, leaf_rows, levels, operator) -- CALU items with the 2D multilevel
+# reduction operator of depth 1 and 2
+OP_CASES = [
+    (256, 256, 32, 64, [(0, BIN)], [(8, 16)]),
+    (300, 300, 64, 128, [(2, BIN), (0, FLAT)], [(16, 32)]),
+    (512, 512, 64, 256, [(0, BIN)], [(32, 64), (8, 16)]),
+    (2000, 64, 64, 256, [(0, BIN)], [(16, 64), (4, 8)]),
+    (777, 40, 40, 50, [(3, FLAT), (0, BIN)], [(8, 24)]),
+    (100, 100, 16, 16, [(0, BIN)], [(16, 16)]),      # one inner panel per node: GEPP at the nodes
+]
+
+
+def test_batched_2d_operator_matches_oracle(ca):
+    hosts = [inputs.gaussian(m, n, 1300 + i) for i, (m, n, *_r) in enumerate(OP_CASES)]
+    devs = [to_dev(A) for A in hosts]
+    bf = ca.BatchedFactor(devs, ["lu"] * len(OP_CASES), [c[2] for c in OP_CASES],
+                          [ca.make_tree(c[3], c[4], c[5]) for c in OP_CASES])
+    bf.run()
+    torch.cuda.synchronize()
+    for i, (m, n, b, L, lv, op) in enumerate(OP_CASES):
+        LU_o, ipiv_o, info_o, nt = oracle.calu(hosts[i], b, oracle.make_tree(L, lv, op))
+        assert nt == 0
+        assert np.array_equal(bf.ipiv(i).cpu().numpy(), ipiv_o), (m, n, b, op)
+        assert rel(devs[i].cpu().numpy(), LU_o) < 1e-12, (m, n, b, op)
+        assert bf.info(i).cpu().tolist() == [0, 0]
+    # the operator changes the pivots of a genuine case
+    plain = ca.BatchedFactor([to_dev(hosts[2])], ["lu"], [64], [ca.make_tree(256)])
+    plain.run()
+    torch.cuda.synchronize()
+    assert not torch.equal(plain.ipiv(0), bf.ipiv(2))
+
+
+def test_batched_2d_operator_rejected_elsewhere(ca):
+    t = ca.make_tree(64, op=[(8, 16)])
+    A = to_dev(inputs.gaussian(128, 128, 1))
+    with pytest.raises(ca.CaError):
+        ca.calu_factor(A, 32, t)
+    with pytest.raises(ca.CaError):
+        ca.BatchedFactor([A], ["qr"], [32], [t])

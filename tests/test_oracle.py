@@ -393,3 +393,69 @@ def test_fp32_oracle_is_single_precision():
     LU32, _, info32, _ = oracle.calu(A, 2, oracle.make_tree(2), dtype=np.float32)
     assert LU64[1, 1] == 2.0 ** -30 and info64 == 0
     assert LU32[1, 1] == 0.0 and info32 == 2
+
+
+# ---------------------------------------------------------------------------
+# the 2D multilevel CALU reduction operator (every tournament node factored
+# by CALU of the level below instead of GEPP)
+# ---------------------------------------------------------------------------
+OPS = [
+    [(2, 4)],             # one level below: CALU with b = 2 over 4-row leaves
+    [(3, 3)],
+    [(4, 8), (2, 4)],     # two levels below
+]
+
+
+@pytest.mark.parametrize("op", OPS)
+@pytest.mark.parametrize("m,n,b,L,levels", [(16, 12, 4, 8, [(0, BIN)]), (20, 9, 4, 8, [(0, FLAT)]),
+                                            (18, 18, 6, 12, [(2, BIN), (0, BIN)])])
+def test_calu_2d_operator_exact_rational(op, m, n, b, L, levels):
+    A = tie_free_int(m, n, 500 + m * n + len(op),
+                     lambda A: bf.calu(bf.to_frac(A), b, L, levels, op)[2], span=99)
+    ipiv_x, W, _ = bf.calu(bf.to_frac(A), b, L, levels, op)
+    LU, ipiv, info, _ = oracle.calu(A, b, oracle.make_tree(L, levels, op))
+    assert list(ipiv) == ipiv_x and info == 0
+    exact = np.array([[float(v) for v in row] for row in W])
+    assert np.allclose(LU, exact, rtol=1e-12, atol=1e-12)
+
+
+def test_calu_2d_operator_degenerates_to_gepp():
+    """An operator whose CALU has one panel and one leaf per node is GEPP."""
+    A = inputs.gaussian(400, 96, 21)
+    tree = oracle.make_tree(64, [(2, BIN), (0, BIN)])
+    op_tree = oracle.make_tree(64, [(2, BIN), (0, BIN)], op=[(32, 1024)])
+    LU, ipiv, _, nt = oracle.calu(A, 32, tree)
+    LU2, ipiv2, _, nt2 = oracle.calu(A, 32, op_tree)
+    assert nt == 0 and nt2 == 0
+    assert np.array_equal(ipiv, ipiv2)
+    assert np.array_equal(LU, LU2)
+
+
+def test_calu_2d_operator_changes_pivots_and_stays_stable():
+    """A genuine inner level picks other pivots than GEPP at the nodes; the
+    factorization stays backward stable, with growth within the soft bands
+    of the paper's experiments (Sec. 5.1: growth of the same order as GEPP)."""
+    n, b, L = 256, 32, 64
+    tree = oracle.make_tree(L, [(0, BIN)])
+    op_tree = oracle.make_tree(L, [(0, BIN)], op=[(8, 16)])
+    diff = 0
+    for seed in range(3):
+        A = inputs.gaussian(n, n, 60 + seed)
+        LU, ipiv, _, _ = oracle.calu(A, b, tree)
+        LU2, ipiv2, info2, _ = oracle.calu(A, b, op_tree)
+        diff += int(not np.array_equal(ipiv, ipiv2))
+        perm, Lf, U = oracle.lu_unpack(LU2, ipiv2)
+        assert info2 == 0
+        assert np.linalg.norm(A[perm] - Lf @ U) / np.linalg.norm(A) < 1e-13
+        _, _, U0 = oracle.lu_unpack(*oracle.getf2(A)[:2])
+        g_gepp = np.abs(U0).max() / np.abs(A).max()
+        g_2d = np.abs(U).max() / np.abs(A).max()
+        assert 0.002 < g_2d / g_gepp < 2.4 * 4
+        assert np.abs(Lf).max() <= 64.0           # |L| stays bounded (tournament pivoting)
+    assert diff >= 1
+
+
+def test_caqr_rejects_reduction_operator():
+    A = inputs.gaussian(64, 32, 1)
+    with pytest.raises(ValueError):
+        oracle.caqr(A, 16, oracle.make_tree(32, op=[(4, 8)]))
