@@ -203,21 +203,23 @@ def run_reference(a, rank: int, world: int):
 # the GPU arm
 # ---------------------------------------------------------------------------
 def traffic_for(kernel: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if
-    the summary was taken on the current kernel sources."""
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary
+    (profiles/traffic.txt: kernel, its source files, a hash of them, bytes),
+    if the counters were taken on the current sources of that kernel."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1303_5837_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
-    digest = h.hexdigest()[:16]
     for ln in open(path):
         p = ln.split()
-        if len(p) >= 3 and p[0] == kernel and p[1] == digest:
-            return float(p[2])
+        if len(p) < 4 or p[0] != kernel:
+            continue
+        h = hashlib.sha256()
+        for f in p[1].split(","):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest()[:16] == p[2]:
+            return float(p[3])
     return None
 
 
