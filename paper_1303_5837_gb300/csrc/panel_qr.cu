@@ -325,6 +325,24 @@ struct ApplyArgs {
   int ldc, ncols;
 };
 
+// W[u][v] += sum over the chunk's rows of Y(i, kb + 32 u) C(i, cb + 8 v) for
+// U0 <= u < U1 (the k-slices that hold nonzeros of Y in this chunk).
+template <int U0, int U1>
+__device__ __forceinline__ void accum_w(const double *Ys, const double *Cs, int nr, int ldy, int kb, int cb,
+                                        int bk, double (&W)[4][4]) {
+  for (int i = 0; i < nr; ++i) {
+    double yv[4], cv[4];
+#pragma unroll
+    for (int u = U0; u < U1; ++u) yv[u] = (kb + 32 * u < bk) ? Ys[i * ldy + kb + 32 * u] : 0.0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) cv[v] = Cs[i * kCs + cb + 8 * v];
+#pragma unroll
+    for (int u = U0; u < U1; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) W[u][v] = fma(yv[u], cv[v], W[u][v]);
+  }
+}
+
 __global__ void __launch_bounds__(kApThreads, 1) tree_apply_kernel(ApplyArgs a) {
   extern __shared__ __align__(16) double asm_[];
   const int bk = a.bk;
@@ -419,16 +437,24 @@ __global__ void __launch_bounds__(kApThreads, 1) tree_apply_kernel(ApplyArgs a) 
         Cs[i * kCs + c] = (i < nr && c < ncl) ? a.C[srow + r0 + i + (size_t)(c0 + c) * a.ldc] : 0.0;
       }
       __syncthreads();
-      for (int i = 0; i < nr; ++i) {
-        double yv[4], cv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) yv[u] = (kb + 32 * u < bk) ? Ys[i * ldy + kb + 32 * u] : 0.0;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) cv[v] = Cs[i * kCs + cb + 8 * v];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) W[u][v] = fma(yv[u], cv[v], W[u][v]);
+      // Y of a leaf is unit lower trapezoidal (row gi has nonzeros at k <= gi),
+      // a merge block upper trapezoidal (k >= gi): only k-slices u with
+      // 32 u <= r0 + 31 (leaf) or 32 u + 31 >= r0 (merge) hold nonzeros
+      const int uq = r0 >> 5;
+      if (type == 0) {
+        switch (uq) {
+          case 0: accum_w<0, 1>(Ys, Cs, nr, ldy, kb, cb, bk, W); break;
+          case 1: accum_w<0, 2>(Ys, Cs, nr, ldy, kb, cb, bk, W); break;
+          case 2: accum_w<0, 3>(Ys, Cs, nr, ldy, kb, cb, bk, W); break;
+          default: accum_w<0, 4>(Ys, Cs, nr, ldy, kb, cb, bk, W); break;
+        }
+      } else {
+        switch (uq) {
+          case 0: accum_w<0, 4>(Ys, Cs, nr, ldy, kb, cb, bk, W); break;
+          case 1: accum_w<1, 4>(Ys, Cs, nr, ldy, kb, cb, bk, W); break;
+          case 2: accum_w<2, 4>(Ys, Cs, nr, ldy, kb, cb, bk, W); break;
+          default: accum_w<3, 4>(Ys, Cs, nr, ldy, kb, cb, bk, W); break;
+        }
       }
     }
   }
@@ -501,7 +527,10 @@ __global__ void __launch_bounds__(kApThreads, 1) tree_apply_kernel(ApplyArgs a) 
       const int i = tid & 31;
       if (i < nr) {
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int k = 0; k < bk; ++k) {
+        // the chunk's nonzero columns of Y: k <= r0 + 31 (leaf), k >= r0 (merge)
+        const int k_lo = (type == 2) ? r0 : 0;
+        const int k_hi = (type == 0) ? min(bk, r0 + kChunk) : bk;
+        for (int k = k_lo; k < k_hi; ++k) {
           const double y = Ys[i * ldy + k];
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[v] = fma(y, Ws[k * kCt + cb + 8 * v], acc[v]);
@@ -648,8 +677,14 @@ cudaError_t tree_apply_qt(int mk, int bk, int b, const double *P, int lda, int l
   a.top_out = ws.top[0];
   a.c_out = ws.c[0];
   {
-    // W = Y^T C and C -= Y W over every leaf's rows, W = T^T W
-    const double f = 4.0 * mk * bk * (double)ncols + (double)plan.nleaves * bk * bk * ncols;
+    // W = Y^T C and C -= Y W over the nonzeros of every leaf's unit lower
+    // trapezoid Y (rows x k, k = min(rows, bk)), and W = T^T W (triangular)
+    double f = 0.0;
+    for (int j = 0; j < plan.nleaves; ++j) {
+      const double r = (double)(leaf_rows < mk - j * leaf_rows ? leaf_rows : mk - j * leaf_rows);
+      const double k = r < bk ? r : bk;
+      f += (4.0 * (r * k - k * (k - 1) / 2.0) + k * (k + 1)) * ncols;
+    }
     ProfScope ps(kClsTreeApply, st, f);
     tree_apply_kernel<<<dim3(plan.nleaves, ntiles), kApThreads, smem, st>>>(a);
   }
@@ -664,13 +699,16 @@ cudaError_t tree_apply_qt(int mk, int bk, int b, const double *P, int lda, int l
     a.top_out = ws.top[buf ^ 1];
     a.c_out = ws.c[buf ^ 1];
     {
-      // each merge: the stacked non-first children's Y (dense b x b blocks)
+      // each merge: the non-first children's upper triangular Y blocks
+      // (bk x bk, bk (bk + 1) / 2 nonzeros each), W = T^T W (triangular),
+      // and the first child's identity block (one add and one subtract)
       const RoundDesc &rd = plan.r[r];
       double f = 0.0;
+      const double kb2 = (double)bk;
       for (int o = 0; o < rd.n_out; ++o) {
         int s0, cnt, mi;
         round_node(rd, o, s0, cnt, mi);
-        if (cnt >= 2) f += 4.0 * (cnt - 1) * bk * (double)bk * ncols + (double)bk * bk * ncols;
+        if (cnt >= 2) f += (4.0 * (cnt - 1) * kb2 * (kb2 + 1) / 2.0 + kb2 * (kb2 + 1) + 2.0 * kb2) * ncols;
       }
       ProfScope ps(kClsTreeApply, st, f);
       tree_apply_kernel<<<dim3(plan.r[r].n_out, ntiles), kApThreads, smem, st>>>(a);
