@@ -59,10 +59,12 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=100.0)
     p.add_argument("--serve-duration", type=float, default=3.0)
     p.add_argument("--serve-nmax", type=int, default=2048)
+    p.add_argument("--serve-slots", type=int, default=4, help="concurrent requests (one stream each)")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--batch-count", type=int, default=4096, help="matrices of the batched workload")
     p.add_argument("--batch-steps", type=int, default=3)
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--only-serve", action="store_true", help="diagnostic: run only the serving workload")
     p.add_argument("--only-batch", default="", choices=["", "f64", "f32", "ops"],
                    help="diagnostic: run only the batched workload in this precision")
     return p.parse_args()
@@ -231,6 +233,10 @@ def run_ours(a, rank: int, world: int, local: int):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     ca.load()
+    if a.only_serve:
+        if rank == 0:
+            print(json.dumps({"serving": serving_run(a)}), flush=True)
+        return
     if a.only_batch:
         if a.only_batch == "ops":
             print(json.dumps({"batched": {"operators": operator_diagnostics(a, ca, torch, dev)}}), flush=True)
@@ -641,9 +647,9 @@ def serving_run(a):
         if key not in pool:
             pool[key] = (inputs.gaussian(m, n, n + (7 if kind == "ls" else 0)), inputs.gaussian(m, 16, n + 1))
     out = {"rate_per_s": a.serve_rate, "duration_s": a.serve_duration, "requests": len(work),
-           "n_range": [64, a.serve_nmax], "pool_sizes": len(pool)}
+           "n_range": [64, a.serve_nmax], "pool_sizes": len(pool), "slots": a.serve_slots}
     for form in ("fp64", "mixed"):
-        srv = serve.SolveServer(hbm_budget=64 << 30, slots=4, form=form)
+        srv = serve.SolveServer(hbm_budget=64 << 30, slots=a.serve_slots, form=form)
         try:
             t0 = time.perf_counter()
             for t, kind, m, n, nrhs in work:
