@@ -4,7 +4,7 @@ benchmark times.
 Where the oracle finishes in seconds it runs in full (tall-skinny TSLU / TSQR
 panels of 1,048,576 x 64 and 8,388,608 x 32 with 256-row leaves: pivots must
 match exactly, factors, every stored Y and every T within 1e-12).  At
-n = 16384 (b = 128, 256-row leaves, the benchmark's tree) the oracle computes
+n = 16384 (b = 128, the benchmark's leaves and tree) the oracle computes
 the first panel's tournament exactly and sampled outputs one by one: rows of
 P A - L U, column norms of R, backward errors of the solves, and the tensor-core
 forms against the FP64 form.
@@ -122,7 +122,8 @@ def lu_rows_residual(LU, perm, A0, count=48, seed=3):
 
 def test_calu_bench_configuration(ca, big):
     A0, B0, x = big
-    n, b, L = A0.shape[0], 128, 256
+    import bench
+    n, b, L = A0.shape[0], 128, bench.BENCH_LEAF_ROWS
     tree = ca.make_tree(L, BENCH_TREE)
     # first panel: the tournament over 64 leaves, exactly the oracle's
     P = A0[:, :b].cpu().numpy()
@@ -162,7 +163,8 @@ def test_calu_bench_configuration(ca, big):
 
 def test_caqr_bench_configuration(ca, big):
     A0, B0, x = big
-    n, b, L = A0.shape[0], 128, 256
+    import bench
+    n, b, L = A0.shape[0], 128, bench.BENCH_LEAF_ROWS
     tree = ca.make_tree(L, BENCH_TREE)
     A = A0.clone()
     qtree, info = ca.caqr_factor(A, b, tree)
