@@ -43,6 +43,19 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # SMs x DFMA/clk/SM x flops/DFMA x max GH
 BENCH_LEAF_ROWS = 1024
 
 
+def _hbm_peak() -> float:
+    """Measured copy bandwidth of this machine's GB300 (MEASURED_PEAKS.json),
+    else the profiling recipe's fallback 6800 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_GBS = _hbm_peak()
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -68,6 +81,7 @@ def parse():
     p.add_argument("--batch-count", type=int, default=4096, help="matrices of the batched workload")
     p.add_argument("--batch-steps", type=int, default=3)
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-configs", action="store_true")
     p.add_argument("--only-serve", action="store_true", help="diagnostic: run only the serving workload")
     p.add_argument("--only-batch", default="", choices=["", "f64", "f32", "ops"],
                    help="diagnostic: run only the batched workload in this precision")
@@ -347,6 +361,11 @@ def run_ours(a, rank: int, world: int, local: int):
         if rank == 0:
             batched["operators"] = operator_diagnostics(a, ca, torch, dev)
 
+    # ---- the other configurations (tall-skinny panels, the small square) ----
+    configs = None
+    if not a.no_configs and rank == 0:
+        configs = other_configs(a, ca, torch, dev)
+
     # ---- end to end through the public API with host buffers --------------
     e2e = None
     if a.e2e_steps > 0:
@@ -406,6 +425,7 @@ def run_ours(a, rank: int, world: int, local: int):
         "lu_forms": lu_forms,
         "serving": serving,
         "batched": batched,
+        "other_configs": configs,
     }
     print(json.dumps(line), flush=True)
 
@@ -527,6 +547,66 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
                                        "update on the tensor cores"}
     for k, v in kernels_of.items():
         out[k]["kernels"] = v
+    return out
+
+
+def other_configs(a, ca, torch, dev):
+    """The other configurations of the workload family, each timed on its own
+    (3 runs after a warm-up, CUDA events, the input restored between runs):
+    the tall-skinny panels alone (TSLU and TSQR of 1,048,576 x 64 and
+    8,388,608 x 32 N(0, 1) matrices, leaves of 256 rows, 4-level tree) with
+    algorithmic HBM bytes (TSQR: A read, Y written = 16 m n; TSLU: A read
+    twice, L written = 24 m n) and standard flops (TSQR 2 m n^2 - 2 n^3 / 3,
+    TSLU m n^2 - n^3 / 3), and the small square case (CALU and CAQR of one
+    1024 x 1024 matrix, b = 64, leaves of 128 rows, binary tree)."""
+    out = {}
+    gen = torch.Generator(device=dev).manual_seed(31)
+
+    def timed(fn, A, A0, reps=3):
+        A.copy_(A0)
+        fn(A)
+        torch.cuda.synchronize()
+        best = []
+        for _ in range(reps):
+            A.copy_(A0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(A)
+            e1.record()
+            e1.synchronize()
+            best.append(e0.elapsed_time(e1))
+        return statistics.median(best)
+
+    tree4 = ca.make_tree(256, [(4, 0), (8, 0), (0, 0)])
+    for m, n in ((1048576, 64), (8388608, 32)):
+        A0 = torch.randn(n, m, dtype=torch.float64, device=dev, generator=gen).t()
+        A = torch.empty_like(A0)
+        qb, wb = ca.ca_caqr_workspace(m, n, n, tree4)
+        qt = torch.empty((qb + 7) // 8, dtype=torch.float64, device=dev)
+        qw = torch.empty((wb + 7) // 8, dtype=torch.float64, device=dev)
+        lw = torch.empty((ca.ca_calu_workspace(m, n, n, tree4) + 7) // 8, dtype=torch.float64, device=dev)
+        ipiv = torch.empty(n, dtype=torch.int32, device=dev)
+        info = torch.zeros(2, dtype=torch.int32, device=dev)
+        ms_q = timed(lambda X: ca.tsqr(X, tree4, qtree=qt, work=qw, dev_info=info), A, A0)
+        ms_l = timed(lambda X: ca.tslu(X, tree4, ipiv=ipiv, work=lw, dev_info=info), A, A0)
+        fq, fl = 2.0 * m * n * n - 2.0 * n ** 3 / 3, m * n * n - n ** 3 / 3.0
+        bq, bl = 16.0 * m * n, 24.0 * m * n
+        out[f"panel_{m}x{n}"] = {
+            "tsqr": {"ms": ms_q, "gflops": fq / ms_q / 1e6, "gbs": bq / ms_q / 1e6,
+                     "frac_fp64": fq / ms_q / 1e6 / FP64_PEAK_GFLOPS, "frac_hbm": bq / ms_q / 1e6 / HBM_GBS},
+            "tslu": {"ms": ms_l, "gflops": fl / ms_l / 1e6, "gbs": bl / ms_l / 1e6,
+                     "frac_fp64": fl / ms_l / 1e6 / FP64_PEAK_GFLOPS, "frac_hbm": bl / ms_l / 1e6 / HBM_GBS}}
+        del A0, A, qt, qw, lw
+    n, b = 1024, 64
+    t2 = ca.make_tree(128, [(0, 0)])
+    A0 = torch.randn(n, n, dtype=torch.float64, device=dev, generator=gen).t()
+    A = torch.empty_like(A0)
+    ms_lu = timed(lambda X: ca.calu_factor(X, b, t2), A, A0)
+    ms_qr = timed(lambda X: ca.caqr_factor(X, b, t2), A, A0)
+    out["square_1024_b64"] = {"calu_ms": ms_lu, "calu_gflops": 2.0 * n ** 3 / 3 / ms_lu / 1e6,
+                              "caqr_ms": ms_qr, "caqr_gflops": 4.0 * n ** 3 / 3 / ms_qr / 1e6}
+    out["hbm_peak_gbs"] = HBM_GBS
     return out
 
 

@@ -339,10 +339,13 @@ static int node_factor(int r, int c, real *W, int ldw, int *perm, const ora_tree
 
 /* Tournament on the m x b panel P (ld ldp, original values are read, never
  * written).  sel[0..k) receives the panel-relative rows chosen by the root,
- * in root selection order, k = min(m, b).  Every leaf is factored by GEPP and
- * yields min(rows, b) candidate rows; every merge stacks its children's
- * candidate rows (original values, child order, each child in its selection
- * order) and GEPP picks min(sum, b) of them (Sec. 3.2, reduction steps). */
+ * in root selection order, k = min(m, b).  Every leaf is factored by the
+ * node operator (GEPP, or the 2D multilevel CALU operator) and yields
+ * min(rows, b) candidate rows; every merge stacks its children's candidate
+ * rows (original values, child order, each child in its selection order) and
+ * the operator picks min(sum, b) of them (Sec. 3.2, reduction steps).
+ * Negative returns: -1 bad argument, -2 bad tree, -3 / -1000 out of memory
+ * (like the other allocation failures here, nothing is freed on that path). */
 int ora_tslu_select(int m, int b, const real *P, int ldp, const ora_tree *t, int *sel,
                     long *nearties) {
   if (m < 1 || b < 1 || t->leaf_rows < b || !op_valid(t)) return -1;
