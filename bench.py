@@ -83,6 +83,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-configs", action="store_true")
     p.add_argument("--only-serve", action="store_true", help="diagnostic: run only the serving workload")
+    p.add_argument("--only-configs", action="store_true", help="diagnostic: run only the other configurations")
     p.add_argument("--only-batch", default="", choices=["", "f64", "f32", "ops"],
                    help="diagnostic: run only the batched workload in this precision")
     return p.parse_args()
@@ -254,6 +255,10 @@ def run_ours(a, rank: int, world: int, local: int):
     if a.only_serve:
         if rank == 0:
             print(json.dumps({"serving": serving_run(a)}), flush=True)
+        return
+    if a.only_configs:
+        if rank == 0:
+            print(json.dumps({"other_configs": other_configs(a, ca, torch, dev)}), flush=True)
         return
     if a.only_batch:
         if a.only_batch == "ops":

@@ -709,16 +709,29 @@ __device__ int node_qr(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool use_
       if (!use_fz || F.fz[p] <= j) cj[p] *= scal;
     __syncthreads();
     if (tid == 0) cj[j] = F.scal[1];
-    // w_q = tau v^T A(:, q), then A(:, q) -= v w_q; one warp per column q
-    for (int q = j + 1 + warp; q < bk; q += kBW) {
-      T *cq = tile + (size_t)q * ld;
-      T acc = (lane == 0) ? cq[j] : T(0);
-      for (int p = j + 1 + lane; p < rows; p += 32)
-        if (!use_fz || F.fz[p] <= j) acc = fma(cj[p], cq[p], acc);
-      const T wq = tj * wsum(acc);
-      if (lane == 0) cq[j] -= wq;
-      for (int p = j + 1 + lane; p < rows; p += 32)
-        if (!use_fz || F.fz[p] <= j) cq[p] = fma(-cj[p], wq, cq[p]);
+    // w_q = tau v^T A(:, q), then A(:, q) -= v w_q; a group of 8 lanes per
+    // column (4 columns per warp), so that the cross-lane sum of each dot
+    // product takes 3 steps: floating-point adds across lanes cost the same
+    // pipe as the multiply-adds
+    const int grp = lane >> 3, gl = lane & 7;
+    for (int q0 = j + 1 + 4 * warp; q0 < bk; q0 += 4 * kBW) {
+      const int q = q0 + grp;
+      const bool act = q < bk;
+      T *cq = tile + (size_t)(act ? q : j) * ld;
+      T acc = T(0);
+      if (act) {
+        acc = (gl == 0) ? cq[j] : T(0);
+        for (int p = j + 1 + gl; p < rows; p += 8)
+          if (!use_fz || F.fz[p] <= j) acc = fma(cj[p], cq[p], acc);
+      }
+#pragma unroll
+      for (int off = 4; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (act) {
+        const T wq = tj * acc;
+        if (gl == 0) cq[j] -= wq;
+        for (int p = j + 1 + gl; p < rows; p += 8)
+          if (!use_fz || F.fz[p] <= j) cq[p] = fma(-cj[p], wq, cq[p]);
+      }
     }
     __syncthreads();
   }
@@ -734,22 +747,29 @@ __device__ int node_qr(T *tile, int ld, int rows, int bk, Fixed<T> &F, bool use_
     for (int e = tid; e < b * b; e += kBT) Tg[e] = T(0);
     __syncthreads();
   }
+  const int grp = lane >> 3, gl = lane & 7;
   for (int jj = 0; jj < kk; ++jj) {
-    for (int q = warp; q < jj; q += kBW) {
-      const T *cq = tile + (size_t)q * ld;
-      const T *cjj = tile + (size_t)jj * ld;
-      T acc = (lane == 0) ? cq[jj] : T(0);
-      for (int p = jj + 1 + lane; p < rows; p += 32) acc = fma(cq[p], cjj[p], acc);
-      acc = wsum(acc);
-      if (lane == 0) F.z[q] = acc;
+    // z_q = v_q^T v_jj (q < jj): a group of 8 lanes per q
+    const T *cjj = tile + (size_t)jj * ld;
+    for (int q0 = 4 * warp; q0 < jj; q0 += 4 * kBW) {
+      const int q = q0 + grp;
+      T acc = T(0);
+      if (q < jj) {
+        const T *cq = tile + (size_t)q * ld;
+        acc = (gl == 0) ? cq[jj] : T(0);
+        for (int p = jj + 1 + gl; p < rows; p += 8) acc = fma(cq[p], cjj[p], acc);
+      }
+#pragma unroll
+      for (int off = 4; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (q < jj && gl == 0) F.z[q] = acc;
     }
     __syncthreads();
+    // T(i, jj) = -tau_jj sum_{q=i}^{jj-1} T(i, q) z_q: one thread per row
     const T tj = F.tau[jj];
-    for (int i = warp; i < jj; i += kBW) {
+    for (int i = tid; i < jj; i += kBT) {
       T acc = T(0);
-      for (int q = i + lane; q < jj; q += 32) acc = fma(Tw[i + (size_t)q * ldt], F.z[q], acc);
-      acc = wsum(acc);
-      if (lane == 0) Tw[i + (size_t)jj * ldt] = -tj * acc;
+      for (int q = i; q < jj; ++q) acc = fma(Tw[i + (size_t)q * ldt], F.z[q], acc);
+      Tw[i + (size_t)jj * ldt] = -tj * acc;
     }
     if (tid == 0) Tw[jj + (size_t)jj * ldt] = tj;
     __syncthreads();

@@ -40,6 +40,7 @@ __host__ __device__ inline size_t tsqr_smem_bytes(int rloc, int ld, int bk) {
   s += (size_t)bk * 8;                     // tau
   s += 128;                                // scalars and reduce scratch
   s += (size_t)rloc * 4;                   // first structurally nonzero column per row
+  s += (size_t)rloc * 4;                   // panel row of each local row
   size_t zs = (size_t)bk * (bk - 1) / 2 * 8 + 8;  // packed strict upper Gram matrix
   return s + zs + 64;
 }
@@ -77,8 +78,9 @@ __global__ void __launch_bounds__(kQrThreads, 1) tsqr_node_kernel(TsqrNodeArgs a
   double *tau = w + bk;                         // bk
   double *sc = tau + bk;                        // 8 scalars + 8 reduce slots
   int *fz = (int *)(sc + 16);                   // rloc
+  int *prw = fz + rloc;                         // rloc: panel row of each local row
   // Z(i, j), i < j, packed column by column at j (j - 1) / 2 + i
-  double *Z = (double *)(((uintptr_t)(fz + rloc) + 15) & ~(uintptr_t)15);
+  double *Z = (double *)(((uintptr_t)(prw + rloc) + 15) & ~(uintptr_t)15);
   // sc: [0] ss partial of this CTA, [1] beta, [2] tau, [3] scal, [4] skip;
   //     sc[8..15]: block-reduction scratch
 
@@ -129,20 +131,24 @@ __global__ void __launch_bounds__(kQrThreads, 1) tsqr_node_kernel(TsqrNodeArgs a
     return -1;
   };
 
-  // ---- load --------------------------------------------------------------
+  // ---- load (lanes over rows: consecutive rows of a column are adjacent) --
+  for (int i = tid; i < myrows; i += kQrThreads) prw[i] = prow_of(i);
+  __syncthreads();
   bool bad = false;
-  for (int i = warp; i < myrows; i += kQrWarps) {
-    const int pr = prow_of(i);
-    const int z = fz[i];
-    for (int k = lane; k < bk; k += 32) {
+  for (int k = warp; k < bk; k += kQrWarps) {
+    const double *col = a.P + (size_t)k * a.lda;
+    for (int i = lane; i < myrows; i += 32) {
       double v = 0.0;
-      if (k >= z) v = a.P[pr + (size_t)k * a.lda];
+      if (k >= fz[i]) v = col[prw[i]];
       bad |= not_finite(v);
       tile[i + (size_t)k * ld] = v;
     }
   }
   if (bad && a.dev_info) atomicOr(a.dev_info + 1, CA_STATUS_NONFINITE);
   __syncthreads();
+  // merge rows are structurally zero left of their child-local index (fz);
+  // leaves have none, and their loops skip the test
+  const bool leaf = a.is_leaf != 0;
 
   // ---- Householder QR on the distributed tile --------------------------
   const int kmax = min(R, bk);
@@ -151,7 +157,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) tsqr_node_kernel(TsqrNodeArgs a
     // (a) partial ||x2||^2 over positions > j (structurally nonzero rows)
     double ss = 0.0;
     for (int i = max(j + 1 - p0, 0) + tid; i < myrows; i += kQrThreads)
-      if (fz[i] <= j) {
+      if (leaf || fz[i] <= j) {
         double v = tile[i + (size_t)j * ld];
         ss = fma(v, v, ss);
       }
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) tsqr_node_kernel(TsqrNodeArgs a
     const double scal = sc[3], tj = sc[2];
     // (c) v = x2 / (alpha - beta); R_jj = beta
     for (int i = max(j + 1 - p0, 0) + tid; i < myrows; i += kQrThreads)
-      if (fz[i] <= j) tile[i + (size_t)j * ld] *= scal;
+      if (leaf || fz[i] <= j) tile[i + (size_t)j * ld] *= scal;
     if (oj == rank && tid == 0) tile[lj + (size_t)j * ld] = sc[1];
     __syncthreads();
     // (d) partial w_q = v^T A(:, q) for q > j: thread (g, qq), rows = g mod 4
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) tsqr_node_kernel(TsqrNodeArgs a
         const int q = j + 1 + qq;
         double acc = 0.0;
         for (int i = max(j - p0, 0) + g; i < myrows; i += kQrGroups) {
-          if (fz[i] > j) continue;
+          if (!leaf && fz[i] > j) continue;
           double v = (p0 + i == j) ? 1.0 : tile[i + (size_t)j * ld];
           acc = fma(v, tile[i + (size_t)q * ld], acc);
         }
@@ -234,7 +240,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) tsqr_node_kernel(TsqrNodeArgs a
         const int q = j + 1 + qq;
         const double wq = w[q];
         for (int i = max(j - p0, 0) + g; i < myrows; i += kQrGroups) {
-          if (fz[i] > j) continue;
+          if (!leaf && fz[i] > j) continue;
           double v = (p0 + i == j) ? 1.0 : tile[i + (size_t)j * ld];
           tile[i + (size_t)q * ld] = fma(-v, wq, tile[i + (size_t)q * ld]);
         }
@@ -244,7 +250,9 @@ __global__ void __launch_bounds__(kQrThreads, 1) tsqr_node_kernel(TsqrNodeArgs a
   }
 
   // ---- T (LAPACK larft, forward columnwise) ----------------------------
-  // Z(i, j) = v_i^T v_j for i < j: partial over this CTA's rows
+  // Z(i, j) = v_i^T v_j for i < j: partial over this CTA's rows; each thread
+  // owns whole dot products (no cross-lane FP64 reductions: on this part the
+  // FP64 pipe is the scarce resource)
   const int kk = kmax;
   const int nz = kk * (kk - 1) / 2;
   for (int idx = tid; idx < kk * kk; idx += kQrThreads) {
@@ -286,11 +294,10 @@ __global__ void __launch_bounds__(kQrThreads, 1) tsqr_node_kernel(TsqrNodeArgs a
 
   // ---- write back: leaf in place; merge: R into the first child's rows,
   //      Y blocks into the other children's rows (on and above the diagonal)
-  for (int i = warp; i < myrows; i += kQrWarps) {
-    const int pr = prow_of(i);
-    const int z = fz[i];
-    for (int k = lane; k < bk; k += 32)
-      if (k >= z) a.P[pr + (size_t)k * a.lda] = tile[i + (size_t)k * ld];
+  for (int k = warp; k < bk; k += kQrWarps) {
+    double *col = a.P + (size_t)k * a.lda;
+    for (int i = lane; i < myrows; i += 32)
+      if (k >= fz[i]) col[prw[i]] = tile[i + (size_t)k * ld];
   }
   if (rank == 0 && tid == 0) {
     a.top_out[node] = a.is_leaf ? r0 : a.top_in[start];
