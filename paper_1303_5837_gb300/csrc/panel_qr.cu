@@ -397,6 +397,50 @@ __global__ void __launch_bounds__(kApThreads, 1) tree_apply_kernel(ApplyArgs a) 
     for (int v = 0; v < 4; ++v) W[u][v] = 0.0;
 
   const int nseg = a.is_leaf ? 1 : cnt;
+  // Software pipeline over row chunks: the next chunk's Y (and C) are loaded
+  // into registers while the current chunk is multiplied from shared memory.
+  constexpr int kYPer = kChunk * 128 / kApThreads;  // Y chunk elements per thread (bk <= 128)
+  constexpr int kCPer = kChunk * kCt / kApThreads;  // C chunk elements per thread
+  double py[kYPer], pc[kCPer];
+  auto load_y = [&](int srow, int type, int r0, int nr) {
+#pragma unroll
+    for (int t = 0; t < kYPer; ++t) {
+      const int idx = tid + t * kApThreads;
+      const int i = idx % kChunk, k = idx / kChunk;  // rows fastest: coalesced column reads
+      const int gi = r0 + i;
+      double y = 0.0;
+      if (i < nr && k < bk) {
+        if (type == 0)
+          y = (gi > k) ? a.P[srow + gi + (size_t)k * a.lda] : (gi == k ? 1.0 : 0.0);
+        else
+          y = (gi <= k) ? a.P[srow + gi + (size_t)k * a.lda] : 0.0;
+      }
+      py[t] = y;
+    }
+  };
+  auto store_y = [&]() {
+#pragma unroll
+    for (int t = 0; t < kYPer; ++t) {
+      const int idx = tid + t * kApThreads;
+      const int i = idx % kChunk, k = idx / kChunk;
+      if (k < bk) Ys[i * ldy + k] = py[t];
+    }
+  };
+  auto load_c = [&](int srow, int r0, int nr) {
+#pragma unroll
+    for (int t = 0; t < kCPer; ++t) {
+      const int idx = tid + t * kApThreads;
+      const int i = idx % kChunk, c = idx / kChunk;
+      pc[t] = (i < nr && c < ncl) ? a.C[srow + r0 + i + (size_t)(c0 + c) * a.ldc] : 0.0;
+    }
+  };
+  auto store_c = [&]() {
+#pragma unroll
+    for (int t = 0; t < kCPer; ++t) {
+      const int idx = tid + t * kApThreads;
+      Cs[(idx % kChunk) * kCs + idx / kChunk] = pc[t];
+    }
+  };
   // ---- phase 1: W = Y^T C ---------------------------------------------
   for (int sg = 0; sg < nseg; ++sg) {
     int srow, srows, type;
@@ -422,28 +466,18 @@ __global__ void __launch_bounds__(kApThreads, 1) tree_apply_kernel(ApplyArgs a) 
       }
       continue;
     }
+    load_y(srow, type, 0, min(kChunk, srows));
+    load_c(srow, 0, min(kChunk, srows));
     for (int r0 = 0; r0 < srows; r0 += kChunk) {
       const int nr = min(kChunk, srows - r0);
       __syncthreads();
-      for (int idx = tid; idx < kChunk * bk; idx += kApThreads) {
-        int i = idx % kChunk, k = idx / kChunk;  // rows fastest: coalesced column reads
-        int gi = r0 + i;
-        double y = 0.0;
-        if (i < nr) {
-          if (type == 0)
-            y = (gi > k) ? a.P[srow + gi + (size_t)k * a.lda] : (gi == k ? 1.0 : 0.0);
-          else if (type == 1)
-            y = (gi == k) ? 1.0 : 0.0;
-          else
-            y = (gi <= k) ? a.P[srow + gi + (size_t)k * a.lda] : 0.0;
-        }
-        Ys[i * ldy + k] = y;
-      }
-      for (int idx = tid; idx < kChunk * kCt; idx += kApThreads) {
-        int i = idx % kChunk, c = idx / kChunk;
-        Cs[i * kCs + c] = (i < nr && c < ncl) ? a.C[srow + r0 + i + (size_t)(c0 + c) * a.ldc] : 0.0;
-      }
+      store_y();
+      store_c();
       __syncthreads();
+      if (r0 + kChunk < srows) {
+        load_y(srow, type, r0 + kChunk, min(kChunk, srows - r0 - kChunk));
+        load_c(srow, r0 + kChunk, min(kChunk, srows - r0 - kChunk));
+      }
       // Y of a leaf is unit lower trapezoidal (row gi has nonzeros at k <= gi),
       // a merge block upper trapezoidal (k >= gi): only k-slices u with
       // 32 u <= r0 + 31 (leaf) or 32 u + 31 >= r0 (merge) hold nonzeros
@@ -514,22 +548,13 @@ __global__ void __launch_bounds__(kApThreads, 1) tree_apply_kernel(ApplyArgs a) 
       }
       continue;
     }
+    load_y(srow, type, 0, min(kChunk, srows));
     for (int r0 = 0; r0 < srows; r0 += kChunk) {
       const int nr = min(kChunk, srows - r0);
       __syncthreads();
-      for (int idx = tid; idx < kChunk * bk; idx += kApThreads) {
-        int i = idx % kChunk, k = idx / kChunk;
-        int gi = r0 + i;
-        double y = 0.0;
-        if (i < nr) {
-          if (type == 0)
-            y = (gi > k) ? a.P[srow + gi + (size_t)k * a.lda] : (gi == k ? 1.0 : 0.0);
-          else
-            y = (gi <= k) ? a.P[srow + gi + (size_t)k * a.lda] : 0.0;
-        }
-        Ys[i * ldy + k] = y;
-      }
+      store_y();
       __syncthreads();
+      if (r0 + kChunk < srows) load_y(srow, type, r0 + kChunk, min(kChunk, srows - r0 - kChunk));
       // thread -> (row i = tid % 32, columns c = tid / 32 + 8 v)
       const int i = tid & 31;
       if (i < nr) {
