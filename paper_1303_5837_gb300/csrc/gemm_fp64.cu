@@ -25,18 +25,40 @@ __global__ void __launch_bounds__(256) gemm_minus_kernel(int m, int n, int k, co
 #pragma unroll
     for (int b = 0; b < TN; ++b) acc[a][b] = 0.0;
 
-  for (int k0 = 0; k0 < k; k0 += BK) {
-    for (int idx = tid; idx < BK * BM; idx += 256) {
-      int i = idx % BM, kk = idx / BM;
-      int gi = i0 + i, gk = k0 + kk;
-      As[kk][i] = (gi < m && gk < k) ? A[gi + (size_t)gk * lda] : 0.0;
+  // software pipeline: the next K chunk of A and B is loaded into registers
+  // while the current one is multiplied from shared memory
+  constexpr int PA = BK * BM / 256, PB = BK * BN / 256;
+  double ra[PA], rb[PB];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int t = 0; t < PA; ++t) {
+      const int idx = tid + 256 * t;
+      const int i = idx % BM, kk = idx / BM;
+      const int gi = i0 + i, gk = k0 + kk;
+      ra[t] = (gi < m && gk < k) ? A[gi + (size_t)gk * lda] : 0.0;
     }
-    for (int idx = tid; idx < BK * BN; idx += 256) {
-      int kk = idx % BK, j = idx / BK;
-      int gj = j0 + j, gk = k0 + kk;
-      Bs[kk][j] = (gj < n && gk < k) ? B[gk + (size_t)gj * ldb] : 0.0;
+#pragma unroll
+    for (int t = 0; t < PB; ++t) {
+      const int idx = tid + 256 * t;
+      const int kk = idx % BK, j = idx / BK;
+      const int gj = j0 + j, gk = k0 + kk;
+      rb[t] = (gj < n && gk < k) ? B[gk + (size_t)gj * ldb] : 0.0;
+    }
+  };
+  load(0);
+  for (int k0 = 0; k0 < k; k0 += BK) {
+#pragma unroll
+    for (int t = 0; t < PA; ++t) {
+      const int idx = tid + 256 * t;
+      As[idx / BM][idx % BM] = ra[t];
+    }
+#pragma unroll
+    for (int t = 0; t < PB; ++t) {
+      const int idx = tid + 256 * t;
+      Bs[idx % BK][idx / BK] = rb[t];
     }
     __syncthreads();
+    if (k0 + BK < k) load(k0 + BK);
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
       double af[TM], bf[TN];
