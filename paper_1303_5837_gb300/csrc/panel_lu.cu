@@ -181,20 +181,20 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
     //     row at position j
     if (tid < G) s.gslot[tid] = (tid == rank) ? *s.slot : *cl.map_shared_rank(s.slot, tid);
     __syncthreads();
-    if (tid == 0) {
-      ArgMax b = s.gslot[0];
-      for (int q = 1; q < G; ++q) b = argmax_better(b, s.gslot[q]);
-      s.iscal[0] = b.pos;
-      s.iscal[3] = (b.key == 0ull);
-    }
-    __syncthreads();
-    const int zero = s.iscal[3];
-    const int p = s.iscal[0];
+    // every thread combines the G partial maxima (same order, same result)
+    ArgMax gb = s.gslot[0];
+    for (int q = 1; q < G; ++q) gb = argmax_better(gb, s.gslot[q]);
+    const int zero = (gb.key == 0ull);
+    const int p = gb.pos;
     if (!zero) {
       const int op = p / rloc, lp = p - op * rloc;
       const int oj = j / rloc, lj = j - oj * rloc;
       const double *tp = (op == rank) ? s.tile : cl.map_shared_rank(s.tile, op);
-      for (int k = tid; k < bk; k += kNodeThreads) s.prow[k] = tp[lp + (size_t)k * rloc];
+      for (int k = tid; k < bk; k += kNodeThreads) {
+        const double v = tp[lp + (size_t)k * rloc];
+        s.prow[k] = v;
+        if (k == j) s.scal[0] = 1.0 / v;  // the pivot's reciprocal, read after the barrier below
+      }
       if (tid == 0) s.iscal[1] = (op == rank) ? s.lab[lp] : *cl.map_shared_rank(s.lab + lp, op);
       if (p != j && op == rank) {
         const double *tj = (oj == rank) ? s.tile : cl.map_shared_rank(s.tile, oj);
@@ -219,9 +219,9 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
         if (tid == 0) s.lab[lp] = s.iscal[2];
       }
     }
-    // (d) multipliers l_i = a_ij / a_jj for positions > j
-    if (tid == 0) s.scal[0] = 1.0 / s.prow[j];
-    __syncthreads();
+    // (d) multipliers l_i = a_ij / a_jj for positions > j (the swap's writes
+    //     are visible after the barrier; without a swap there is nothing to wait for)
+    if (p != j) __syncthreads();
     const double rinv = s.scal[0];
     const int i1 = max(j + 1 - p0, 0);
     double *cj = s.tile + (size_t)j * rloc;
