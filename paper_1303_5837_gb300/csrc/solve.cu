@@ -2,10 +2,12 @@
 // factors (PA = LU: swaps, unit-lower forward and upper back substitution;
 // A = QR: back substitution with R after Q^T is applied through the tree).
 //
-// Blocked by kTb rows: the diagonal block is solved by one CTA in shared
-// memory, then the rows below (or above) are updated -- for few right-hand
-// sides in one cooperative launch, otherwise with one launch per block and
-// the FP64 GEMM.
+// Blocked by kTb rows: for few right-hand sides one cooperative launch with
+// one CTA per diagonal block, ordered by ready flags; otherwise the diagonal
+// block is solved by one CTA in shared memory and the rows below (or above)
+// are updated with the FP64 GEMM, one launch per block.
+#include <mutex>
+
 #include "ca_internal.cuh"
 
 namespace cagb {
@@ -102,121 +104,189 @@ __global__ void __launch_bounds__(256) trsm_diag_kernel(int nb, int nrhs, const 
 }
 
 // ---------------------------------------------------------------------------
-// Few right-hand sides: one cooperative launch over every SM.
-//   Phase 0: CTA c inverts diagonal block c of T in place in its shared memory
-//            (LAPACK trti2 order, unit lower or non-unit upper), so no block
-//            step needs a serial substitution chain.
-//   Per block (forward for L, backward for U): the owning CTA computes
-//            x_i = T_ii^-1 b_i (a GEMV from shared memory); grid-wide sync;
-//            every CTA updates its share of the rows below / above
-//            (b_r -= T(r, block) x_i, rows coalesced); grid-wide sync.
-// Needs one CTA per diagonal block: n <= gridDim.x * kTb.
+// Few right-hand sides: one cooperative launch, one CTA per diagonal block,
+// ordered by per-block ready flags instead of grid-wide barriers.
+//   Phase 0: CTA c inverts diagonal block c of T in its shared memory
+//            (LAPACK trti2 order, unit lower or non-unit upper).
+//   Then CTA c takes the blocks it depends on in order (the ones before it
+//   for L, after it for U): it waits until block j's solution is published
+//   (flag j), subtracts T(c, j) x_j from its right-hand sides, and after the
+//   last one computes x_c = T_cc^-1 b_c, writes it to B and publishes flag c.
+//   The chain of dependent steps is one GEMV of a 128 x 128 block and one
+//   small triangular multiply per block; the earlier GEMVs of a CTA overlap
+//   with the chain.  The cooperative launch makes every CTA resident, as the
+//   waits require; every wait is bounded (about 2 s of SM clock), after
+//   which the CTA records the timeout in the flag word after the last block
+//   and leaves.
+// Needs one CTA per diagonal block: n <= SMs * kTb.
 // ---------------------------------------------------------------------------
 constexpr int kCoopMaxRhs = 16;
 constexpr int kLdI = kTb + 1;
+constexpr int kMaxFlagBlocks = 1024;            // flag words per stream (covers any SM count here)
+constexpr long long kSolveWaitLimit = 4000000000ll;
 
-__global__ void __launch_bounds__(256, 1) trsv_coop_kernel(int n, int nrhs, const double *T, int ldt, double *B,
-                                                           int ldb, int lower, int unit) {
-  cg::grid_group grid = cg::this_grid();
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int *p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(256, 1) trsv_flag_kernel(int n, int nrhs, const double *T, int ldt, double *B,
+                                                           int ldb, int lower, int unit, int *flags) {
   extern __shared__ __align__(16) double csm[];
-  double *Ti = csm;                      // the inverted diagonal block, ld kLdI
-  double *tmp = Ti + kTb * kLdI;         // kTb column buffer
-  double *xs = tmp + kTb;                // kTb x nrhs solved block
+  double *Ti = csm;                          // the inverted diagonal block, ld kLdI
+  double *tmp = Ti + kTb * kLdI;             // kTb column buffer
+  double *sb = tmp + kTb;                    // kTb x nrhs: my right-hand sides being reduced
+  double *xj = sb + kTb * kCoopMaxRhs;       // kTb x nrhs: a published solution block
+  double *part = xj + kTb * kCoopMaxRhs;     // 2 x kTb x nrhs: half-row partial sums
+  __shared__ int abort_flag;
   const int tid = threadIdx.x;
   const int nblk = (n + kTb - 1) / kTb;
-  const long long nthreads = (long long)gridDim.x * blockDim.x;
-  const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
+  const int blk = blockIdx.x;
+  if (blk >= nblk) return;
+  const int r0 = blk * kTb, nb = min(kTb, n - r0);
 
   // ---- phase 0: invert my diagonal block ----------------------------------
-  const int myblk = blockIdx.x;
-  if (myblk < nblk) {
-    const int r0 = myblk * kTb, nb = min(kTb, n - r0);
-    for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
-      const int i = idx % nb, k = idx / nb;
-      const bool keep = lower ? (i >= k) : (i <= k);
-      Ti[i + k * kLdI] = keep ? T[(r0 + i) + (size_t)(r0 + k) * ldt] : 0.0;
+  for (int idx = tid; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx % nb, k = idx / nb;
+    const bool keep = lower ? (i >= k) : (i <= k);
+    Ti[i + k * kLdI] = keep ? T[(r0 + i) + (size_t)(r0 + k) * ldt] : 0.0;
+  }
+  for (int idx = tid; idx < nb * nrhs; idx += blockDim.x) {
+    const int k = idx % nb, c = idx / nb;
+    sb[k + c * kTb] = B[(r0 + k) + (size_t)c * ldb];
+  }
+  __syncthreads();
+  if (lower) {
+    // unit lower: columns right to left; X(j+1:, j) = -X(j+1:, j+1:) T(j+1:, j)
+    for (int j = nb - 1; j >= 0; --j) {
+      for (int i = j + 1 + tid; i < nb; i += blockDim.x) {
+        double acc = 0.0;
+        for (int k = j + 1; k <= i; ++k) acc = fma(Ti[i + k * kLdI], Ti[k + j * kLdI], acc);
+        tmp[i] = -acc;
+      }
+      __syncthreads();
+      for (int i = j + 1 + tid; i < nb; i += blockDim.x) Ti[i + j * kLdI] = tmp[i];
+      if (tid == 0) Ti[j + j * kLdI] = 1.0;
+      __syncthreads();
+    }
+  } else {
+    // non-unit upper: columns left to right; X(j, j) = 1 / T(j, j),
+    // X(0:j, j) = -X(j, j) X(0:j, 0:j) T(0:j, j)
+    for (int i = tid; i < nb; i += blockDim.x) xj[i] = 1.0 / Ti[i + i * kLdI];  // all pivots at once
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+      const double djj = xj[j];
+      for (int i = tid; i < j; i += blockDim.x) {
+        double acc = 0.0;
+        for (int k = i; k < j; ++k) acc = fma(Ti[i + k * kLdI], Ti[k + j * kLdI], acc);
+        tmp[i] = -djj * acc;
+      }
+      __syncthreads();
+      for (int i = tid; i < j; i += blockDim.x) Ti[i + j * kLdI] = tmp[i];
+      if (tid == 0) Ti[j + j * kLdI] = djj;
+      __syncthreads();
+    }
+  }
+
+  // ---- the blocks this one depends on, in order ----------------------------
+  const int ndep = lower ? blk : nblk - 1 - blk;
+  const int r = tid & (kTb - 1), half = tid >> 7;  // row of my block, half of the columns
+  for (int t = 0; t < ndep; ++t) {
+    const int j = lower ? t : nblk - 1 - t;
+    const int c0 = j * kTb, nbj = min(kTb, n - c0);
+    // prefetch this thread's half row of T(blk, j) while waiting
+    double trow[kTb / 2];
+    const int k0 = half * (kTb / 2);
+#pragma unroll
+    for (int k = 0; k < kTb / 2; ++k)
+      trow[k] = (r < nb && k0 + k < nbj) ? T[(r0 + r) + (size_t)(c0 + k0 + k) * ldt] : 0.0;
+    if (tid == 0) {
+      const long long tstart = clock64();
+      int ok = 1;
+      while (ld_acquire_gpu(flags + j) == 0) {
+        if (clock64() - tstart > kSolveWaitLimit) {
+          ok = 0;
+          atomicOr(flags + kMaxFlagBlocks, 1);  // the timeout word
+          break;
+        }
+      }
+      abort_flag = !ok;
     }
     __syncthreads();
-    if (lower) {
-      // unit lower: columns right to left; X(j+1:, j) = -X(j+1:, j+1:) T(j+1:, j)
-      for (int j = nb - 1; j >= 0; --j) {
-        for (int i = j + 1 + tid; i < nb; i += blockDim.x) {
-          double acc = 0.0;
-          for (int k = j + 1; k <= i; ++k) acc = fma(Ti[i + k * kLdI], Ti[k + j * kLdI], acc);
-          tmp[i] = -acc;
-        }
-        __syncthreads();
-        for (int i = j + 1 + tid; i < nb; i += blockDim.x) Ti[i + j * kLdI] = tmp[i];
-        if (tid == 0) Ti[j + j * kLdI] = 1.0;
-        __syncthreads();
-      }
+    if (abort_flag) return;
+    for (int idx = tid; idx < nbj * nrhs; idx += blockDim.x) {
+      const int k = idx % nbj, c = idx / nbj;
+      xj[k + c * kTb] = __ldcg(B + (c0 + k) + (size_t)c * ldb);
+    }
+    __syncthreads();
+    if (nrhs == 1) {  // one right-hand side: four independent partial sums
+      double a4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int k = 0; k < kTb / 2; ++k) a4[k & 3] = fma(trow[k], xj[k0 + k], a4[k & 3]);
+      part[half * kTb * kCoopMaxRhs + r] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
     } else {
-      // non-unit upper: columns left to right; X(j, j) = 1 / T(j, j),
-      // X(0:j, j) = -X(j, j) X(0:j, 0:j) T(0:j, j)
-      for (int i = tid; i < nb; i += blockDim.x) xs[i] = 1.0 / Ti[i + i * kLdI];  // all pivots at once
-      __syncthreads();
-      for (int j = 0; j < nb; ++j) {
-        const double djj = xs[j];
-        for (int i = tid; i < j; i += blockDim.x) {
-          double acc = 0.0;
-          for (int k = i; k < j; ++k) acc = fma(Ti[i + k * kLdI], Ti[k + j * kLdI], acc);
-          tmp[i] = -djj * acc;
-        }
-        __syncthreads();
-        for (int i = tid; i < j; i += blockDim.x) Ti[i + j * kLdI] = tmp[i];
-        if (tid == 0) Ti[j + j * kLdI] = djj;
-        __syncthreads();
-      }
-    }
-  }
-  grid.sync();
-
-  for (int s = 0; s < nblk; ++s) {
-    const int blk = lower ? s : nblk - 1 - s;
-    const int r0 = blk * kTb;
-    const int nb = min(kTb, n - r0);
-    // x_blk = T_ii^-1 b_blk by the CTA that holds the inverse
-    if (blockIdx.x == blk) {
-      for (int idx = tid; idx < nb * nrhs; idx += blockDim.x) {
-        const int k = idx % nb, c = idx / nb;
-        xs[k + c * kTb] = B[(r0 + k) + (size_t)c * ldb];
-      }
-      __syncthreads();
-      for (int idx = tid; idx < nb * nrhs; idx += blockDim.x) {
-        const int i = idx % nb, c = idx / nb;
-        double acc = 0.0;
-        for (int k = 0; k < nb; ++k) acc = fma(Ti[i + k * kLdI], xs[k + c * kTb], acc);
-        B[(r0 + i) + (size_t)c * ldb] = acc;
-      }
-    }
-    grid.sync();
-    // rows outside the block: below it (lower) or above it (upper)
-    const int rlo = lower ? r0 + nb : 0, rhi = lower ? n : r0;
-    if (rhi > rlo) {
-      for (int idx = tid; idx < nb * nrhs; idx += blockDim.x) {
-        const int k = idx % nb, c = idx / nb;
-        xs[k + c * kTb] = B[(r0 + k) + (size_t)c * ldb];
-      }
-      __syncthreads();
-      for (long long r = rlo + gtid; r < rhi; r += nthreads) {
-        double acc[kCoopMaxRhs];
+      double acc[kCoopMaxRhs];
 #pragma unroll
-        for (int c = 0; c < kCoopMaxRhs; ++c) acc[c] = 0.0;
-        const double *tr = T + r + (size_t)r0 * ldt;
-#pragma unroll 16
-        for (int k = 0; k < nb; ++k) {  // unrolled: many loads of T in flight per thread
-          const double tv = tr[(size_t)k * ldt];
+      for (int c = 0; c < kCoopMaxRhs; ++c) acc[c] = 0.0;
 #pragma unroll
-          for (int c = 0; c < kCoopMaxRhs; ++c)
-            if (c < nrhs) acc[c] = fma(tv, xs[k + c * kTb], acc[c]);
-        }
+      for (int k = 0; k < kTb / 2; ++k) {
+        const double tv = trow[k];
 #pragma unroll
         for (int c = 0; c < kCoopMaxRhs; ++c)
-          if (c < nrhs) B[r + (size_t)c * ldb] -= acc[c];
+          if (c < nrhs) acc[c] = fma(tv, xj[k0 + k + c * kTb], acc[c]);
       }
+#pragma unroll
+      for (int c = 0; c < kCoopMaxRhs; ++c)
+        if (c < nrhs) part[half * kTb * kCoopMaxRhs + r + c * kTb] = acc[c];
     }
-    grid.sync();
+    __syncthreads();
+    for (int idx = tid; idx < nb * nrhs; idx += blockDim.x) {
+      const int i = idx % nb, c = idx / nb;
+      sb[i + c * kTb] -= part[i + c * kTb] + part[kTb * kCoopMaxRhs + i + c * kTb];
+    }
+    __syncthreads();
   }
+
+  // ---- x = T_blk^-1 b_blk, published ---------------------------------------
+  for (int idx = tid; idx < nb * nrhs; idx += blockDim.x) {
+    const int i = idx % nb, c = idx / nb;
+    double acc = 0.0;
+    for (int k = 0; k < nb; ++k) acc = fma(Ti[i + k * kLdI], sb[k + c * kTb], acc);
+    B[(r0 + i) + (size_t)c * ldb] = acc;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) st_release_gpu(flags + blk, 1);
+}
+
+// Flag words of the dependency-driven solve: one array per (device, caller
+// stream), created on first use (make the first solve on a stream before
+// capturing it in a graph) and kept until the process exits.
+static int *solve_flags_for(cudaStream_t st) {
+  struct Entry {
+    int dev;
+    cudaStream_t st;
+    int *flags;
+  };
+  static std::mutex mu;
+  static Entry pool[64];
+  static int used = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  for (int i = 0; i < used; ++i)
+    if (pool[i].dev == dev && pool[i].st == st) return pool[i].flags;
+  if (used == 64) return nullptr;
+  int *f = nullptr;
+  if (cudaMalloc(&f, (kMaxFlagBlocks + 1) * sizeof(int)) != cudaSuccess) return nullptr;
+  if (cudaMemset(f, 0, (kMaxFlagBlocks + 1) * sizeof(int)) != cudaSuccess) return nullptr;
+  pool[used] = {dev, st, f};
+  return pool[used++].flags;
 }
 
 // one CTA per SM, one diagonal block per CTA
@@ -228,34 +298,50 @@ static int coop_max_n() {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       sms = 1;
   }
-  return sms * kTb;
+  return (sms < kMaxFlagBlocks ? sms : kMaxFlagBlocks) * kTb;
 }
 
-static cudaError_t trsm_left_coop(bool lower, bool unit, int n, int nrhs, const double *T, int ldt, double *B,
-                                  int ldb, cudaStream_t st) {
-  static int grid = 0;
-  const size_t smem = ((size_t)kTb * kLdI + kTb + (size_t)kTb * kCoopMaxRhs) * 8;
-  if (grid == 0) {
-    cudaError_t e = cudaFuncSetAttribute(trsv_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, trsv_coop_kernel, 256, smem)) != cudaSuccess)
-      return e;
-    if (per < 1) return cudaErrorInvalidConfiguration;
-    grid = sms;  // one CTA per SM: every CTA resident, as the grid-wide sync requires
+// 0: launched; 1: not available here (use the per-block path); <0 error
+static int trsm_left_flags(bool lower, bool unit, int n, int nrhs, const double *T, int ldt, double *B, int ldb,
+                           cudaStream_t st, cudaError_t *err) {
+  static bool init = false;
+  const size_t smem = ((size_t)kTb * kLdI + kTb + 4 * (size_t)kTb * kCoopMaxRhs) * 8;
+  if (!init) {
+    cudaError_t e = cudaFuncSetAttribute(trsv_flag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+      *err = e;
+      return -1;
+    }
+    init = true;
+  }
+  int *flags = solve_flags_for(st);
+  if (!flags) return 1;
+  const int nblk = (n + kTb - 1) / kTb;
+  cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)nblk * sizeof(int), st);
+  if (e != cudaSuccess) {
+    *err = e;
+    return -1;
   }
   int lo = lower ? 1 : 0, un = unit ? 1 : 0;
-  void *args[] = {&n, &nrhs, (void *)&T, &ldt, &B, &ldb, &lo, &un};
+  void *args[] = {&n, &nrhs, (void *)&T, &ldt, &B, &ldb, &lo, &un, &flags};
   ProfScope ps(kClsSolve, st, (double)n * n * nrhs);
-  return cudaLaunchCooperativeKernel((void *)trsv_coop_kernel, dim3(grid), dim3(256), args, smem, st);
+  e = cudaLaunchCooperativeKernel((void *)trsv_flag_kernel, dim3(nblk), dim3(256), args, smem, st);
+  if (e != cudaSuccess) {
+    *err = e;
+    return -1;
+  }
+  return 0;
 }
 
 cudaError_t trsm_left(bool lower, bool unit, int n, int nrhs, const double *T, int ldt, double *B,
                       int ldb, cudaStream_t st) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
-  if (nrhs <= kCoopMaxRhs && n > kTb && n <= coop_max_n()) return trsm_left_coop(lower, unit, n, nrhs, T, ldt, B, ldb, st);
+  if (nrhs <= kCoopMaxRhs && n > kTb && n <= coop_max_n()) {
+    cudaError_t err = cudaSuccess;
+    const int rc = trsm_left_flags(lower, unit, n, nrhs, T, ldt, B, ldb, st, &err);
+    if (rc == 0) return cudaSuccess;
+    if (rc < 0) return err;
+  }
   const size_t smem = ((size_t)kTb * (kTb + 1) + (size_t)kTb * 33) * 8;
   static bool init = false;
   if (!init) {
