@@ -42,7 +42,7 @@ struct TsluNodeArgs {
 
 struct TsluSmem {
   // layout inside dynamic shared memory
-  double *tile;     // rloc x bk, ld rloc
+  double *tile;     // rloc x bk, ld rloc | 1 (odd: row accesses across columns hit distinct banks)
   double *prow;     // bk
   double *trow;     // bk
   int *lab;         // rloc labels (panel rows)
@@ -55,7 +55,7 @@ struct TsluSmem {
 };
 
 __host__ __device__ inline size_t tslu_smem_bytes(int rloc, int bk) {
-  size_t s = (size_t)rloc * bk * 8 + 2 * (size_t)bk * 8;
+  size_t s = (size_t)(rloc | 1) * bk * 8 + 2 * (size_t)bk * 8;
   s += (size_t)rloc * 4 + 16 * (kNodeWarps + 1) + 16 * 8 + 16 + 16 + 4 * (size_t)bk * 4 + 64;
   return s;
 }
@@ -63,7 +63,7 @@ __host__ __device__ inline size_t tslu_smem_bytes(int rloc, int bk) {
 __device__ inline TsluSmem tslu_carve(char *base, int rloc, int bk) {
   TsluSmem s;
   s.tile = (double *)base;
-  base += (size_t)rloc * bk * 8;
+  base += (size_t)(rloc | 1) * bk * 8;
   s.prow = (double *)base;
   base += (size_t)bk * 8;
   s.trow = (double *)base;
@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
   const int node = blockIdx.x / G;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bk = a.bk, rloc = a.rloc;
+  const int ldt = rloc | 1;  // tile leading dimension
   extern __shared__ __align__(16) char smem_raw[];
   TsluSmem s = tslu_carve(smem_raw, rloc, bk);
 
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
     for (int i = lane; i < myrows; i += 32) {
       double v = col[s.lab[i]];
       bad |= not_finite(v);
-      s.tile[i + (size_t)k * rloc] = v;
+      s.tile[i + (size_t)k * ldt] = v;
     }
   }
   if (bad && a.dev_info) atomicOr(a.dev_info + 1, CA_STATUS_NONFINITE);
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
     // (a) local argmax over positions >= j of column j
     ArgMax best{0ull, INT_MAX};
     const int i0 = max(j - p0, 0);
-    const double *colj = s.tile + (size_t)j * rloc;
+    const double *colj = s.tile + (size_t)j * ldt;
     for (int i = i0 + tid; i < myrows; i += kNodeThreads)
       best = argmax_better(best, ArgMax{absbits(colj[i]), p0 + i});
     best = warp_argmax(best);
@@ -191,14 +192,14 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
       const int oj = j / rloc, lj = j - oj * rloc;
       const double *tp = (op == rank) ? s.tile : cl.map_shared_rank(s.tile, op);
       for (int k = tid; k < bk; k += kNodeThreads) {
-        const double v = tp[lp + (size_t)k * rloc];
+        const double v = tp[lp + (size_t)k * ldt];
         s.prow[k] = v;
         if (k == j) s.scal[0] = 1.0 / v;  // the pivot's reciprocal, read after the barrier below
       }
       if (tid == 0) s.iscal[1] = (op == rank) ? s.lab[lp] : *cl.map_shared_rank(s.lab + lp, op);
       if (p != j && op == rank) {
         const double *tj = (oj == rank) ? s.tile : cl.map_shared_rank(s.tile, oj);
-        for (int k = tid; k < bk; k += kNodeThreads) s.trow[k] = tj[lj + (size_t)k * rloc];
+        for (int k = tid; k < bk; k += kNodeThreads) s.trow[k] = tj[lj + (size_t)k * ldt];
         if (tid == 0) s.iscal[2] = (oj == rank) ? s.lab[lj] : *cl.map_shared_rank(s.lab + lj, oj);
       }
     } else if (a.is_root && rank == 0 && tid == 0 && a.dev_info) {
@@ -211,11 +212,11 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
       const int op = p / rloc, lp = p - op * rloc;
       const int oj = j / rloc, lj = j - oj * rloc;
       if (oj == rank) {
-        for (int k = tid; k < bk; k += kNodeThreads) s.tile[lj + (size_t)k * rloc] = s.prow[k];
+        for (int k = tid; k < bk; k += kNodeThreads) s.tile[lj + (size_t)k * ldt] = s.prow[k];
         if (tid == 0) s.lab[lj] = s.iscal[1];
       }
       if (op == rank) {
-        for (int k = tid; k < bk; k += kNodeThreads) s.tile[lp + (size_t)k * rloc] = s.trow[k];
+        for (int k = tid; k < bk; k += kNodeThreads) s.tile[lp + (size_t)k * ldt] = s.trow[k];
         if (tid == 0) s.lab[lp] = s.iscal[2];
       }
     }
@@ -224,13 +225,13 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
     if (p != j) __syncthreads();
     const double rinv = s.scal[0];
     const int i1 = max(j + 1 - p0, 0);
-    double *cj = s.tile + (size_t)j * rloc;
+    double *cj = s.tile + (size_t)j * ldt;
     for (int i = i1 + tid; i < myrows; i += kNodeThreads) cj[i] *= rinv;
     __syncthreads();
     // (e) rank-1 update of the trailing columns
     for (int k = j + 1 + warp; k < bk; k += kNodeWarps) {
       const double u = s.prow[k];
-      double *ck = s.tile + (size_t)k * rloc;
+      double *ck = s.tile + (size_t)k * ldt;
       for (int i = i1 + lane; i < myrows; i += 32) ck[i] = fma(-cj[i], u, ck[i]);
     }
     __syncthreads();
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
   // root: L11 \ U11 of the selected rows, and the row permutation
   for (int k = warp; k < bk; k += kNodeWarps)
     for (int i = lane; i < myrows; i += 32)
-      if (p0 + i < bk) a.lu11[(p0 + i) + (size_t)k * a.cand_ld] = s.tile[i + (size_t)k * rloc];
+      if (p0 + i < bk) a.lu11[(p0 + i) + (size_t)k * a.cand_ld] = s.tile[i + (size_t)k * ldt];
   node_sync(cl, G);  // every CTA's labels are final and visible
   if (rank != 0) {
     node_sync(cl, G);  // keep shared memory alive until rank 0 has read it

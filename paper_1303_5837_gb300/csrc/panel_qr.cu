@@ -152,7 +152,91 @@ __global__ void __launch_bounds__(kQrThreads, 1) tsqr_node_kernel(TsqrNodeArgs a
 
   // ---- Householder QR on the distributed tile --------------------------
   const int kmax = min(R, bk);
-  for (int j = 0; j < kmax; ++j) {
+  if (G == 1) {
+    // One CTA holds the node: five barriers per column.  Column j's sub-
+    // diagonal part x is scaled to v = x / (alpha - beta) only at the start
+    // of the next column's pass (sc[6] holds the factor), so the dot
+    // products w_q = tau v^T A(:, q) = tau (A(j, q) + s x^T A(j+1:, q)) and
+    // the update A(:, q) -= v w_q = x (s w_q) read the unscaled column.
+    const int g = tid / (kQrThreads / kQrGroups);
+    const int qq0 = tid - g * (kQrThreads / kQrGroups);
+    if (tid == 0) sc[6] = 1.0;
+    for (int j = 0; j < kmax; ++j) {
+      // pass 1: scale the previous column's v, sum of squares of this one
+      const double sprev = sc[6];
+      double ss = 0.0;
+      for (int i = j + tid; i < myrows; i += kQrThreads) {
+        if (j > 0 && (leaf || fz[i] <= j - 1)) tile[i + (size_t)(j - 1) * ld] *= sprev;
+        if (i > j && (leaf || fz[i] <= j)) {
+          const double v = tile[i + (size_t)j * ld];
+          ss = fma(v, v, ss);
+        }
+      }
+      ss = warp_sum(ss);
+      if (lane == 0) sc[8 + warp] = ss;
+      __syncthreads();
+      if (tid == 0) {
+        double xn2 = 0.0;
+#pragma unroll
+        for (int w2 = 0; w2 < kQrWarps; ++w2) xn2 += sc[8 + w2];
+        const double alpha = tile[j + (size_t)j * ld];
+        if (xn2 == 0.0) {
+          sc[4] = 1.0;
+          sc[6] = 1.0;
+          tau[j] = 0.0;
+        } else {
+          const double nrm = sqrt(fma(alpha, alpha, xn2));
+          const double beta = (alpha >= 0.0) ? -nrm : nrm;
+          tau[j] = (beta - alpha) / beta;
+          sc[6] = 1.0 / (alpha - beta);
+          sc[4] = 0.0;
+          tile[j + (size_t)j * ld] = beta;
+        }
+      }
+      __syncthreads();
+      if (sc[4] != 0.0) continue;
+      const double scal = sc[6], tj = tau[j];
+      // pass 2: partial dot products over rows i = g mod 4, i > j
+      const int nq = bk - j - 1;
+      for (int qq = qq0; qq < nq; qq += kQrThreads / kQrGroups) {
+        const int q = j + 1 + qq;
+        const double *cq = tile + (size_t)q * ld;
+        const double *cj = tile + (size_t)j * ld;
+        double acc = 0.0;
+        for (int i = j + 1 + g; i < myrows; i += kQrGroups)
+          if (leaf || fz[i] <= j) acc = fma(cj[i], cq[i], acc);
+        part[g * bk + q] = (g == 0 ? cq[j] : 0.0) + scal * acc;
+      }
+      __syncthreads();
+      for (int q = j + 1 + tid; q < bk; q += kQrThreads) {
+        double s2 = part[q];
+#pragma unroll
+        for (int g2 = 1; g2 < kQrGroups; ++g2) s2 += part[g2 * bk + q];
+        w[q] = tj * s2;
+      }
+      __syncthreads();
+      // pass 3: A(j, q) -= w_q; A(i, q) -= x_i (s w_q) for i > j
+      for (int qq = qq0; qq < nq; qq += kQrThreads / kQrGroups) {
+        const int q = j + 1 + qq;
+        double *cq = tile + (size_t)q * ld;
+        const double *cj = tile + (size_t)j * ld;
+        const double wq = w[q], swq = scal * wq;
+        if (g == 0) cq[j] -= wq;
+        for (int i = j + 1 + g; i < myrows; i += kQrGroups)
+          if (leaf || fz[i] <= j) cq[i] = fma(-cj[i], swq, cq[i]);
+      }
+      __syncthreads();
+    }
+    // the last column's deferred scaling
+    if (kmax > 0) {
+      const double sprev = sc[6];
+      const int jl = kmax - 1;
+      for (int i = jl + 1 + tid; i < myrows; i += kQrThreads)
+        if (leaf || fz[i] <= jl) tile[i + (size_t)jl * ld] *= sprev;
+    }
+    __syncthreads();
+  }
+  for (int j = 0; j < (G == 1 ? 0 : kmax); ++j) {
     const int oj = j / rloc, lj = j - oj * rloc;
     // (a) partial ||x2||^2 over positions > j (structurally nonzero rows)
     double ss = 0.0;
