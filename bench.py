@@ -626,9 +626,11 @@ OPERATOR_FORMS = [  # (name, panel width, leaf rows, levels, reduction operator)
 def operator_diagnostics(a, ca, torch, dev, count=64, n=512):
     """Stability of the reduction operators on `count` seeded N(0, 1)
     matrices of order n, each form one batched launch: growth max|U| / max|A|,
-    normwise backward error ||P A - L U||_F / ||A||_F and max |L| (median and
-    worst over the sample), and the launch time.  GEPP is CALU with one leaf
-    holding every row (blocked GEPP)."""
+    normwise backward error ||P A - L U||_F / ||A||_F, max |L| and the pivot
+    threshold tau_min = 1 / max |L| (at step k the Schur complement's column
+    is L(k:, k) U(k, k)), the componentwise backward error of a solve with
+    the factors (median and worst over the sample), and the launch time.  GEPP
+    is CALU with one leaf holding every row (blocked GEPP)."""
     gen = torch.Generator(device=dev).manual_seed(4242)
     A0 = [torch.randn(n, n, dtype=torch.float64, device=dev, generator=gen).t() for _ in range(count)]
     out = {"matrices": count, "n": n}
@@ -645,7 +647,8 @@ def operator_diagnostics(a, ca, torch, dev, count=64, n=512):
         bf.run()
         e1.record()
         e1.synchronize()
-        growth, berr, lmax = [], [], []
+        growth, berr, lmax, cberr = [], [], [], []
+        xt = torch.ones(n, 1, dtype=torch.float64, device=dev)
         for i, (F, A) in enumerate(zip(mats, A0)):
             Lf = torch.tril(F, -1) + torch.eye(n, dtype=F.dtype, device=dev)
             U = torch.triu(F)
@@ -655,10 +658,17 @@ def operator_diagnostics(a, ca, torch, dev, count=64, n=512):
             growth.append(float(U.abs().max() / A.abs().max()))
             berr.append(float(torch.linalg.norm(A[perm] - Lf @ U) / torch.linalg.norm(A)))
             lmax.append(float(Lf.abs().max()))
+            # componentwise backward error of a solve with these factors
+            bb = A @ xt
+            y = torch.linalg.solve_triangular(Lf, bb[perm], upper=False, unitriangular=True)
+            x = torch.linalg.solve_triangular(U, y, upper=True)
+            cberr.append(float(((bb - A @ x).abs() / (A.abs() @ x.abs() + bb.abs())).max()))
         out[name] = {"b": b, "leaf_rows": L, "operator": op, "ms": e0.elapsed_time(e1),
                      "growth_median": statistics.median(growth), "growth_max": max(growth),
                      "berr_median": statistics.median(berr), "berr_max": max(berr),
-                     "lmax_max": max(lmax), "nonzero_info": int((bf.info_all != 0).sum())}
+                     "lmax_max": max(lmax), "tau_min": 1.0 / max(lmax),
+                     "componentwise_berr_max": max(cberr),
+                     "nonzero_info": int((bf.info_all != 0).sum())}
     return out
 
 

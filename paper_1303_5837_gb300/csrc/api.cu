@@ -1,12 +1,23 @@
 // api.cu -- the C-ABI: argument checks, the reduction-tree plan, workspace
 // layout and the panel loops of CALU and CAQR (host side; every step runs in
 // the kernels of panel_lu.cu, panel_qr.cu, gemm_fp64.cu and solve.cu).
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstring>
 #include <mutex>
 
 #include "ca_internal.cuh"
 
 namespace cagb {
+
+// NVTX range around a host-side step (a panel of CALU / CAQR): visible in a
+// timeline profiler, a null operation when none is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Largest node tile (rows) of a panel: a leaf, or a merge of max_cnt sets.
 static int max_node_rows(const Plan &p, int mk, int leaf_rows, int bk) {
@@ -147,6 +158,7 @@ int calu_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int
     return gemm_minus_f64(mrows, ncols, kdim, L21, lda, U12, lda, C, lda, stream);
   };
   for (int kb = 0; kb < K; kb += b) {
+    NvtxRange range("calu panel");
     const int bk = (K - kb < b) ? K - kb : b;
     const int mk = m - kb;
     Plan plan;
@@ -202,6 +214,7 @@ int caqr_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, dou
   if (la && cudaEventRecord(la->ev_next, stream) != cudaSuccess) return CA_ERR_LAUNCH;
   size_t off = 0;
   for (int kb = 0, k = 0; kb < n; kb += b, ++k) {
+    NvtxRange range("caqr panel");
     const int bk = (n - kb < b) ? n - kb : b;
     const int mk = m - kb;
     Plan plan;
