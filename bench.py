@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--b", type=int, default=128)
     p.add_argument("--leaf", type=int, default=BENCH_LEAF_ROWS)
+    p.add_argument("--tree", default=BENCH_TREE,
+                   help="reduction-tree levels: fan-in + b (binary) or f (flat), last fan-in 0")
     p.add_argument("--cond", type=float, default=1e6)
     p.add_argument("--nrhs", type=int, default=1)
     p.add_argument("--e2e-steps", type=int, default=1)
@@ -97,15 +99,37 @@ def step_flops(n: int, nrhs: int) -> float:
     return lu + qr + getrs + geqrs
 
 
-TREE_LEVELS = [(4, 0), (0, 0)]  # binary merges: 4 leaves per cluster group, then the grid
+BENCH_TREE = "4f,0f"  # one flat merge per group of 4 leaves, then one flat merge of the groups
+
+
+def parse_tree(spec: str):
+    """Reduction-tree levels from "f<style>,..." (fan-in, b = binary merges,
+    f = one flat merge of the group; fan-in 0 = all remaining nodes)."""
+    out = []
+    for tok in spec.split(","):
+        tok = tok.strip()
+        if not tok or tok[-1] not in "bf" or not tok[:-1].isdigit():
+            raise ValueError(f"bad tree level {tok!r} (want e.g. 4b or 0f)")
+        out.append((int(tok[:-1]), 0 if tok[-1] == "b" else 1))
+    if out[-1][0] != 0:
+        raise ValueError("the last tree level must have fan-in 0 (all remaining nodes)")
+    return out
+
+
+def describe_tree(levels) -> str:
+    words = []
+    for f, st in levels:
+        kind = "binary" if st == 0 else "flat"
+        words.append(f"{kind} merges over {'all remaining nodes' if f == 0 else f'groups of {f}'}")
+    return ", then ".join(words)
 
 
 def workload_config(a, extra=None):
     c = {
         "workload": (f"CALU+getrs and CAQR+geqrs of one {a.n}x{a.n} FP64 matrix "
                      f"(A = U diag(s) V^T, cond {a.cond:g}), b={a.b}, leaves of {a.leaf} rows, "
-                     f"binary reduction tree, {a.nrhs} RHS"),
-        "n": a.n, "b": a.b, "leaf_rows": a.leaf, "tree": "binary (fan-in 4 level, then all)",
+                     f"reduction tree {a.tree}, {a.nrhs} RHS"),
+        "n": a.n, "b": a.b, "leaf_rows": a.leaf, "tree": describe_tree(parse_tree(a.tree)),
         "cond": a.cond, "nrhs": a.nrhs, "precision": "plain FP64",
         "l2": "inputs (8 n^2 bytes) larger than the 129 MB L2",
     }
@@ -179,7 +203,7 @@ def oracle_sample(a, n: int):
     from paper_1303_5837_gb300 import inputs
     A = inputs.conditioned(n, a.cond, 2026)
     B = inputs.rhs(n, a.nrhs, 2027)
-    tree = oracle.make_tree(a.leaf, TREE_LEVELS)
+    tree = oracle.make_tree(a.leaf, parse_tree(a.tree))
     oracle.build()
     t0 = time.perf_counter()
     LU, ipiv, _, _ = oracle.calu(A, a.b, tree)
@@ -270,7 +294,7 @@ def run_ours(a, rank: int, world: int, local: int):
             print(json.dumps({"batched": {a.only_batch: out}}), flush=True)
         return
     n, b, nrhs = a.n, a.b, a.nrhs
-    tree = ca.make_tree(a.leaf, TREE_LEVELS)
+    tree = ca.make_tree(a.leaf, parse_tree(a.tree))
 
     # ---- inputs (untimed): A = U diag(s) V^T, B = A x_true ------------------
     A0 = conditioned_device(n, a.cond, 2026 + rank, dev)

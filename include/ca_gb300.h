@@ -346,7 +346,8 @@ int ca_batched_factor(const void *plan_host, const void *plan_dev, void *work, s
 /* time per kernel class, measured with CUDA events recorded on the stream   */
 /* each kernel is launched on.  Classes: 0 tslu_node, 1 laswp, 2 lu_finish,  */
 /* 3 trsm_u12, 4 gemm_fp64, 5 tsqr_node, 6 tree_apply, 7 solve,              */
-/* 8 split_bf16, 9 gemm_tc, 10 refine, 11 batched.                           */
+/* 8 split_bf16, 9 gemm_tc, 10 refine, 11 batched, 12 tree_narrow (the      */
+/* tree update of a few columns, or of too few column tiles to fill the GPU).*/
 /* ------------------------------------------------------------------------ */
 
 /* on = 1: create a pool of 2 * max_launches events (here, not during a

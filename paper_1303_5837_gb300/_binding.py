@@ -98,7 +98,8 @@ SYMBOLS = ("ca_strerror", "ca_calu_workspace", "ca_caqr_workspace", "ca_geqrs_wo
            "calu_factor_mixed", "ca_gesv_mixed_workspace", "calu_gesv_mixed", "ca_caqr_mixed_workspace",
            "caqr_factor_mixed", "ca_batched_plan", "ca_batched_factor")
 KERNEL_CLASSES = ("tslu_node", "laswp", "lu_finish", "trsm_u12", "gemm_fp64", "tsqr_node",
-                  "tree_apply", "solve", "split_bf16", "gemm_tc", "refine", "batched")
+                  "tree_apply", "solve", "split_bf16", "gemm_tc", "refine", "batched",
+                  "tree_narrow")
 
 
 def lib_path() -> str:

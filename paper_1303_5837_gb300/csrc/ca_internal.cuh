@@ -175,6 +175,7 @@ enum KernelClass {
   kClsGemmTc,
   kClsRefine,
   kClsBatched,
+  kClsTreeNarrow,
   kNumClasses
 };
 

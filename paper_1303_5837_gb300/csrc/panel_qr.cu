@@ -662,6 +662,210 @@ __global__ void __launch_bounds__(kApThreads, 1) tree_apply_kernel(ApplyArgs a) 
 }
 
 // ---------------------------------------------------------------------------
+// Narrow tree update: the operation of tree_apply_kernel on NC <= 8 columns
+// per CTA, with the threads spread over the reflectors and the rows instead
+// of over 32 columns, so that no multiply-add works on padding columns.  It
+// serves Q^T B with few right-hand sides and updates whose 32-column tiles
+// would not give every SM a CTA (the look-ahead update of the next panel's
+// columns, the last panels).  Every FP64 multiply-add costs 16 cycles of an
+// SM's FP64 pipe per warp, so only the multiply-adds executed matter.
+//   phase 1: thread (k = tid % 128, row half h = tid / 128) sums
+//            Y(i, k) C(i, :) over its 16 rows of each 32-row chunk;
+//   phase 2: W <- T^T W, thread (k, column parity);
+//   phase 3: thread (row i = tid % 32, k-slice q = tid / 32 of 16 reflectors)
+//            sums Y(i, k) W(k, :) over its slice; the 8 slices are added in
+//            shared memory and subtracted from C.
+// ---------------------------------------------------------------------------
+constexpr int kNcChunk = 32;
+
+template <int NC>
+__global__ void __launch_bounds__(kApThreads, 2) tree_apply_narrow_kernel(ApplyArgs a) {
+  extern __shared__ __align__(16) double nsm_[];
+  const int bk = a.bk;
+  const int ldy = bk + 1;
+  double *Ys = nsm_;                       // kNcChunk x ldy (row-major chunk of Y)
+  double *Cs = Ys + kNcChunk * ldy;        // kNcChunk x NC
+  double *Ws = Cs + kNcChunk * NC;         // 128 x NC
+  double *red = Ws + 128 * NC;             // 8 x kNcChunk x NC (phase 3), 128 x NC (phase 1)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int node = blockIdx.x;
+  const int c0 = blockIdx.y * NC;
+  const int ncl = min(NC, a.ncols - c0);
+
+  int start = 0, cnt = 1, midx = 0, kk;
+  int lrow0 = 0, lrows = 0;
+  if (a.is_leaf) {
+    lrow0 = node * a.leaf_rows;
+    lrows = min(a.leaf_rows, a.mk - lrow0);
+    kk = min(lrows, bk);
+    if (blockIdx.y == 0 && tid == 0) {
+      a.top_out[node] = lrow0;
+      a.c_out[node] = kk;
+    }
+  } else {
+    round_node(a.rd, node, start, cnt, midx);
+    int R = 0;
+    for (int ch = 0; ch < cnt; ++ch) R += a.c_in[start + ch];
+    kk = min(R, bk);
+    if (blockIdx.y == 0 && tid == 0) {
+      a.top_out[node] = a.top_in[start];
+      a.c_out[node] = (cnt == 1) ? a.c_in[start] : kk;
+    }
+    if (cnt == 1) return;
+  }
+  const double *T = a.Tp + (size_t)(a.is_leaf ? node : a.nleaves + midx) * a.b * a.b;
+  const int nseg = a.is_leaf ? 1 : cnt;
+  auto segment = [&](int sg, int &srow, int &srows, int &type) {
+    if (a.is_leaf) {
+      srow = lrow0;
+      srows = lrows;
+      type = 0;
+    } else {
+      srow = a.top_in[start + sg];
+      srows = a.c_in[start + sg];
+      type = (sg == 0) ? 1 : 2;
+    }
+  };
+  // Y chunk (rows r0 .. r0 + nr - 1 of the segment) into Ys, rows fastest
+  // (coalesced column reads); zero outside the stored structure
+  auto stage_y = [&](int srow, int type, int r0, int nr) {
+    for (int idx = tid; idx < kNcChunk * bk; idx += kApThreads) {
+      const int i = idx % kNcChunk, k = idx / kNcChunk;
+      const int gi = r0 + i;
+      double y = 0.0;
+      if (i < nr) {
+        if (type == 0)
+          y = (gi > k) ? a.P[srow + gi + (size_t)k * a.lda] : (gi == k ? 1.0 : 0.0);
+        else
+          y = (gi <= k) ? a.P[srow + gi + (size_t)k * a.lda] : 0.0;
+      }
+      Ys[i * ldy + k] = y;
+    }
+  };
+
+  // ---- phase 1: W = Y^T C ---------------------------------------------
+  const int k1 = tid & 127, h1 = tid >> 7;
+  const int ks1 = 32 * ((tid >> 5) & 3);  // first reflector of this warp's slice
+  double acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+  for (int sg = 0; sg < nseg; ++sg) {
+    int srow, srows, type;
+    segment(sg, srow, srows, type);
+    if (type == 1) {  // identity block: W(k, :) += C(k, :)
+      if (h1 == 0 && k1 < srows) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (c < ncl) acc[c] += a.C[srow + k1 + (size_t)(c0 + c) * a.ldc];
+      }
+      continue;
+    }
+    for (int r0 = 0; r0 < srows; r0 += kNcChunk) {
+      const int nr = min(kNcChunk, srows - r0);
+      __syncthreads();
+      stage_y(srow, type, r0, nr);
+      for (int idx = tid; idx < kNcChunk * NC; idx += kApThreads) {
+        const int i = idx % kNcChunk, c = idx / kNcChunk;
+        Cs[i * NC + c] = (i < nr && c < ncl) ? a.C[srow + r0 + i + (size_t)(c0 + c) * a.ldc] : 0.0;
+      }
+      __syncthreads();
+      // rows of this thread: r0 + 16 h1 .. r0 + 16 h1 + 15; the warp's slice
+      // holds nonzeros only if some k >= ks1 is <= the last row (leaf,
+      // unit lower) or some k <= ks1 + 31 is >= the first row (merge, upper)
+      const int i0 = 16 * h1, i1 = min(16 * h1 + 16, nr);
+      const bool live = k1 < bk && i0 < i1 &&
+                        (type == 0 ? ks1 <= r0 + i1 - 1 : ks1 + 31 >= r0 + i0);
+      if (live) {
+        for (int i = i0; i < i1; ++i) {
+          const double y = Ys[i * ldy + k1];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[c] = fma(y, Cs[i * NC + c], acc[c]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (h1 == 1) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) red[k1 * NC + c] = acc[c];
+  }
+  __syncthreads();
+  if (h1 == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) Ws[k1 * NC + c] = acc[c] + red[k1 * NC + c];
+  }
+  __syncthreads();
+
+  // ---- phase 2: W <- T^T W (T upper triangular, kk x kk) ------------------
+  double s[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) s[c] = 0.0;
+  if (k1 < kk) {
+    const double *Tk = T + (size_t)k1 * a.b;
+    for (int l = 0; l <= k1; ++l) {
+      const double t = __ldg(Tk + l);
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if ((c & 1) == h1) s[c] = fma(t, Ws[l * NC + c], s[c]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if ((c & 1) == h1) Ws[k1 * NC + c] = s[c];  // zero for k >= kk
+  __syncthreads();
+
+  // ---- phase 3: C -= Y W ----------------------------------------------------
+  const int kq = 16 * warp;  // this warp's 16 reflectors
+  for (int sg = 0; sg < nseg; ++sg) {
+    int srow, srows, type;
+    segment(sg, srow, srows, type);
+    if (type == 1) {
+      for (int idx = tid; idx < srows * ncl; idx += kApThreads) {
+        const int i = idx % srows, c = idx / srows;
+        a.C[srow + i + (size_t)(c0 + c) * a.ldc] -= Ws[i * NC + c];
+      }
+      continue;
+    }
+    for (int r0 = 0; r0 < srows; r0 += kNcChunk) {
+      const int nr = min(kNcChunk, srows - r0);
+      __syncthreads();
+      stage_y(srow, type, r0, nr);
+      __syncthreads();
+      // nonzero reflectors of the chunk: k <= r0 + 31 (leaf), k >= r0 (merge)
+      const int k_lo = max(kq, type == 2 ? r0 : 0);
+      const int k_hi = min(min(kq + 16, bk), type == 0 ? r0 + kNcChunk : bk);
+      double p[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) p[c] = 0.0;
+      if (lane < nr) {
+        for (int k = k_lo; k < k_hi; ++k) {
+          const double y = Ys[lane * ldy + k];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) p[c] = fma(y, Ws[k * NC + c], p[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) red[(warp * kNcChunk + lane) * NC + c] = p[c];
+      __syncthreads();
+      for (int o = tid; o < kNcChunk * NC; o += kApThreads) {
+        const int i = o % kNcChunk, c = o / kNcChunk;
+        if (i < nr && c < ncl) {
+          double v = 0.0;
+#pragma unroll
+          for (int q = 0; q < kApThreads / 32; ++q) v += red[(q * kNcChunk + i) * NC + c];
+          a.C[srow + r0 + i + (size_t)(c0 + c) * a.ldc] -= v;
+        }
+      }
+    }
+  }
+}
+
+size_t narrow_smem_bytes(int bk, int nc) {
+  return ((size_t)kNcChunk * (bk + 1) + kNcChunk * nc + 128 * nc + (size_t)(kApThreads / 32) * kNcChunk * nc) * 8;
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 size_t qr_panel_ws_bytes(int nleaves_max) { return 4 * align256((size_t)nleaves_max * 4); }
@@ -769,11 +973,25 @@ cudaError_t tree_apply_qt(int mk, int bk, int b, const double *P, int lda, int l
   const int ldy = bk + 1;
   size_t smem = ((size_t)kChunk * ldy + kChunk * kCs + (size_t)bk * kCt + (size_t)bk * ldy) * 8;
   static bool init = false;
+  static int sms = 0;
   if (!init) {
     const size_t most = ((size_t)kChunk * 129 + kChunk * kCs + 128 * kCt + 128 * 129) * 8;
     cudaError_t e = cudaFuncSetAttribute(tree_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)most);
     if (e != cudaSuccess) return e;
+    const int nmost = (int)narrow_smem_bytes(128, 8);
+    if ((e = cudaFuncSetAttribute(tree_apply_narrow_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  nmost)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(tree_apply_narrow_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  nmost)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(tree_apply_narrow_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  nmost)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(tree_apply_narrow_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  nmost)) != cudaSuccess)
+      return e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     init = true;
   }
   ApplyArgs a = {};
@@ -789,6 +1007,25 @@ cudaError_t tree_apply_qt(int mk, int bk, int b, const double *P, int lda, int l
   a.ldc = ldc;
   a.ncols = ncols;
   const int ntiles = (ncols + kCt - 1) / kCt;
+  // narrow kernel for a few columns, or when the 32-column tiles of the leaf
+  // update would leave SMs without a CTA
+  const int nc = ncols <= 1 ? 1 : ncols <= 2 ? 2 : ncols <= 4 ? 4 : 8;
+  const bool narrow = ncols <= 8 || (long long)plan.nleaves * ntiles < sms;
+  const int gy = narrow ? (ncols + nc - 1) / nc : ntiles;
+  const size_t nsmem = narrow_smem_bytes(bk, nc);
+  auto launch = [&](int gx) {
+    const dim3 grid(gx, gy);
+    if (!narrow)
+      tree_apply_kernel<<<grid, kApThreads, smem, st>>>(a);
+    else if (nc == 1)
+      tree_apply_narrow_kernel<1><<<grid, kApThreads, nsmem, st>>>(a);
+    else if (nc == 2)
+      tree_apply_narrow_kernel<2><<<grid, kApThreads, nsmem, st>>>(a);
+    else if (nc == 4)
+      tree_apply_narrow_kernel<4><<<grid, kApThreads, nsmem, st>>>(a);
+    else
+      tree_apply_narrow_kernel<8><<<grid, kApThreads, nsmem, st>>>(a);
+  };
   a.is_leaf = 1;
   a.top_out = ws.top[0];
   a.c_out = ws.c[0];
@@ -801,8 +1038,8 @@ cudaError_t tree_apply_qt(int mk, int bk, int b, const double *P, int lda, int l
       const double k = r < bk ? r : bk;
       f += (4.0 * (r * k - k * (k - 1) / 2.0) + k * (k + 1)) * ncols;
     }
-    ProfScope ps(kClsTreeApply, st, f);
-    tree_apply_kernel<<<dim3(plan.nleaves, ntiles), kApThreads, smem, st>>>(a);
+    ProfScope ps(narrow ? kClsTreeNarrow : kClsTreeApply, st, f);
+    launch(plan.nleaves);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -826,8 +1063,8 @@ cudaError_t tree_apply_qt(int mk, int bk, int b, const double *P, int lda, int l
         round_node(rd, o, s0, cnt, mi);
         if (cnt >= 2) f += (4.0 * (cnt - 1) * kb2 * (kb2 + 1) / 2.0 + kb2 * (kb2 + 1) + 2.0 * kb2) * ncols;
       }
-      ProfScope ps(kClsTreeApply, st, f);
-      tree_apply_kernel<<<dim3(plan.r[r].n_out, ntiles), kApThreads, smem, st>>>(a);
+      ProfScope ps(narrow ? kClsTreeNarrow : kClsTreeApply, st, f);
+      launch(plan.r[r].n_out);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -34,7 +34,8 @@ Prof &prof() {
 }
 const char *kNames[kNumClasses] = {"tslu_node", "laswp",      "lu_finish", "trsm_u12",
                                    "gemm_fp64", "tsqr_node",  "tree_apply", "solve",
-                                   "split_bf16", "gemm_tc",    "refine",   "batched"};
+                                   "split_bf16", "gemm_tc",    "refine",   "batched",
+                                   "tree_narrow"};
 }  // namespace
 
 ProfScope::ProfScope(int cls, cudaStream_t st, double flops) : cls_(cls), st_(st), flops_(flops) {

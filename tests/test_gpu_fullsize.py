@@ -12,6 +12,7 @@ forms against the FP64 form.
 import numpy as np
 import pytest
 
+import bench
 import oracle
 from paper_1303_5837_gb300 import inputs
 
@@ -19,7 +20,7 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 TREE4 = [(4, 0), (8, 0), (0, 0)]   # leaves in groups of 4, then 8, then the grid
-BENCH_TREE = [(4, 0), (0, 0)]
+BENCH_TREE = bench.parse_tree(bench.BENCH_TREE)
 
 
 @pytest.fixture(scope="module")

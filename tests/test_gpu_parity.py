@@ -202,6 +202,29 @@ def test_geqrs(ca):
     assert rel(to_host(Bd)[:n], x_o) < TOL
 
 
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 5, 8, 9, 40])
+@pytest.mark.parametrize("tname", ["binary", "flat3_binary"])
+def test_geqrs_nrhs(ca, nrhs, tname):
+    """Q^T B through the tree with 1 to 40 right-hand sides (column groups of
+    1, 2, 4 and 8, a ragged last group), ragged leaves (1337 = 8 x 160 + 57),
+    a panel width that is not a multiple of 32 and a ragged last panel
+    (300 = 6 x 48 + 12), binary merges and flat merges of three children."""
+    m, n, b, L = 1337, 300, 48, 160
+    tree = TREES[tname]
+    A = inputs.gaussian(m, n, 41 + nrhs)
+    B = inputs.rhs(m, nrhs, 42 + nrhs)
+    QR_o, T_o = oracle.caqr(A, b, oracle.make_tree(L, tree))
+    x_o = oracle.geqrs(QR_o, T_o, b, oracle.make_tree(L, tree), B)
+    Ad = to_dev(A)
+    t = ca.make_tree(L, tree)
+    qtree, _ = ca.caqr_factor(Ad, b, t)
+    Bd = to_dev(B)
+    ca.caqr_geqrs(Ad, b, t, qtree, Bd)
+    torch.cuda.synchronize()
+    assert rel(to_host(Ad), QR_o) < TOL
+    assert rel(to_host(Bd)[:n], x_o) < TOL
+
+
 def test_repeat_is_deterministic(ca):
     A = inputs.gaussian(2048, 2048 // 4, 77)
     outs = []
