@@ -247,23 +247,42 @@ def run_reference(a, rank: int, world: int):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
-def traffic_for(kernel: str):
+def source_text(csrc: str, item: str) -> bytes:
+    """Bytes of one source item of profiles/traffic.txt: a whole file
+    ("panel_qr.cu") or the lines between "// @region NAME" and
+    "// @endregion NAME" of a file ("panel_qr.cu#NAME")."""
+    fname, _, region = item.partition("#")
+    with open(os.path.join(csrc, fname), "rb") as fh:
+        data = fh.read()
+    if not region:
+        return data
+    begin = f"// @region {region}\n".encode()
+    end = f"// @endregion {region}".encode()
+    i = data.find(begin)
+    j = data.find(end, i + len(begin)) if i >= 0 else -1
+    if i < 0 or j < 0:
+        return b""
+    return data[i + len(begin):j]
+
+
+def traffic_for(kernel: str, plan: str):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary
-    (profiles/traffic.txt: kernel, its source files, a hash of them, bytes),
-    if the counters were taken on the current sources of that kernel."""
+    (profiles/traffic.txt: kernel, its source items, a hash of them, bytes,
+    plan=n/b/leaf_rows/tree/launches per step), if the counters were taken on
+    the current code of that kernel and the per-launch figure was derived for
+    this run's plan of launches."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     csrc = os.path.join(ROOT, "paper_1303_5837_gb300", "csrc")
     for ln in open(path):
         p = ln.split()
-        if len(p) < 4 or p[0] != kernel:
+        if len(p) < 5 or p[0] != kernel or not p[4].startswith("plan="):
             continue
         h = hashlib.sha256()
-        for f in p[1].split(","):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
-        if h.hexdigest()[:16] == p[2]:
+        for item in p[1].split(","):
+            h.update(source_text(csrc, item))
+        if h.hexdigest()[:16] == p[2] and p[4][len("plan="):] == plan:
             return float(p[3])
     return None
 
@@ -443,7 +462,8 @@ def run_ours(a, rank: int, world: int, local: int):
         "config": workload_config(a, {"parallelism": f"replicas{world}" if world > 1 else "single"}),
         "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
                      "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
-                     "traffic": traffic_for(dom),
+                     "traffic": traffic_for(dom, f"{n}/{b}/{a.leaf}/{a.tree}/"
+                                                 f"{round(dk['launches'] / a.steps)}"),
                      "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -31,6 +31,7 @@
 #include <cuda_bf16.h>
 
 #include "ca_internal.cuh"
+#include "device_once.cuh"
 
 namespace cagb {
 
@@ -660,12 +661,11 @@ cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st) {
   a.sign = g.sign > 0 ? 1 : -1;
   a.status = status;
   const size_t smem = cfg.smem;
-  static bool init = false;
-  if (!init) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBudget);
-    if (e != cudaSuccess) return e;
-    init = true;
-  }
+  static std::atomic<unsigned long long> init{0};
+  e = once_per_device(init, [] {
+    return cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBudget);
+  });
+  if (e != cudaSuccess) return e;
   dim3 grid(mp / kTcBM, np / bn, g.nbatch);
   // bf16 tensor-core flops issued: S (S + 1) / 2 digit products
   ProfScope ps(kClsGemmTc, st, 2.0 * (double)mp * np * kp * (S * (S + 1) / 2) * nb);

@@ -12,6 +12,7 @@
 #include <climits>
 
 #include "ca_internal.cuh"
+#include "device_once.cuh"
 
 namespace cagb {
 
@@ -467,13 +468,12 @@ static double gepp_flops(double r, double c) {
 }
 
 static cudaError_t launch_tslu_node(const TsluNodeArgs &args, int nodes, int G, cudaStream_t st) {
-  static bool init = false;
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(tslu_node_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kNodeSmemBudget + 4096);
-    if (e != cudaSuccess) return e;
-    init = true;
-  }
+  static std::atomic<unsigned long long> init{0};
+  cudaError_t e = once_per_device(init, [] {
+    return cudaFuncSetAttribute(tslu_node_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kNodeSmemBudget + 4096);
+  });
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   const double rows = args.is_leaf ? (args.leaf_rows < args.mk ? args.leaf_rows : args.mk)
                                    : (double)args.rd.max_cnt * args.bk;
@@ -556,13 +556,11 @@ cudaError_t laswp_apply(int ncols, double *A, int lda, int row0, const LuPanelWs
 
 cudaError_t lu_panel_finish(int mk, int bk, double *P, int lda, const LuPanelWs &ws,
                             cudaStream_t st) {
-  static bool init = false;
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(lu_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         220 * 1024);
-    if (e != cudaSuccess) return e;
-    init = true;
-  }
+  static std::atomic<unsigned long long> init{0};
+  cudaError_t e = once_per_device(init, [] {
+    return cudaFuncSetAttribute(lu_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  });
+  if (e != cudaSuccess) return e;
   int rt = 8192 / bk;  // 64 KiB row tile
   if (rt > 256) rt = 256;
   size_t smem = ((size_t)bk * bk + bk + (size_t)rt * bk) * 8;
@@ -575,13 +573,11 @@ cudaError_t lu_panel_finish(int mk, int bk, double *P, int lda, const LuPanelWs 
 
 cudaError_t trsm_u12(int bk, int nt, const double *L11, int ldl, double *A12, int lda,
                      cudaStream_t st) {
-  static bool init = false;
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(trsm_u12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         220 * 1024);
-    if (e != cudaSuccess) return e;
-    init = true;
-  }
+  static std::atomic<unsigned long long> init{0};
+  cudaError_t e = once_per_device(init, [] {
+    return cudaFuncSetAttribute(trsm_u12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  });
+  if (e != cudaSuccess) return e;
   if (nt <= 0 || bk <= 1) return cudaSuccess;
   int ct = 8192 / bk;
   if (ct > 128) ct = 128;

@@ -10,6 +10,7 @@
 // the same reflector (Sec. 3.1: leaves factored, then the R factors
 // eliminated two by two; Q kept as Y T Y^T).
 #include "ca_internal.cuh"
+#include "device_once.cuh"
 
 namespace cagb {
 
@@ -389,6 +390,7 @@ __global__ void __launch_bounds__(kQrThreads, 1) tsqr_node_kernel(TsqrNodeArgs a
   }
 }
 
+// @region tree_apply_kernel
 // ---------------------------------------------------------------------------
 // Tree update: C <- Q_node^T C for every node (leaves, then merge rounds).
 // One CTA per (node, tile of kCt columns).  W = Y^T C accumulated in
@@ -661,6 +663,8 @@ __global__ void __launch_bounds__(kApThreads, 1) tree_apply_kernel(ApplyArgs a) 
   }
 }
 
+// @endregion tree_apply_kernel
+// @region tree_apply_narrow_kernel
 // ---------------------------------------------------------------------------
 // Narrow tree update: the operation of tree_apply_kernel on NC <= 8 columns
 // per CTA, with the threads spread over the reflectors and the rows instead
@@ -865,6 +869,7 @@ size_t narrow_smem_bytes(int bk, int nc) {
   return ((size_t)kNcChunk * (bk + 1) + kNcChunk * nc + 128 * nc + (size_t)(kApThreads / 32) * kNcChunk * nc) * 8;
 }
 
+// @endregion tree_apply_narrow_kernel
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -895,13 +900,12 @@ static int pick_qr_cluster(int R, int bk, int nodes, int *rloc, int *ld) {
 }
 
 static cudaError_t launch_tsqr_node(const TsqrNodeArgs &args, int nodes, int G, cudaStream_t st) {
-  static bool init = false;
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(tsqr_node_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kQrSmemBudget + 4096);
-    if (e != cudaSuccess) return e;
-    init = true;
-  }
+  static std::atomic<unsigned long long> init{0};
+  cudaError_t e = once_per_device(init, [] {
+    return cudaFuncSetAttribute(tsqr_node_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kQrSmemBudget + 4096);
+  });
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   const double r = args.is_leaf ? (args.leaf_rows < args.mk ? args.leaf_rows : args.mk)
                                 : (double)args.rd.max_cnt * args.bk;
@@ -972,28 +976,22 @@ cudaError_t tree_apply_qt(int mk, int bk, int b, const double *P, int lda, int l
   if (bk > 128) return cudaErrorInvalidValue;
   const int ldy = bk + 1;
   size_t smem = ((size_t)kChunk * ldy + kChunk * kCs + (size_t)bk * kCt + (size_t)bk * ldy) * 8;
-  static bool init = false;
-  static int sms = 0;
-  if (!init) {
+  static std::atomic<unsigned long long> init{0};
+  cudaError_t e = once_per_device(init, [] {
     const size_t most = ((size_t)kChunk * 129 + kChunk * kCs + 128 * kCt + 128 * 129) * 8;
-    cudaError_t e = cudaFuncSetAttribute(tree_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)most);
-    if (e != cudaSuccess) return e;
     const int nmost = (int)narrow_smem_bytes(128, 8);
-    if ((e = cudaFuncSetAttribute(tree_apply_narrow_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  nmost)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(tree_apply_narrow_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  nmost)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(tree_apply_narrow_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  nmost)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(tree_apply_narrow_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  nmost)) != cudaSuccess)
-      return e;
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    init = true;
-  }
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t r;
+    if ((r = cudaFuncSetAttribute(tree_apply_kernel, a, (int)most)) != cudaSuccess ||
+        (r = cudaFuncSetAttribute(tree_apply_narrow_kernel<1>, a, nmost)) != cudaSuccess ||
+        (r = cudaFuncSetAttribute(tree_apply_narrow_kernel<2>, a, nmost)) != cudaSuccess ||
+        (r = cudaFuncSetAttribute(tree_apply_narrow_kernel<4>, a, nmost)) != cudaSuccess)
+      return r;
+    return cudaFuncSetAttribute(tree_apply_narrow_kernel<8>, a, nmost);
+  });
+  if (e != cudaSuccess) return e;
+  int sms = 0;
+  if ((e = device_sm_count(&sms)) != cudaSuccess) return e;
   ApplyArgs a = {};
   a.P = P;
   a.lda = lda;
@@ -1041,7 +1039,7 @@ cudaError_t tree_apply_qt(int mk, int bk, int b, const double *P, int lda, int l
     ProfScope ps(narrow ? kClsTreeNarrow : kClsTreeApply, st, f);
     launch(plan.nleaves);
   }
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int buf = 0;
   for (int r = 0; r < plan.nrounds; ++r) {

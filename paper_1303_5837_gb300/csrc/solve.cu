@@ -9,6 +9,7 @@
 #include <mutex>
 
 #include "ca_internal.cuh"
+#include "device_once.cuh"
 
 namespace cagb {
 
@@ -49,13 +50,11 @@ __global__ void __launch_bounds__(32) swap_rows_kernel(int n, const int *ipiv, d
 
 cudaError_t getrs_swap(int n, int nrhs, const int *ipiv, double *B, int ldb, cudaStream_t st) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
-  static bool init = false;
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(swap_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
-    if (e != cudaSuccess) return e;
-    init = true;
-  }
+  static std::atomic<unsigned long long> init{0};
+  cudaError_t e = once_per_device(init, [] {
+    return cudaFuncSetAttribute(swap_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  if (e != cudaSuccess) return e;
   int staged = ((size_t)n * 8 <= 200 * 1024) ? 1 : 0;
   ProfScope ps(kClsSolve, st, 0.0);
   swap_rows_kernel<<<nrhs, 32, staged ? (size_t)n * 8 : 0, st>>>(n, ipiv, B, ldb, staged);
@@ -291,33 +290,27 @@ static int *solve_flags_for(cudaStream_t st) {
 
 // one CTA per SM, one diagonal block per CTA
 static int coop_max_n() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 1;
-  }
+  int sms = 1;
+  if (device_sm_count(&sms) != cudaSuccess) sms = 1;
   return (sms < kMaxFlagBlocks ? sms : kMaxFlagBlocks) * kTb;
 }
 
 // 0: launched; 1: not available here (use the per-block path); <0 error
 static int trsm_left_flags(bool lower, bool unit, int n, int nrhs, const double *T, int ldt, double *B, int ldb,
                            cudaStream_t st, cudaError_t *err) {
-  static bool init = false;
+  static std::atomic<unsigned long long> init{0};
   const size_t smem = ((size_t)kTb * kLdI + kTb + 4 * (size_t)kTb * kCoopMaxRhs) * 8;
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(trsv_flag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) {
-      *err = e;
-      return -1;
-    }
-    init = true;
+  cudaError_t e = once_per_device(init, [smem] {
+    return cudaFuncSetAttribute(trsv_flag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) {
+    *err = e;
+    return -1;
   }
   int *flags = solve_flags_for(st);
   if (!flags) return 1;
   const int nblk = (n + kTb - 1) / kTb;
-  cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)nblk * sizeof(int), st);
+  e = cudaMemsetAsync(flags, 0, (size_t)nblk * sizeof(int), st);
   if (e != cudaSuccess) {
     *err = e;
     return -1;
@@ -343,13 +336,11 @@ cudaError_t trsm_left(bool lower, bool unit, int n, int nrhs, const double *T, i
     if (rc < 0) return err;
   }
   const size_t smem = ((size_t)kTb * (kTb + 1) + (size_t)kTb * 33) * 8;
-  static bool init = false;
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(trsm_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    init = true;
-  }
+  static std::atomic<unsigned long long> init{0};
+  cudaError_t e = once_per_device(init, [smem] {
+    return cudaFuncSetAttribute(trsm_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
   const int nblk = (n + kTb - 1) / kTb;
   const dim3 g((nrhs + 31) / 32);
   for (int s = 0; s < nblk; ++s) {

@@ -1,0 +1,48 @@
+"""Host logic of bench.py that needs no GPU: the reduction-tree option and the
+lookup of committed DRAM counters (profiles/traffic.txt), which must only be
+used for the kernel code and the plan of launches they were taken on."""
+import hashlib
+
+import pytest
+
+import bench
+
+
+def test_parse_tree():
+    assert bench.parse_tree("4f,0f") == [(4, 1), (0, 1)]
+    assert bench.parse_tree("4b,0b") == [(4, 0), (0, 0)]
+    assert bench.parse_tree(bench.BENCH_TREE)[-1][0] == 0
+    for bad in ("4x,0b", "4b", "b,0b", ""):
+        with pytest.raises(ValueError):
+            bench.parse_tree(bad)
+    assert "flat" in bench.describe_tree([(4, 1), (0, 1)])
+
+
+def test_source_region(tmp_path):
+    f = tmp_path / "k.cu"
+    f.write_text("a\n// @region K\nbody 1\nbody 2\n// @endregion K\ntail\n")
+    assert bench.source_text(str(tmp_path), "k.cu#K") == b"body 1\nbody 2\n"
+    assert bench.source_text(str(tmp_path), "k.cu") == f.read_bytes()
+    assert bench.source_text(str(tmp_path), "k.cu#missing") == b""
+
+
+def test_traffic_key_matches_current_kernel_and_plan():
+    plan = f"16384/128/{bench.BENCH_LEAF_ROWS}/{bench.BENCH_TREE}/320"
+    v = bench.traffic_for("tree_apply", plan)
+    assert v is not None and v > 0
+    # another plan of launches (or another kernel) gets no figure
+    assert bench.traffic_for("tree_apply", "16384/128/1024/4b,0b/496") is None
+    assert bench.traffic_for("gemm_fp64", plan) is None
+
+
+def test_traffic_key_detects_a_changed_kernel(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_1303_5837_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "k.cu").write_text("// @region K\nint x;\n// @endregion K\n")
+    h = hashlib.sha256(b"int x;\n").hexdigest()[:16]
+    (tmp_path / "profiles" / "traffic.txt").write_text(f"kern k.cu#K {h} 1e6 plan=P note\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_for("kern", "P") == 1e6
+    (csrc / "k.cu").write_text("// @region K\nint y;\n// @endregion K\n")
+    assert bench.traffic_for("kern", "P") is None
