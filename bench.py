@@ -70,7 +70,10 @@ def parse():
     p.add_argument("--cond", type=float, default=1e6)
     p.add_argument("--nrhs", type=int, default=1)
     p.add_argument("--e2e-steps", type=int, default=1)
-    p.add_argument("--cpu-n", type=int, default=1024, help="oracle sample size")
+    p.add_argument("--cpu-n", type=int, default=2048,
+                   help="order of the oracle sample timed for cpu_baseline (about 10 s on one core)")
+    p.add_argument("--ref-n", type=int, default=1024,
+                   help="order of the oracle sample of each step of --impl reference (about 1 s)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--mixed-slices", type=int, default=4)
     p.add_argument("--mixed-exact", type=int, default=1)
@@ -226,7 +229,7 @@ def run_reference(a, rank: int, world: int):
         return
     times = []
     for i in range(a.warmup + a.steps):
-        secs, fl = oracle_sample(a, a.cpu_n)
+        secs, fl = oracle_sample(a, a.ref_n)
         if i >= a.warmup:
             times.append(secs)
     t = sum(times)
@@ -236,9 +239,9 @@ def run_reference(a, rank: int, world: int):
         "warmup": a.warmup, "ms_per_step": 1e3 * t / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": workload_config(a, {"sample_n": a.cpu_n}),
+        "config": workload_config(a, {"sample_n": a.ref_n}),
         "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                         "sample": f"each step: oracle on one {a.cpu_n}x{a.cpu_n} matrix"},
+                         "sample": f"each step: oracle on one {a.ref_n}x{a.ref_n} matrix"},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
