@@ -34,6 +34,13 @@ MUTANTS = {
     "merge_r_lower_kept": ("AT(S, rows, at + i, q) = (q >= i) ? AT(P, ldp, top[ch] + i, q) : 0.0;",
                            "AT(S, rows, at + i, q) = AT(P, ldp, top[ch] + i, q);"),
     "getrs_no_swap": ("int p = ipiv[i] - 1;", "int p = i;"),
+    "getrs_forward_reads_own_row": ("for (int l = 0; l < i; ++l) s = s - AT(LU, lda, i, l) * x[l];",
+                                    "for (int l = 0; l <= i; ++l) s = s - AT(LU, lda, i, l) * x[l];"),
+    "geqrs_r_transposed": ("for (int l = i + 1; l < n; ++l) s = s - AT(QR, lda, i, l) * AT(B, ldb, l, c);",
+                           "for (int l = i + 1; l < n; ++l) s = s - AT(QR, lda, l, i) * AT(B, ldb, l, c);"),
+    "op_inner_tree_flat": ("in.style[0] = ORA_BINARY;", "in.style[0] = ORA_FLAT;"),
+    "op_inner_width_wrong_level": ("in.op_b[0] = t->op_b[1];", "in.op_b[0] = t->op_b[0];"),
+    "op_pivots_not_applied": ("perm[i] = perm[sw];\n    perm[sw] = ti;", "(void)ti;\n    (void)sw;"),
 }
 
 
