@@ -217,6 +217,17 @@ int caqr_geqrs(int m, int n, int nrhs, const double *QR, int lda, int b, const c
                const double *qtree, size_t qtree_bytes, double *B, int ldb, void *work,
                size_t lwork, cudaStream_t stream);
 
+/* ca_solve_status: the triangular solves of calu_getrs, caqr_geqrs and
+ * calu_gesv_mixed order their diagonal blocks by ready flags in device
+ * memory (one flag array per device and stream); each wait for a flag is
+ * bounded (about 2 s of SM clock) and a wait that gives up is recorded.
+ * This call synchronizes `stream`, sets *timed_out to 1 if a solve on it
+ * gave up since the previous call (its right-hand sides are then only partly
+ * solved) and to 0 otherwise, and clears the record.  No counterpart in the
+ * paper.  Returns CA_OK, -2 for a NULL timed_out, CA_ERR_LAUNCH on a CUDA
+ * error. */
+int ca_solve_status(cudaStream_t stream, int *timed_out);
+
 /* ------------------------------------------------------------------------ */
 /* Reduced-precision trailing update on the tensor cores                    */
 /* ------------------------------------------------------------------------ */

@@ -14,7 +14,7 @@ _BINDING_NAMES = {
     "ca_gemm_mixed_workspace", "ca_gemm_minus_mixed", "tslu_noalloc", "ca_calu_mixed_workspace",
     "calu_factor_mixed", "ca_gesv_mixed_workspace", "calu_gesv_mixed", "ca_caqr_mixed_workspace",
     "caqr_factor_mixed", "ca_batched_plan", "ca_batched_factor", "BatchedFactor", "ca_batch_item_t",
-    "CA_BATCH_CALU", "CA_BATCH_CAQR", "CA_DTYPE_F64", "CA_DTYPE_F32",
+    "CA_BATCH_CALU", "CA_BATCH_CAQR", "CA_DTYPE_F64", "CA_DTYPE_F32", "ca_solve_status",
 }
 
 

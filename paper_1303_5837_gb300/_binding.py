@@ -96,7 +96,7 @@ SYMBOLS = ("ca_strerror", "ca_calu_workspace", "ca_caqr_workspace", "ca_geqrs_wo
            "ca_prof_enable", "ca_prof_read", "ca_launch_count", "ca_kernel_class_name",
            "ca_gemm_mixed_workspace", "ca_gemm_minus_mixed", "ca_calu_mixed_workspace",
            "calu_factor_mixed", "ca_gesv_mixed_workspace", "calu_gesv_mixed", "ca_caqr_mixed_workspace",
-           "caqr_factor_mixed", "ca_batched_plan", "ca_batched_factor")
+           "caqr_factor_mixed", "ca_batched_plan", "ca_batched_factor", "ca_solve_status")
 KERNEL_CLASSES = ("tslu_node", "laswp", "lu_finish", "trsm_u12", "gemm_fp64", "tsqr_node",
                   "tree_apply", "solve", "split_bf16", "gemm_tc", "refine", "batched",
                   "tree_narrow")
@@ -142,6 +142,7 @@ def load(build_if_missing: bool = True):
     L.caqr_factor_mixed.argtypes = [I, I, P, I, I, T, I, I, P, S, P, S, P, P]
     L.ca_batched_plan.argtypes = [I, ctypes.POINTER(ca_batch_item_t), I, P, PS, PS]
     L.ca_batched_factor.argtypes = [P, P, P, S, P]
+    L.ca_solve_status.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
     L.ca_prof_enable.argtypes = [I, I]
     L.ca_prof_read.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)]
@@ -301,6 +302,15 @@ def caqr_geqrs(QR: torch.Tensor, b: int, tree: ca_tree_t, qtree: torch.Tensor, B
                            work.numel() * work.element_size(), _stream(stream))
     _check("caqr_geqrs", rc)
     return B
+
+
+def ca_solve_status(stream=None) -> bool:
+    """Synchronizes the stream; True if a triangular solve on it gave up
+    waiting for a block's ready flag since the previous call (its
+    right-hand sides are then only partly solved).  Clears the record."""
+    t = ctypes.c_int(0)
+    _check("ca_solve_status", load().ca_solve_status(_stream(stream), ctypes.byref(t)))
+    return bool(t.value)
 
 
 # ---------------------------------------------------------------------------

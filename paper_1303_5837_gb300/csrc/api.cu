@@ -10,6 +10,9 @@
 
 namespace cagb {
 
+// solve.cu: whether a dependency-ordered solve on `st` gave up waiting
+cudaError_t solve_timeout_read(cudaStream_t st, int *timed_out);
+
 // NVTX range around a host-side step (a panel of CALU / CAQR): visible in a
 // timeline profiler, a null operation when none is attached.
 struct NvtxRange {
@@ -427,6 +430,11 @@ int caqr_geqrs(int m, int n, int nrhs, const double *QR, int lda, int b, const c
   }
   if (trsm_left(false, false, n, nrhs, QR, lda, B, ldb, stream) != cudaSuccess) return CA_ERR_LAUNCH;
   return CA_OK;
+}
+
+int ca_solve_status(cudaStream_t stream, int *timed_out) {
+  if (!timed_out) return -2;
+  return cagb::solve_timeout_read(stream, timed_out) == cudaSuccess ? CA_OK : CA_ERR_LAUNCH;
 }
 
 int ca_gemm_mixed_workspace(int m, int n, int k, int slices, int exact, size_t *work_bytes) {

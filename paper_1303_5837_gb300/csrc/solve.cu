@@ -266,26 +266,55 @@ __global__ void __launch_bounds__(256, 1) trsv_flag_kernel(int n, int nrhs, cons
 // Flag words of the dependency-driven solve: one array per (device, caller
 // stream), created on first use (make the first solve on a stream before
 // capturing it in a graph) and kept until the process exits.
-static int *solve_flags_for(cudaStream_t st) {
+struct FlagPool {
   struct Entry {
     int dev;
     cudaStream_t st;
     int *flags;
   };
-  static std::mutex mu;
-  static Entry pool[64];
-  static int used = 0;
+  std::mutex mu;
+  Entry pool[64];
+  int used = 0;
+};
+
+static FlagPool &flag_pool() {
+  static FlagPool p;
+  return p;
+}
+
+// The flag array of (current device, st), or nullptr if none exists and
+// `create` is false (or it cannot be created).
+static int *solve_flags_lookup(cudaStream_t st, bool create) {
+  FlagPool &fp = flag_pool();
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-  std::lock_guard<std::mutex> g(mu);
-  for (int i = 0; i < used; ++i)
-    if (pool[i].dev == dev && pool[i].st == st) return pool[i].flags;
-  if (used == 64) return nullptr;
+  std::lock_guard<std::mutex> g(fp.mu);
+  for (int i = 0; i < fp.used; ++i)
+    if (fp.pool[i].dev == dev && fp.pool[i].st == st) return fp.pool[i].flags;
+  if (!create || fp.used == 64) return nullptr;
   int *f = nullptr;
   if (cudaMalloc(&f, (kMaxFlagBlocks + 1) * sizeof(int)) != cudaSuccess) return nullptr;
   if (cudaMemset(f, 0, (kMaxFlagBlocks + 1) * sizeof(int)) != cudaSuccess) return nullptr;
-  pool[used] = {dev, st, f};
-  return pool[used++].flags;
+  fp.pool[fp.used] = {dev, st, f};
+  return fp.pool[fp.used++].flags;
+}
+
+static int *solve_flags_for(cudaStream_t st) { return solve_flags_lookup(st, true); }
+
+// Whether a flag wait of a solve on `st` gave up since the last call: waits
+// for the stream, reads the timeout word and clears it.
+cudaError_t solve_timeout_read(cudaStream_t st, int *timed_out) {
+  *timed_out = 0;
+  int *flags = solve_flags_lookup(st, false);
+  if (!flags) return cudaSuccess;  // no dependency-ordered solve ran on st
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  int word = 0;
+  if ((e = cudaMemcpy(&word, flags + kMaxFlagBlocks, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return e;
+  if (word != 0 && (e = cudaMemset(flags + kMaxFlagBlocks, 0, sizeof(int))) != cudaSuccess) return e;
+  *timed_out = word != 0;
+  return cudaSuccess;
 }
 
 // one CTA per SM, one diagonal block per CTA

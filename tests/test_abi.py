@@ -64,6 +64,11 @@ def test_argument_errors_without_gpu(lib):
     assert lib.ca_strerror(-1001).decode().startswith("workspace")
     wide = B.make_tree(512)
     assert lib.ca_calu_workspace(4096, 4096, 256, ctypes.byref(wide), ctypes.byref(size)) == -1002
+    # solve status: a NULL result pointer is an argument error; with no solve
+    # run on the stream (here: no device at all) nothing timed out
+    assert lib.ca_solve_status(None, None) == -2
+    flag = ctypes.c_int(7)
+    assert lib.ca_solve_status(None, ctypes.byref(flag)) == 0 and flag.value == 0
 
 
 def test_workspace_matches_tree_counts(lib):
