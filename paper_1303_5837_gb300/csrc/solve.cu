@@ -312,7 +312,10 @@ cudaError_t solve_timeout_read(cudaStream_t st, int *timed_out) {
   int word = 0;
   if ((e = cudaMemcpy(&word, flags + kMaxFlagBlocks, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return e;
-  if (word != 0 && (e = cudaMemset(flags + kMaxFlagBlocks, 0, sizeof(int))) != cudaSuccess) return e;
+  if (word != 0) {  // cleared in the stream's order, before its later solves
+    if ((e = cudaMemsetAsync(flags + kMaxFlagBlocks, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  }
   *timed_out = word != 0;
   return cudaSuccess;
 }
