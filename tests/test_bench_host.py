@@ -46,3 +46,15 @@ def test_traffic_key_detects_a_changed_kernel(tmp_path, monkeypatch):
     assert bench.traffic_for("kern", "P") == 1e6
     (csrc / "k.cu").write_text("// @region K\nint y;\n// @endregion K\n")
     assert bench.traffic_for("kern", "P") is None
+
+
+def test_clock_rejection_rule():
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 100}
+    assert not bench.clocks_rejected(ok)
+    assert not bench.clocks_rejected(dict(ok, reasons=["sw_power_cap"]))            # kept, noted
+    assert not bench.clocks_rejected(dict(ok, sm_mhz=1500.0, reasons=["sw_power_cap"]))
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clocks_rejected(dict(ok, reasons=[r]))
+    assert bench.clocks_rejected(dict(ok, sm_mhz=1200.0))                            # stuck low, no reason
+    assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None,
+                                      "reasons": ["nvidia-smi unavailable"]})
