@@ -87,6 +87,9 @@ def parse():
     p.add_argument("--batch-steps", type=int, default=3)
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-configs", action="store_true")
+    p.add_argument("--derive-traffic", default="",
+                   help="LEAF_RATE,MERGE_RATE: DRAM bytes per C element of a wide leaf / merge launch "
+                        "(ncu); prints the per-launch traffic line for this workload and exits (no GPU)")
     p.add_argument("--only-serve", action="store_true", help="diagnostic: run only the serving workload")
     p.add_argument("--only-configs", action="store_true", help="diagnostic: run only the other configurations")
     p.add_argument("--only-batch", default="", choices=["", "f64", "f32", "ops"],
@@ -266,6 +269,118 @@ def run_reference(a, rank: int, world: int):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+def tree_rounds(nleaves: int, levels):
+    """Merge rounds of the reduction tree over `nleaves` leaves, as the
+    library plans them (one launch per round): per round, the number of
+    inputs of each output node, in order.  Per level, groups of fan_in
+    consecutive nodes (the last level takes all); binary style pairs
+    neighbours until one node is left per group (an odd one passes through),
+    flat style merges a group at once.  Rounds without a merge are dropped."""
+    rounds = []
+    cur = nleaves
+    for li, (fan, style) in enumerate(levels):
+        f = cur if li == len(levels) - 1 else fan
+        ngroups = -(-cur // f)
+        sizes = [f] * (ngroups - 1) + [cur - (ngroups - 1) * f] if ngroups > 1 else [cur]
+        if style == 1:
+            if any(g >= 2 for g in sizes):
+                rounds.append(list(sizes))
+        else:
+            while any(g > 1 for g in sizes):
+                rnd, nxt = [], []
+                for g in sizes:
+                    outs = [2] * (g // 2) + ([1] if g % 2 else [])
+                    rnd += outs
+                    nxt.append(len(outs))
+                rounds.append(rnd)
+                sizes = nxt
+        cur = ngroups
+    return rounds
+
+
+def tree_update_launches(n: int, b: int, leaf: int, levels, nrhs: int, sms: int = 152):
+    """The tree-update launches of one benchmark step (caqr_factor with the
+    look-ahead, then caqr_geqrs), in order: (kernel, is_leaf, C elements).
+    The library runs an update on the narrow kernel when it has at most 8
+    columns or its leaf launch would have fewer 32-column CTAs than SMs.
+    C elements: a leaf launch touches every panel row of its columns, a
+    merge launch the stacked R rows of the nodes that merge."""
+    out = []
+
+    def apply(mk, bk, nl, rounds, ncols):
+        if ncols <= 0:
+            return
+        narrow = ncols <= 8 or nl * (-(-ncols // 32)) < sms
+        kind = "tree_narrow" if narrow else "tree_apply"
+        out.append((kind, True, mk * ncols))
+        rows = [min(leaf, mk - j * leaf, bk) for j in range(nl)]   # R rows per node
+        for rnd in rounds:
+            nxt, at, el = [], 0, 0
+            for cnt in rnd:
+                kids = rows[at:at + cnt]
+                at += cnt
+                if cnt >= 2:
+                    el += sum(kids)
+                nxt.append(min(sum(kids), bk) if cnt >= 2 else kids[0])
+            rows = nxt
+            out.append((kind, False, el * ncols))
+
+    panels = [(kb, min(b, n - kb)) for kb in range(0, n, b)]
+    for kb, bk in panels:
+        mk = n - kb
+        nl = -(-mk // leaf)
+        rounds = tree_rounds(nl, levels)
+        nt = n - kb - bk
+        if nt > 0:
+            nnext = min(nt, b)
+            if n > b and nnext < nt:
+                apply(mk, bk, nl, rounds, nnext)
+                apply(mk, bk, nl, rounds, nt - nnext)
+            else:
+                apply(mk, bk, nl, rounds, nt)
+    for kb, bk in panels:
+        mk = n - kb
+        nl = -(-mk // leaf)
+        apply(mk, bk, nl, tree_rounds(nl, levels), nrhs)
+    return out
+
+
+def derive_traffic(leaf_rate: float, merge_rate: float, n: int, b: int, leaf: int, levels,
+                   nrhs: int = 1, sms: int = 152):
+    """Per-launch DRAM bytes of the wide tree update over one step: DRAM
+    bytes per C element of a leaf launch and per stacked C element of a merge
+    launch (from an ncu capture of a smaller case) times the elements each
+    wide launch processes, averaged over the wide launches."""
+    ls = tree_update_launches(n, b, leaf, levels, nrhs, sms)
+    wide = [(is_leaf, el) for kind, is_leaf, el in ls if kind == "tree_apply"]
+    narrow = sum(1 for kind, _, _ in ls if kind == "tree_narrow")
+    total = sum((leaf_rate if is_leaf else merge_rate) * el for is_leaf, el in wide)
+    return {"wide_launches": len(wide), "narrow_launches": narrow,
+            "bytes_per_wide_launch": total / max(1, len(wide))}
+
+
+TRAFFIC_SOURCES = {"tree_apply": "panel_qr.cu#tree_apply_kernel,ca_internal.cuh"}
+
+
+def print_traffic_line(a):
+    """The profiles/traffic.txt line of the wide tree update for this
+    workload, from the per-element DRAM rates of an ncu capture."""
+    leaf_rate, merge_rate = (float(x) for x in a.derive_traffic.split(","))
+    d = derive_traffic(leaf_rate, merge_rate, a.n, a.b, a.leaf, parse_tree(a.tree), a.nrhs)
+    csrc = os.path.join(ROOT, "paper_1303_5837_gb300", "csrc")
+    h = hashlib.sha256()
+    for item in TRAFFIC_SOURCES["tree_apply"].split(","):
+        h.update(source_text(csrc, item))
+    print(f"tree_apply {TRAFFIC_SOURCES['tree_apply']} {h.hexdigest()[:16]} "
+          f"{d['bytes_per_wide_launch']:.4e} plan={a.n}/{a.b}/{a.leaf}/{a.tree}/{d['wide_launches']} "
+          f"per-launch average of the {d['wide_launches']} wide launches of one step "
+          f"(CALU+getrs and CAQR+geqrs, n={a.n}, b={a.b}, {a.leaf}-row leaves, tree {a.tree}, "
+          f"{a.nrhs} RHS; {d['narrow_launches']} narrow launches), derived by "
+          f"python bench.py --derive-traffic {a.derive_traffic}: {leaf_rate} DRAM bytes per C element "
+          f"of a leaf launch, {merge_rate} per stacked C element of a merge launch "
+          f"(ncu capture at n=6144 in tree_apply_n6144_full.md)")
+
+
 def source_text(csrc: str, item: str) -> bytes:
     """Bytes of one source item of profiles/traffic.txt: a whole file
     ("panel_qr.cu") or the lines between "// @region NAME" and
@@ -890,6 +1005,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.derive_traffic:
+        print_traffic_line(a)
+        return
     if a.impl == "reference":
         run_reference(a, rank, world)
         return

@@ -58,3 +58,47 @@ def test_clock_rejection_rule():
     assert bench.clocks_rejected(dict(ok, sm_mhz=1200.0))                            # stuck low, no reason
     assert not bench.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None,
                                       "reasons": ["nvidia-smi unavailable"]})
+
+
+@pytest.mark.parametrize("levels", ["0b", "0f", "4b,0b", "4f,0f", "2b,4b,0b", "3f,0b", "8f,0f", "2f,3b,0f"])
+def test_tree_rounds_match_the_oracle_counts(levels):
+    """The benchmark's replica of the library's merge rounds merges as many
+    nodes as the oracle's (independent) tree plan, for ragged leaf counts."""
+    import oracle
+    lv = bench.parse_tree(levels)
+    for nl in list(range(1, 40)) + [64, 97, 128, 513]:
+        merges = sum(1 for rnd in bench.tree_rounds(nl, lv) for c in rnd if c >= 2)
+        _, nm = oracle.tree_counts(nl * 64, oracle.make_tree(64, lv))
+        assert merges == nm, (levels, nl)
+        # every round's inputs are the previous round's outputs
+        n_in = nl
+        for rnd in bench.tree_rounds(nl, lv):
+            assert sum(rnd) == n_in
+            n_in = len(rnd)
+        assert n_in == 1
+
+
+def test_tree_update_plan_matches_the_measured_launch_counts():
+    """Launch counts per step of the benchmark (n = 16384, b = 128, 1024-row
+    leaves, one right-hand side) as the library's own counters reported them
+    on the GPU: 320 wide / 709 narrow with flat merges of 4, 496 / 1061 with
+    binary merges in groups of 4."""
+    for tree, wide, narrow in (("4f,0f", 320, 709), ("4b,0b", 496, 1061)):
+        d = bench.derive_traffic(14.54, 8.22, 16384, 128, 1024, bench.parse_tree(tree))
+        assert (d["wide_launches"], d["narrow_launches"]) == (wide, narrow)
+    d = bench.derive_traffic(1.0, 0.0, 6144, 128, 1024, bench.parse_tree("4f,0f"))
+    ls = bench.tree_update_launches(6144, 128, 1024, bench.parse_tree("4f,0f"), 1)
+    # panel 0 at n = 6144: the look-ahead update (narrow: 6 leaves x 4 tiles < 152
+    # SMs), then the wide leaf launch of the other 5888 columns and two merge rounds
+    assert [k for k, _, _ in ls[:6]] == ["tree_narrow"] * 3 + ["tree_apply"] * 3
+    assert ls[3] == ("tree_apply", True, 6144 * 5888)
+    assert ls[4] == ("tree_apply", False, 6 * 128 * 5888) and ls[5] == ("tree_apply", False, 2 * 128 * 5888)
+
+
+def test_committed_traffic_line_is_the_derived_one():
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, "bench.py", "--derive-traffic", "14.54,8.22"],
+                         cwd=bench.ROOT, capture_output=True, text=True, check=True).stdout
+    committed = open(f"{bench.ROOT}/profiles/traffic.txt").read()
+    assert out == committed
