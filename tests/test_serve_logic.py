@@ -6,7 +6,6 @@ import threading
 import time
 
 import numpy as np
-import pytest
 
 from paper_1303_5837_gb300 import serve
 
