@@ -7,7 +7,8 @@ the library's workspace, sized by the C-ABI workspace queries) fits in the
 remaining budget; a request larger than the whole budget is rejected.  Each
 slot is a worker thread with its own CUDA stream, so admitted requests run
 concurrently on the device while later ones wait.  Factors stay on the device
-for the life of a request; the result comes back to the host.
+for the life of a request; the result comes back to the host.  A request can
+be cancelled until it is admitted; one that runs is never interrupted.
 
 Every computation goes through the C-ABI (``_binding``); this module only
 schedules, allocates (torch caching allocator) and moves data.
@@ -34,7 +35,7 @@ class Request:
     B: np.ndarray               # host, m x nrhs
     arrival: float = 0.0
     footprint: int = 0
-    status: str = "pending"     # pending, running, done, rejected, failed
+    status: str = "pending"     # pending, running, done, rejected, failed, cancelled
     X: np.ndarray | None = None
     t_done: float = 0.0
     error: str = ""
@@ -85,6 +86,7 @@ class SolveServer:
         self._finished = 0
         self.completed: list[Request] = []
         self.rejected: list[Request] = []
+        self.cancelled: list[Request] = []
         self._stop = False
         self._sched = threading.Thread(target=self._schedule, daemon=True)
         self._workers = [threading.Thread(target=self._worker, args=(i,), daemon=True) for i in range(slots)]
@@ -112,6 +114,20 @@ class SolveServer:
         self._pending.put(r)
         return r
 
+    def cancel(self, r: Request) -> bool:
+        """Withdraws a request that has not started: True if it was still
+        pending (it finishes as "cancelled" and nothing of it reaches the GPU),
+        False if it already runs or has finished.  A running request is never
+        interrupted: its kernels complete and its result is kept."""
+        with self._cv:
+            if r.status != "pending":
+                return False
+            r.status = "cancelled"
+            r.t_done = time.perf_counter()
+            self.cancelled.append(r)
+            self._finish(r)
+            return True
+
     def _finish(self, r: Request):
         with self._cv:
             self._finished += 1
@@ -119,7 +135,8 @@ class SolveServer:
         r.done.set()
 
     def drain(self, timeout: float = 600.0):
-        """Wait until every submitted request is done, failed or rejected."""
+        """Wait until every submitted request is done, failed, rejected or
+        cancelled."""
         deadline = time.perf_counter() + timeout
         with self._cv:
             while self._finished < self._submitted:
@@ -140,10 +157,11 @@ class SolveServer:
     def stats(self) -> dict:
         lat = sorted(r.latency for r in self.completed)
         if not lat:
-            return {"completed": 0, "rejected": len(self.rejected)}
+            return {"completed": 0, "rejected": len(self.rejected), "cancelled": len(self.cancelled)}
         pct = lambda p: lat[min(len(lat) - 1, int(math.ceil(p * len(lat))) - 1)]
         span = max(r.t_done for r in self.completed) - min(r.arrival for r in self.completed)
-        return {"completed": len(lat), "rejected": len(self.rejected), "p50_s": pct(0.50),
+        return {"completed": len(lat), "rejected": len(self.rejected),
+                "cancelled": len(self.cancelled), "p50_s": pct(0.50),
                 "p99_s": pct(0.99), "solves_per_s": len(lat) / span if span > 0 else float("inf"),
                 "max_hbm_in_use": self.max_used, "budget": self.budget}
 
@@ -153,18 +171,23 @@ class SolveServer:
             r = self._pending.get()
             if r is None:
                 return
-            if r.footprint > self.budget:
-                r.status = "rejected"
-                r.t_done = time.perf_counter()
-                self.rejected.append(r)
-                self._finish(r)
-                continue
             with self._cv:
+                if r.status == "cancelled":  # finished by cancel()
+                    continue
+                if r.footprint > self.budget:
+                    r.status = "rejected"
+                    r.t_done = time.perf_counter()
+                    self.rejected.append(r)
+                    self._finish(r)
+                    continue
                 # arrival order: the head request waits for a slot and memory
-                while not self._stop and (not self._free_slots or self._used + r.footprint > self.budget):
+                while not self._stop and r.status != "cancelled" and (
+                        not self._free_slots or self._used + r.footprint > self.budget):
                     self._cv.wait(timeout=0.05)
                 if self._stop:
                     return
+                if r.status == "cancelled":
+                    continue
                 slot = self._free_slots.pop(0)
                 self._used += r.footprint
                 self.max_used = max(self.max_used, self._used)

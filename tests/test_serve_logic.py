@@ -69,3 +69,36 @@ def test_failed_request_does_not_stop_the_server():
         srv.close()
     assert bad.status == "failed" and "planted" in bad.error
     assert good.status == "done"
+
+
+def test_cancel_a_pending_request():
+    """A request still waiting for a slot can be cancelled: it finishes as
+    "cancelled" and never reaches the executor; a running one cannot be
+    cancelled and completes; later requests are served in order."""
+    seen = []
+    started = threading.Event()
+
+    def slow(r, ctx):
+        seen.append(r)
+        started.set()
+        time.sleep(0.3)
+        return np.zeros((1, 1))
+
+    srv = serve.SolveServer(hbm_budget=1 << 40, slots=1, execute=slow)
+    try:
+        first = srv.submit("lu", np.eye(64), np.ones(64))
+        assert started.wait(10)
+        second = srv.submit("lu", np.eye(64), np.ones(64))
+        third = srv.submit("lu", np.eye(64), np.ones(64))
+        assert not srv.cancel(first)           # running: not interrupted
+        assert srv.cancel(second)              # still waiting for the slot
+        assert not srv.cancel(second)          # only once
+        assert second.done.is_set() and second.status == "cancelled"
+        srv.drain(timeout=30)
+        assert not srv.cancel(third)           # finished
+    finally:
+        srv.close()
+    assert first.status == "done" and third.status == "done"
+    assert second not in seen and seen == [first, third]
+    st = srv.stats()
+    assert st["completed"] == 2 and st["cancelled"] == 1 and st["rejected"] == 0
