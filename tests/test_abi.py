@@ -115,3 +115,30 @@ def test_batched_plan_checks_without_gpu(lib):
     assert wb.value > 256
     bogus = ctypes.create_string_buffer(256)
     assert lib.ca_batched_factor(bogus, None, None, 0, None) == -1
+
+
+def test_corrupted_tree_is_rejected_on_the_host(lib):
+    """Fault injection on the host: a corrupted tree description (no levels,
+    too many levels, an unknown merge style, a zero fan-in below the top, a
+    NULL pointer, leaves narrower than the panel) is reported as a bad tree
+    argument by every query before anything is enqueued."""
+    from paper_1303_5837_gb300 import _binding as B
+    size, q = ctypes.c_size_t(), ctypes.c_size_t()
+
+    def corrupt():
+        out = []
+        t = B.make_tree(128); t.nlevels = 0; out.append(t)
+        t = B.make_tree(128); t.nlevels = 9; out.append(t)
+        t = B.make_tree(128); t.style[0] = 7; out.append(t)
+        out.append(B.make_tree(128, [(0, 0), (0, 0)]))
+        out.append(B.make_tree(32))   # leaf rows < b = 64
+        return out
+
+    for t in corrupt() + [None]:
+        ref = ctypes.byref(t) if t is not None else None
+        assert lib.ca_calu_workspace(4096, 256, 64, ref, ctypes.byref(size)) == -4
+        assert lib.ca_caqr_workspace(4096, 256, 64, ref, ctypes.byref(q), ctypes.byref(size)) == -4
+        assert lib.ca_geqrs_workspace(4096, 256, 1, 64, ref, ctypes.byref(size)) == -5
+    # a deep but well-formed tree is accepted (one leaf per row, 26 binary rounds)
+    deep = B.make_tree(1)
+    assert lib.ca_calu_workspace(1 << 26, 1, 1, ctypes.byref(deep), ctypes.byref(size)) == 0
