@@ -1,0 +1,75 @@
+"""Property-based pins of the oracle (CPU; needs hypothesis, skipped where it
+is not installed): on random small shapes and random reduction trees, the
+oracle's tournament pivots and CALU factors equal an exact rational brute
+force of the same algorithm (Sec. 3.2: GEPP on every leaf, GEPP on the
+stacked candidate rows of every merge, in the tree's order), and the
+tournament over a single leaf is GEPP."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1303_5837_gb300 import inputs
+from tests import bruteforce as bf
+
+hyp = pytest.importorskip("hypothesis")
+st = pytest.importorskip("hypothesis.strategies")
+given, settings, HealthCheck, event = hyp.given, hyp.settings, hyp.HealthCheck, hyp.event
+
+
+def tie_free(m, n, seed, chk, span):
+    for s in range(seed, seed + 200):
+        A = inputs.int_matrix(m, n, s, -span, span)
+        if not chk(A):
+            return A
+    return None
+
+
+@st.composite
+def tree_case(draw):
+    b = draw(st.integers(1, 5))
+    L = draw(st.integers(b, 10))
+    m = draw(st.integers(b, 45))
+    nlev = draw(st.integers(1, 3))
+    levels = [(draw(st.integers(2, 4)), draw(st.sampled_from([0, 1]))) for _ in range(nlev - 1)]
+    levels.append((0, draw(st.sampled_from([0, 1]))))
+    return m, b, L, levels, draw(st.integers(0, 10_000))
+
+
+@settings(max_examples=60, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+@given(tree_case())
+def test_tournament_equals_rational_brute_force(case):
+    m, b, L, levels, seed = case
+    A = tie_free(m, b, seed, lambda A: bf.tournament(bf.to_frac(A), b, L, levels)[1], span=999)
+    event("no tie-free matrix" if A is None else "compared")
+    if A is None:
+        return
+    want, _ = bf.tournament(bf.to_frac(A), b, L, levels)
+    got, _ = oracle.tslu_select(A, oracle.make_tree(L, levels))
+    assert list(got) == want
+
+
+@settings(max_examples=40, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+@given(tree_case(), st.integers(1, 12))
+def test_calu_equals_rational_brute_force(case, n):
+    m, b, L, levels, seed = case
+    A = tie_free(m, n, seed, lambda A: bf.calu(bf.to_frac(A), b, L, levels)[2], span=99)
+    event("no tie-free matrix" if A is None else "compared")
+    if A is None:
+        return
+    ipiv_x, W, _ = bf.calu(bf.to_frac(A), b, L, levels)
+    LU, ipiv, info, _ = oracle.calu(A, b, oracle.make_tree(L, levels))
+    assert list(ipiv) == ipiv_x and info == 0
+    exact = np.array([[float(v) for v in row] for row in W])
+    assert np.allclose(LU, exact, rtol=1e-12, atol=1e-12)
+
+
+@settings(max_examples=30, deadline=None)
+@given(st.integers(1, 40), st.integers(1, 8), st.integers(0, 10_000))
+def test_one_leaf_tournament_is_gepp(m, n, seed):
+    P = inputs.gaussian(m, n, seed)
+    sel, _ = oracle.tslu_select(P, oracle.make_tree(max(m, n)))
+    _, ipiv, _, _ = oracle.getf2(P)
+    order = np.arange(m)
+    for i, p in enumerate(ipiv):
+        order[[i, p - 1]] = order[[p - 1, i]]
+    assert np.array_equal(sel, order[:min(m, n)])
