@@ -118,3 +118,36 @@ def test_caqr_is_a_qr_factorization(case):
     x = oracle.geqrs(QR, T, b, tree, Bm)
     x_ls = np.linalg.lstsq(A, Bm, rcond=None)[0]
     assert _rel(x, x_ls) < 1e-9
+
+
+@st.composite
+def op_case(draw):
+    m, b, L, levels, seed = draw(tree_case())
+    b = max(b, 2)
+    L = max(L, b)
+    m = max(m, b)
+    depth = draw(st.integers(1, 2))
+    b1 = draw(st.integers(1, b))
+    op = [(b1, draw(st.integers(b1, 6)))]
+    if depth == 2:
+        b2 = draw(st.integers(1, b1))
+        op.append((b2, draw(st.integers(b2, max(b2, 4)))))
+    return m, b, L, levels, op, seed
+
+
+@settings(max_examples=40, deadline=None, derandomize=True, suppress_health_check=[HealthCheck.too_slow])
+@given(op_case(), st.integers(1, 10))
+def test_2d_operator_equals_rational_brute_force(case, n):
+    """Alg. 2D-ML-CALU: every tournament node factored by CALU of the level
+    below (depth 1 or 2, random inner widths and row blocks) gives the exact
+    rational brute force's pivots and factors."""
+    m, b, L, levels, op, seed = case
+    A = tie_free(m, n, seed, lambda A: bf.calu(bf.to_frac(A), b, L, levels, op)[2], span=99)
+    event("no tie-free matrix" if A is None else "compared")
+    if A is None:
+        return
+    ipiv_x, W, _ = bf.calu(bf.to_frac(A), b, L, levels, op)
+    LU, ipiv, info, _ = oracle.calu(A, b, oracle.make_tree(L, levels, op))
+    assert list(ipiv) == ipiv_x and info == 0
+    exact = np.array([[float(v) for v in row] for row in W])
+    assert np.allclose(LU, exact, rtol=1e-12, atol=1e-12)
