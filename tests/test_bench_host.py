@@ -136,3 +136,13 @@ def test_reference_arm_runs_on_rank_zero_only():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
                         "--ref-n", "64"], cwd=bench.ROOT, env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_all_cores_oracle_baseline():
+    """The oracle on every host core at once: spawned processes (safe after
+    CUDA use), started together, aggregate throughput over the common span."""
+    import argparse
+    a = argparse.Namespace(cond=1e6, nrhs=1, b=64, leaf=128, tree="0b", cpu_n=128)
+    d = bench.cpu_baseline_all_cores(a, cores=2)
+    assert d is not None and d["cores"] == 2 and d["kind"] == "oracle"
+    assert d["value"] > 0 and d["seconds"] > 0 and "2 concurrent copies" in d["sample"]
