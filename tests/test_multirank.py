@@ -1,6 +1,7 @@
 """The multi-rank plumbing of bench.py on CPU: two gloo ranks (127.0.0.1)
 agree on the barrier and take the maximum of their step times; the whole-job
-value aggregates every rank's units (weak scaling, independent replicas)."""
+value aggregates every rank's units (weak scaling, independent replicas); a
+slowdown seen by one rank makes every rank measure again."""
 import os
 import socket
 import sys
@@ -31,7 +32,10 @@ def _rank(rank, world, port, q):
     ms = bench.allreduce_max(100.0 + 50.0 * rank, world)
     flops = bench.step_flops(1024, 1)
     value = world * flops * 2 / (ms / 1e3) / 1e9  # 2 steps, as bench computes it
-    q.put((rank, ms, value))
+    # the re-measure decision is collective: rank 1 alone saw a slowdown
+    clocks = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown"] if rank == 1 else []}
+    again = bench.allreduce_max(1.0 if bench.clocks_rejected(clocks) else 0.0, world) > 0
+    q.put((rank, ms, value, again))
     dist.destroy_process_group()
 
 
@@ -46,7 +50,8 @@ def test_two_gloo_ranks_take_the_max_time():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    times = {r: ms for r, ms, _ in out}
+    times = {r: ms for r, ms, _, _ in out}
     assert times == {0: 150.0, 1: 150.0}
-    vals = {v for _, _, v in out}
+    vals = {v for _, _, v, _ in out}
     assert len(vals) == 1
+    assert all(again for _, _, _, again in out)   # both ranks measure again
