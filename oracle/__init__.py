@@ -176,19 +176,35 @@ def _arr(a, dtype) -> np.ndarray:
     return np.asfortranarray(np.array(a, dtype=dtype, copy=True))
 
 
-def calu(A, b: int, tree: dict, dtype=np.float64):
+def _padded(a, dtype, ld_pad: int):
+    """A column-major copy of ``a`` whose leading dimension is m + ld_pad
+    (marshalling only: the C code sees the same values through a larger lda;
+    a leading dimension that is a large power of two makes the row-wise loops
+    of the C code alias in the host cache).  Returns (buffer, view of the top
+    m rows, lda)."""
+    a = np.asarray(a)
+    m, n = a.shape
+    lda = max(1, m + int(ld_pad))
+    buf = np.zeros((lda, n), dtype=dtype, order="F")
+    buf[:m] = a
+    return buf, buf[:m], lda
+
+
+def calu(A, b: int, tree: dict, dtype=np.float64, ld_pad: int = 0):
     """CALU with tournament pivoting.  Returns (LU, ipiv 1-based, info, nearties).
-    dtype float32: the FP32 build (every operation and pivot decision in FP32)."""
+    dtype float32: the FP32 build (every operation and pivot decision in FP32).
+    ld_pad: rows of padding below the matrix in the buffer handed to the C
+    code (same result; see ``_padded``)."""
     lib = _load(dtype)
-    A = _arr(A, dtype)
+    buf, A, lda = _padded(A, dtype, ld_pad)
     m, n = A.shape
     ipiv = np.zeros(max(1, min(m, n)), dtype=np.int32)
     nt = ctypes.c_long(0)
     t = _ctree(tree)
-    info = lib.ora_calu(m, n, _ptr(A), max(1, m), b, ctypes.byref(t), _ptr(ipiv), ctypes.byref(nt))
+    info = lib.ora_calu(m, n, _ptr(buf), lda, b, ctypes.byref(t), _ptr(ipiv), ctypes.byref(nt))
     if info < 0:
         raise ValueError(f"ora_calu failed ({info})")
-    return A, ipiv[: min(m, n)], info, nt.value
+    return np.asfortranarray(A), ipiv[: min(m, n)], info, nt.value
 
 
 def getrs(LU, ipiv, B):
@@ -223,18 +239,18 @@ def caqr_tcount(m: int, n: int, b: int, tree: dict) -> int:
     return int(c)
 
 
-def caqr(A, b: int, tree: dict, dtype=np.float64):
+def caqr(A, b: int, tree: dict, dtype=np.float64, ld_pad: int = 0):
     """CAQR (TSQR panels + tree update).  Returns (QR factors, T storage).
-    dtype float32: the FP32 build."""
+    dtype float32: the FP32 build.  ld_pad: as for ``calu``."""
     lib = _load(dtype)
-    A = _arr(A, dtype)
+    buf, A, lda = _padded(A, dtype, ld_pad)
     m, n = A.shape
     T = np.zeros(max(1, caqr_tcount(m, n, b, tree)), dtype=dtype)
     t = _ctree(tree)
-    rc = lib.ora_caqr(m, n, _ptr(A), max(1, m), b, ctypes.byref(t), _ptr(T))
+    rc = lib.ora_caqr(m, n, _ptr(buf), lda, b, ctypes.byref(t), _ptr(T))
     if rc:
         raise ValueError(f"ora_caqr failed ({rc})")
-    return A, T
+    return np.asfortranarray(A), T
 
 
 def tsqr(A, tree: dict):

@@ -1,13 +1,19 @@
 """GPU parity at the full sizes of the workloads, in the configurations the
 benchmark times.
 
-Where the oracle finishes in seconds it runs in full (tall-skinny TSLU / TSQR
-panels of 1,048,576 x 64 and 8,388,608 x 32 with 256-row leaves: pivots must
-match exactly, factors, every stored Y and every T within 1e-12).  At
-n = 16384 (b = 128, the benchmark's leaves and tree) the oracle computes
-the first panel's tournament exactly and sampled outputs one by one: rows of
-P A - L U, column norms of R, backward errors of the solves, and the tensor-core
-forms against the FP64 form.
+Where the oracle finishes in seconds it runs in full, and every element is
+compared (``tests/parity.py``):
+  * tall-skinny TSLU / TSQR panels of 1,048,576 x 64 and 8,388,608 x 32 with
+    256-row leaves: pivots exactly; L, U, R, every stored Y and every T
+    element within 1e-12 of its rounding scale;
+  * CALU and CAQR of a 4096 x 4096 matrix in the benchmark's own shape
+    (b = 128, 1024-row leaves, one flat merge per group of 4 leaves then one
+    flat merge of the groups, 32 panels): pivots exactly over all panels,
+    every factor, Y and T element.
+At n = 16384 (the benchmark's size) the oracle computes the first panel's
+tournament exactly and sampled outputs one by one: rows of P A - L U, column
+norms of R, backward errors of the solves, and the tensor-core forms against
+the FP64 form.
 """
 import numpy as np
 import pytest
@@ -15,6 +21,7 @@ import pytest
 import bench
 import oracle
 from paper_1303_5837_gb300 import inputs
+from tests.parity import check, lu_err, qr_err, qtree_err
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -48,45 +55,61 @@ def rows_from_ipiv(ipiv, m):
 def test_tslu_full_size(ca, m, n):
     L = 256
     A = inputs.gaussian(m, n, 2026)
-    sel, nt = oracle.tslu_select(A, oracle.make_tree(L, TREE4))
-    assert nt == 0
+    t = oracle.make_tree(L, TREE4)
+    LU_o, ipiv_o, info_o, nt = oracle.calu(A, n, t, ld_pad=8)
+    assert nt == 0 and info_o == 0
     Ad = to_dev(A)
+    del A
     ipiv, info = ca.tslu(Ad, ca.make_tree(L, TREE4))
     torch.cuda.synchronize()
     assert info.cpu().tolist() == [0, 0]
-    perm = rows_from_ipiv(ipiv.cpu().numpy(), m)
-    assert np.array_equal(perm[:n], sel)
-    # U11 and L11: the LU without pivoting of the selected rows
-    LU = Ad[:n].cpu().numpy()
-    S = A[sel].copy()
-    for j in range(n):
-        S[j + 1:, j] /= S[j, j]
-        S[j + 1:, j + 1:] -= np.outer(S[j + 1:, j], S[j, j + 1:])
-    assert np.linalg.norm(LU - S) / np.linalg.norm(S) < 1e-12
-    # sampled rows of L21 = A21 U11^-1
-    rng = np.random.default_rng(1)
-    rows = rng.choice(np.arange(n, m), 2000, replace=False)
-    U = np.triu(S)
-    want = np.linalg.solve(U.T, A[perm[rows]].T).T
-    got = Ad[torch.from_numpy(rows).cuda()].cpu().numpy()
-    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-12
+    assert np.array_equal(ipiv.cpu().numpy(), ipiv_o)
+    check(lu_err(Ad.cpu().numpy(), LU_o), 1e-12, (m, n))
 
 
 @pytest.mark.parametrize("m,n", [(1_048_576, 64), (8_388_608, 32)])
 def test_tsqr_full_size(ca, m, n):
     L = 256
     A = inputs.gaussian(m, n, 2027)
-    QR_o, T_o = oracle.tsqr(A, oracle.make_tree(L, TREE4))
+    t = oracle.make_tree(L, TREE4)
+    QR_o, T_o = oracle.caqr(A, n, t, ld_pad=8)
     Ad = to_dev(A)
+    del A
     qtree, info = ca.tsqr(Ad, ca.make_tree(L, TREE4))
     torch.cuda.synchronize()
     assert info.cpu().tolist() == [0, 0]
-    QR = Ad.cpu().numpy()
-    R, R_o = np.triu(QR[:n]), np.triu(QR_o[:n])
-    assert np.linalg.norm(R - R_o) / np.linalg.norm(R_o) < 1e-12
-    assert np.linalg.norm(QR - QR_o) / np.linalg.norm(QR_o) < 1e-12      # every stored Y
-    T = qtree.cpu().numpy()[: T_o.size]
-    assert np.linalg.norm(T - T_o) / np.linalg.norm(T_o) < 1e-12          # every T
+    check(qr_err(Ad.cpu().numpy(), QR_o), 1e-12, (m, n))                      # R, every stored Y
+    check(qtree_err(qtree.cpu().numpy(), T_o, QR_o, n, t, oracle.tree_counts), 1e-12, (m, n))   # every T
+
+
+def test_calu_caqr_4096_benchmark_shape(ca):
+    """CALU and CAQR of 4096 x 4096 (iid N(0,1)) with the benchmark's panel
+    width, leaves and tree, against the full oracle (both oracle runs in two
+    threads: the C code runs without the interpreter lock)."""
+    import threading
+    n, b, L = 4096, 128, bench.BENCH_LEAF_ROWS
+    A = inputs.gaussian(n, n, 4096)
+    t = oracle.make_tree(L, BENCH_TREE)
+    out = {}
+    th = [threading.Thread(target=lambda: out.__setitem__("lu", oracle.calu(A, b, t, ld_pad=8))),
+          threading.Thread(target=lambda: out.__setitem__("qr", oracle.caqr(A, b, t, ld_pad=8)))]
+    for x in th:
+        x.start()
+    tree = ca.make_tree(L, BENCH_TREE)
+    Alu, Aqr = to_dev(A), to_dev(A)
+    ipiv, info = ca.calu_factor(Alu, b, tree)
+    qtree, qinfo = ca.caqr_factor(Aqr, b, tree)
+    torch.cuda.synchronize()
+    for x in th:
+        x.join()
+    LU_o, ipiv_o, info_o, nt = out["lu"]
+    QR_o, T_o = out["qr"]
+    assert nt == 0 and info_o == 0
+    assert info.cpu().tolist() == [0, 0] and qinfo.cpu().tolist() == [0, 0]
+    assert np.array_equal(ipiv.cpu().numpy(), ipiv_o)            # all 32 panels' pivots
+    check(lu_err(Alu.cpu().numpy(), LU_o), 1e-12, "CALU 4096")
+    check(qr_err(Aqr.cpu().numpy(), QR_o, b), 1e-12, "CAQR 4096")
+    check(qtree_err(qtree.cpu().numpy(), T_o, QR_o, b, t, oracle.tree_counts), 1e-12, "CAQR 4096 T")
 
 
 @pytest.fixture(scope="module")
