@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--cond", type=float, default=1e6)
     p.add_argument("--nrhs", type=int, default=1)
     p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--aux-steps", type=int, default=2,
+                   help="timed runs of each secondary measurement (LU forms, C3 grid), after one warm-up")
     p.add_argument("--cpu-n", type=int, default=2048,
                    help="order of the oracle sample timed for cpu_baseline (about 10 s on one core)")
     p.add_argument("--ref-n", type=int, default=1024,
@@ -256,6 +258,16 @@ def _oracle_worker(job, barrier, out):
     out.put((t0, time.monotonic(), step_flops(n, nrhs)))
 
 
+def usable_cores():
+    """(cores this process may run on, where the figure came from): the CPU
+    affinity mask (which honours cgroup / container limits set through it),
+    else os.cpu_count()."""
+    try:
+        return len(os.sched_getaffinity(0)), "sched_getaffinity"
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1, "os.cpu_count"
+
+
 def cpu_baseline_all_cores(a, cores=None):
     """The same oracle (unchanged, single-threaded) on every host core at
     once: one process per core, each on its own copy of the sample matrix,
@@ -266,7 +278,9 @@ def cpu_baseline_all_cores(a, cores=None):
     import queue as _queue
     import oracle
     oracle.build()
-    cores = cores or os.cpu_count() or 1
+    cores_source = "argument"
+    if not cores:
+        cores, cores_source = usable_cores()
     ctx = mp.get_context("spawn")
     barrier = ctx.Barrier(cores)
     out = ctx.Queue()
@@ -303,7 +317,8 @@ def cpu_baseline_all_cores(a, cores=None):
         return None
     span = max(r[1] for r in res) - min(r[0] for r in res)
     flops = sum(r[2] for r in res)
-    return {"value": flops / span / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+    return {"value": flops / span / 1e9, "unit": "GFLOP/s", "cores": cores, "cores_source": cores_source,
+            "kind": "oracle",
             "sample": (f"{cores} concurrent copies (one process per host core) of the single-core sample: "
                        f"oracle CALU+getrs and CAQR+geqrs of one {a.cpu_n}x{a.cpu_n} matrix each, "
                        f"{span:.1f} s"),
@@ -434,7 +449,7 @@ def derive_traffic(leaf_rate: float, merge_rate: float, n: int, b: int, leaf: in
             "bytes_per_wide_launch": total / max(1, len(wide))}
 
 
-TRAFFIC_SOURCES = {"tree_apply": "panel_qr.cu#tree_apply_kernel,ca_internal.cuh"}
+TRAFFIC_SOURCES = {"tree_apply": "panel_qr.cu#tree_apply_kernel,ca_internal.cuh#tree_plan"}
 
 
 def print_traffic_line(a):
@@ -453,7 +468,7 @@ def print_traffic_line(a):
           f"{a.nrhs} RHS; {d['narrow_launches']} narrow launches), derived by "
           f"python bench.py --derive-traffic {a.derive_traffic}: {leaf_rate} DRAM bytes per C element "
           f"of a leaf launch, {merge_rate} per stacked C element of a merge launch "
-          f"(ncu capture at n=6144 in tree_apply_n6144_full.md)")
+          f"(from an ncu capture of the leaf and merge launches at n=6144)")
 
 
 def source_text(csrc: str, item: str) -> bytes:
@@ -533,8 +548,10 @@ def run_ours(a, rank: int, world: int, local: int):
     X = torch.empty_like(B0)
     ipiv = torch.empty(n, dtype=torch.int32, device=dev)
     info = torch.zeros(2, dtype=torch.int32, device=dev)
+    qinfo = torch.zeros(2, dtype=torch.int32, device=dev)
     lwork = ca.ca_calu_workspace(n, n, b, tree)
     work = torch.empty((lwork + 7) // 8, dtype=torch.float64, device=dev)
+    swork = torch.empty((ca.ca_getrs_workspace(n, nrhs) + 7) // 8, dtype=torch.float64, device=dev)
     qb, qw = ca.ca_caqr_workspace(n, n, b, tree)
     qtree = torch.empty((qb + 7) // 8, dtype=torch.float64, device=dev)
     qwork = torch.empty((max(qw, ca.ca_geqrs_workspace(n, n, nrhs, b, tree)) + 7) // 8,
@@ -544,13 +561,23 @@ def run_ours(a, rank: int, world: int, local: int):
         A.copy_(src_A)
         X.copy_(src_B)
         ca.calu_factor(A, b, tree, ipiv=ipiv, work=work, dev_info=info)
-        ca.calu_getrs(A, ipiv, X)
+        ca.calu_getrs(A, ipiv, X, work=swork)
         x_lu = X.clone() if check else None
         A.copy_(src_A)
         X.copy_(src_B)
-        ca.caqr_factor(A, b, tree, qtree=qtree, work=qwork, dev_info=info)
+        ca.caqr_factor(A, b, tree, qtree=qtree, work=qwork, dev_info=qinfo)
         ca.caqr_geqrs(A, b, tree, qtree, X, work=qwork)
         return x_lu
+
+    def library_status():
+        """What the library reported about the last step: dev_info of the
+        factorizations and whether a triangular solve gave up waiting."""
+        return {"calu_info": info.cpu().tolist(), "caqr_info": qinfo.cpu().tolist(),
+                "getrs_timed_out": ca.ca_solve_status(swork), "geqrs_timed_out": ca.ca_solve_status(qwork)}
+
+    def status_ok(stt):
+        return (stt["calu_info"] == [0, 0] and stt["caqr_info"] == [0, 0] and not stt["getrs_timed_out"]
+                and not stt["geqrs_timed_out"])
 
     # ---- correctness of the timed configuration (untimed) -----------------
     check = True
@@ -591,6 +618,7 @@ def run_ours(a, rank: int, world: int, local: int):
         return ms, launches, clocks, kernels
 
     ms, launches, clocks, kernels = timed_region()
+    lib_status = library_status()   # the last timed step's own report (a failure voids the number)
     st = torch.cuda.current_stream()
     first_clocks = None
     # a region that saw a slowdown (on any rank) is measured once more
@@ -598,6 +626,7 @@ def run_ours(a, rank: int, world: int, local: int):
         first_clocks = clocks
         barrier(world)
         ms, launches, clocks, kernels = timed_region()
+        lib_status = library_status()
     ms_max = allreduce_max(ms, world)
 
     flops = step_flops(n, nrhs)
@@ -645,7 +674,7 @@ def run_ours(a, rank: int, world: int, local: int):
             A.copy_(A_h, non_blocking=True)      # H2D: the matrix
             X.copy_(B_h, non_blocking=True)      # H2D: the right-hand side
             ca.calu_factor(A, b, tree, ipiv=ipiv, work=work, dev_info=info)
-            ca.calu_getrs(A, ipiv, X)
+            ca.calu_getrs(A, ipiv, X, work=swork)
             X_h.copy_(X, non_blocking=True)      # D2H: the LU solution
             A.copy_(A_h, non_blocking=True)
             X.copy_(B_h, non_blocking=True)
@@ -695,7 +724,8 @@ def run_ours(a, rank: int, world: int, local: int):
         "clocks": clocks if first_clocks is None else dict(clocks, remeasured_after=first_clocks),
         "gpu_launches": launches,
         "kernels": kernels,
-        "check": {"x_rel_err_calu": err_lu, "x_rel_err_caqr": err_qr},
+        "check": {"x_rel_err_calu": err_lu, "x_rel_err_caqr": err_qr, "library_status": lib_status,
+                  "ok": status_ok(lib_status)},
         "lu_forms": lu_forms,
         "serving": serving,
         "batched": batched,
@@ -705,8 +735,8 @@ def run_ours(a, rank: int, world: int, local: int):
 
 
 def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
-    """CALU solve of A x = b three ways, each timed over a.steps runs after one
-    warm-up: plain FP64 (calu_factor + calu_getrs), the reduced-precision
+    """CALU solve of A x = b three ways, each timed over a.aux_steps runs after
+    one warm-up: plain FP64 (calu_factor + calu_getrs), the reduced-precision
     update on the tensor cores with FP64 refinement (calu_gesv_mixed), and the
     exact 7-digit tensor-core update (FP64-accurate factors) + calu_getrs."""
     n, b = a.n, a.b
@@ -726,9 +756,10 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
         e1 = torch.cuda.Event(enable_timing=True)
         if name:
             ca.ca_prof_enable(True, 200000)
+        reps = max(1, a.aux_steps)
         e0.record(st)
         res = None
-        for _ in range(a.steps):
+        for _ in range(reps):
             res = fn()
         e1.record(st)
         torch.cuda.synchronize()
@@ -737,10 +768,10 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
             for c, kn in enumerate(ca.KERNEL_CLASSES):
                 cnt, kms, kfl, _ = ca.ca_prof_read(c)
                 if cnt:
-                    ks[kn] = {"launches": cnt // a.steps, "ms": kms / a.steps, "gflop": kfl / a.steps / 1e9}
+                    ks[kn] = {"launches": cnt // reps, "ms": kms / reps, "gflop": kfl / reps / 1e9}
             ca.ca_prof_enable(False, 1)
             kernels_of[name] = ks
-        return allreduce_max(e0.elapsed_time(e1), world) / a.steps, res
+        return allreduce_max(e0.elapsed_time(e1), world) / reps, res
 
     def berr_of(Xs):
         R = B0 - A0 @ Xs
@@ -749,28 +780,30 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
         return float((num / den).max())
 
     work = torch.empty((ca.ca_calu_workspace(n, n, b, tree) + 7) // 8, dtype=torch.float64, device=A0.device)
+    swork = torch.empty((ca.ca_getrs_workspace(n, a.nrhs) + 7) // 8, dtype=torch.float64, device=A0.device)
 
     def plain():
         A.copy_(A0)
         X.copy_(B0)
         ca.calu_factor(A, b, tree, ipiv=ipiv, work=work, dev_info=info)
-        ca.calu_getrs(A, ipiv, X)
+        ca.calu_getrs(A, ipiv, X, work=swork)
 
     ms, _ = timed(plain)
     out["fp64"] = {"ms": ms, "gflops": lu_flops / ms / 1e6, "berr": berr_of(X),
                    "form": "calu_factor + calu_getrs, FP64 DFMA update"}
     S, ex = a.mixed_slices, bool(a.mixed_exact)
     LU = torch.empty_like(A0)
-    wmix = torch.empty((ca.ca_gesv_mixed_workspace(n, a.nrhs, b, tree, S, ex) + 7) // 8,
+    wmix = torch.empty((ca.ca_gesv_mixed_workspace(n, a.nrhs, b, tree, S, ex, "auto") + 7) // 8,
                        dtype=torch.float64, device=A0.device)
 
     def mixed():
         _, it, be, _ = ca.calu_gesv_mixed(A0, B0, b, tree, slices=S, exact=ex, max_iter=30, tol=1e-14,
-                                          LU=LU, X=X, ipiv=ipiv, work=wmix, dev_info=info)
+                                          refine="auto", LU=LU, X=X, ipiv=ipiv, work=wmix, dev_info=info)
         return it, be
 
     ms, (it, be) = timed(mixed, "mixed_ir")
-    out["mixed_ir"] = {"ms": ms, "gflops": lu_flops / ms / 1e6, "iters": it, "berr": be,
+    it, be = int(it.item()), float(be.item())
+    out["mixed_ir"] = {"ms": ms, "gflops": lu_flops / ms / 1e6, "iters": it, "berr": be, "refine": "auto",
                        "berr_check": berr_of(X), "slices": S, "exact": ex,
                        "x_rel_err": float(torch.linalg.norm(X - x_true) / torch.linalg.norm(x_true)),
                        "speedup_vs_fp64": out["fp64"]["ms"] / ms,
@@ -782,7 +815,7 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
         A.copy_(A0)
         X.copy_(B0)
         ca.calu_factor_mixed(A, b, tree, slices=7, exact=True, ipiv=ipiv, work=wemu, dev_info=info)
-        ca.calu_getrs(A, ipiv, X)
+        ca.calu_getrs(A, ipiv, X, work=swork)
 
     ms, _ = timed(emulated, "fp64_emulated")
     out["fp64_emulated"] = {"ms": ms, "gflops": lu_flops / ms / 1e6, "berr": berr_of(X),

@@ -90,6 +90,14 @@ typedef struct {
 #define CA_ERR_BATCH_ITEM -1005  /* an item of a batch is invalid            */
 
 #define CA_STATUS_NONFINITE 1
+#define CA_STATUS_SOLVE_TIMEOUT 16 /* dev_info[1] of calu_gesv_mixed: a solve gave up waiting */
+#define CA_STATUS_REFACTORED 32    /* dev_info[1] of calu_gesv_mixed: the fallback refactorization ran */
+
+/* Correction method of calu_gesv_mixed's refinement */
+#define CA_REFINE_CLASSIC 0 /* x += M^-1 r, one solve with the reduced-precision factors M */
+#define CA_REFINE_GMRES 1   /* x += d, (M^-1 A) d = M^-1 r solved by GMRES                 */
+#define CA_REFINE_AUTO 2    /* classic while each step gains 10x, then GMRES, then a      */
+                            /* refactorization with 7 exact digits if GMRES stalls too   */
 
 /* Human-readable text for a return code (static storage). */
 const char *ca_strerror(int code);
@@ -109,8 +117,14 @@ int ca_calu_workspace(int m, int n, int b, const ca_tree_t *tree, size_t *work_b
 int ca_caqr_workspace(int m, int n, int b, const ca_tree_t *tree, size_t *qtree_bytes,
                       size_t *work_bytes);
 
-/* Bytes of scratch workspace needed by caqr_geqrs. */
+/* Bytes of scratch workspace needed by caqr_geqrs (its first bytes are a
+ * solve workspace, as for calu_getrs). */
 int ca_geqrs_workspace(int m, int n, int nrhs, int b, const ca_tree_t *tree, size_t *work_bytes);
+
+/* Bytes of the solve workspace of calu_getrs for order n (a few hundred
+ * bytes: the ready flags of the dependency-ordered triangular solves and a
+ * timeout record).  Arguments: 1 n, 2 nrhs, 3 work_bytes. */
+int ca_getrs_workspace(int n, int nrhs, size_t *work_bytes);
 
 /* ------------------------------------------------------------------------ */
 /* LU with tournament pivoting                                              */
@@ -133,7 +147,7 @@ int calu_factor(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, 
                 void *work, size_t lwork, int *dev_info, cudaStream_t stream);
 
 /* tslu: the panel factorization alone (TSLU, Sec. 3.2): calu_factor of an
- * m x n tall-skinny matrix with a single panel of width n (n <= 256). */
+ * m x n tall-skinny matrix with a single panel of width n (n <= 128). */
 int tslu(int m, int n, double *A, int lda, const ca_tree_t *tree, int *ipiv, void *work,
          size_t lwork, int *dev_info, cudaStream_t stream);
 
@@ -166,10 +180,14 @@ int tslu_noalloc(int m, int n, double *A, int lda, const ca_tree_t *tree, int *i
 /* calu_getrs: solve A X = B from calu_factor's output (n x n, PA = LU):
  * apply the ipiv swaps to B, then forward substitution with the unit L and
  * back substitution with U (Sec. 3.2: PA = LU).  B is n x nrhs (ld ldb),
- * overwritten with X.  Arguments: 1 n, 2 nrhs, 3 LU, 4 lda, 5 ipiv, 6 B,
- * 7 ldb, 8 stream. */
+ * overwritten with X.  work: device memory of ca_getrs_workspace bytes, owned
+ * by the caller (the triangular solves with up to 16 right-hand sides order
+ * their 128-row blocks by ready flags kept there; the library allocates
+ * nothing); one workspace must not be used by two solves in flight at once.
+ * Arguments: 1 n, 2 nrhs, 3 LU, 4 lda, 5 ipiv, 6 B, 7 ldb, 8 work, 9 lwork,
+ * 10 stream. */
 int calu_getrs(int n, int nrhs, const double *LU, int lda, const int *ipiv, double *B, int ldb,
-               cudaStream_t stream);
+               void *work, size_t lwork, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* QR by tree-based Householder reflections                                 */
@@ -203,7 +221,7 @@ int caqr_factor(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, 
 
 /* tsqr: the panel factorization alone (TSQR, Sec. 3.1 R-elimination tree):
  * caqr_factor of an m x n tall-skinny matrix with one panel of width n
- * (n <= 256). */
+ * (n <= 128). */
 int tsqr(int m, int n, double *A, int lda, const ca_tree_t *tree, double *qtree,
          size_t qtree_bytes, void *work, size_t lwork, int *dev_info, cudaStream_t stream);
 
@@ -217,16 +235,25 @@ int caqr_geqrs(int m, int n, int nrhs, const double *QR, int lda, int b, const c
                const double *qtree, size_t qtree_bytes, double *B, int ldb, void *work,
                size_t lwork, cudaStream_t stream);
 
-/* ca_solve_status: the triangular solves of calu_getrs, caqr_geqrs and
- * calu_gesv_mixed order their diagonal blocks by ready flags in device
- * memory (one flag array per device and stream); each wait for a flag is
- * bounded (about 2 s of SM clock) and a wait that gives up is recorded.
- * This call synchronizes `stream`, sets *timed_out to 1 if a solve on it
- * gave up since the previous call (its right-hand sides are then only partly
- * solved) and to 0 otherwise, and clears the record.  No counterpart in the
- * paper.  Returns CA_OK, -2 for a NULL timed_out, CA_ERR_LAUNCH on a CUDA
+/* ca_solve_status: the dependency-ordered triangular solves of calu_getrs
+ * and caqr_geqrs wait for ready flags in their workspace; every wait is
+ * bounded (about 2 s of SM clock) and a wait that gives up is recorded in the
+ * workspace (the first int; each solve clears it when it starts).  This call
+ * synchronizes `stream`, then sets *timed_out to 1 if the last solve that
+ * used `work` gave up (its right-hand sides are then only partly solved) and
+ * to 0 otherwise.  No counterpart in the paper.  Arguments: 1 work (the
+ * workspace given to calu_getrs / caqr_geqrs), 2 timed_out (host), 3 stream.
+ * Returns CA_OK, -1 / -2 for a NULL argument, CA_ERR_LAUNCH on a CUDA
  * error. */
-int ca_solve_status(cudaStream_t stream, int *timed_out);
+int ca_solve_status(const void *work, int *timed_out, cudaStream_t stream);
+
+/* ca_test_solve_hook: a test hook with no counterpart in the paper.  With
+ * withhold = 1, the dependency-ordered triangular solves enqueued after this
+ * call leave their first block's ready flag unset, so every wait on it runs
+ * out after wait_cycles SM clock cycles (<= 0: the default, about 2 s) and
+ * the timeout is recorded; withhold = 0 restores normal solves.  Host state
+ * of the library, not thread-safe against solves being enqueued. */
+void ca_test_solve_hook(long long wait_cycles, int withhold);
 
 /* ------------------------------------------------------------------------ */
 /* Reduced-precision trailing update on the tensor cores                    */
@@ -282,24 +309,40 @@ int caqr_factor_mixed(int m, int n, double *A, int lda, int b, const ca_tree_t *
                       int exact, double *qtree, size_t qtree_bytes, void *work, size_t lwork,
                       int *dev_info, cudaStream_t stream);
 
-/* calu_gesv_mixed: solve A X = B (n x n, nrhs <= 256) by the mixed
- * factorization plus FP64 iterative refinement: LU <- A (copy in the caller's
- * LU buffer), calu_factor_mixed, X = U^-1 L^-1 P B, then repeat R = B - A X
- * (FP64), stop when the normwise backward error
+/* calu_gesv_mixed: solve A X = B (n x n) by the mixed factorization plus
+ * FP64 iterative refinement: LU <- A (copy in the caller's LU buffer),
+ * calu_factor_mixed, X = U^-1 L^-1 P B, then repeat R = B - A X (FP64),
+ * stop when the normwise backward error
  * max_j ||R_j||inf / (||A||inf ||X_j||inf + ||B_j||inf) <= tol, when it fails
- * to halve twice in a row, or after max_iter corrections X += (LU)^-1 R.
- * Unlike the other entry points this call waits for the stream (it reads the
- * backward error on the host once per step).  *iters gets the number of
- * corrections, *berr the final backward error (host pointers, may be NULL).
- * Arguments: 1 n, 2 nrhs, 3 A, 4 lda, 5 b, 6 tree, 7 slices, 8 exact, 9 LU,
- * 10 ldlu, 11 ipiv, 12 B, 13 ldb, 14 X, 15 ldx, 16 work, 17 lwork,
- * 18 max_iter, 19 tol, 20 iters, 21 berr, 22 dev_info, 23 stream. */
-int ca_gesv_mixed_workspace(int n, int nrhs, int b, const ca_tree_t *tree, int slices, int exact,
+ * to halve twice in a row, or after max_iter corrections.  The correction
+ * (`refine`): CA_REFINE_CLASSIC X += (LU)^-1 R; CA_REFINE_GMRES X += D with
+ * (M^-1 A) D = M^-1 R solved column by column by GMRES (FP64, at most 20
+ * steps, until the preconditioned residual drops by 1e-6), M = P^T L U the
+ * reduced-precision factors, which converges for matrices too ill
+ * conditioned for the classic correction with the same digits; CA_REFINE_AUTO
+ * three phases, each started only if the one before stopped above tol:
+ * classic corrections while every step reduces the backward error at least
+ * tenfold (up to max_iter); then up to 3 GMRES corrections; then, when the
+ * reduced-precision factors are too far from A for either to converge
+ * (roughly cond(A) 2^(-8 slices) >= 1), A factored again with 7 exact digits
+ * (FP64-accurate factors), X from those and up to 3 classic corrections, with
+ * CA_STATUS_REFACTORED in dev_info[1] (dev_info[0] then describes the second
+ * factorization, and ipiv / LU hold it).  The stop tests run on the device:
+ * the whole procedure is enqueued and the call returns without waiting
+ * (kernels of steps and phases that are not needed do nothing).
+ * dev_iters (int) and dev_berr (double), device pointers or NULL, receive
+ * the number of corrections and the final backward error.  dev_info[1] gets
+ * CA_STATUS_SOLVE_TIMEOUT if a triangular solve gave up waiting, and the
+ * tensor-core timeout bits.  Arguments: 1 n, 2 nrhs, 3 A, 4 lda, 5 b,
+ * 6 tree, 7 slices, 8 exact, 9 refine, 10 LU, 11 ldlu, 12 ipiv, 13 B,
+ * 14 ldb, 15 X, 16 ldx, 17 work, 18 lwork, 19 max_iter, 20 tol,
+ * 21 dev_iters, 22 dev_berr, 23 dev_info, 24 stream. */
+int ca_gesv_mixed_workspace(int n, int nrhs, int b, const ca_tree_t *tree, int slices, int exact, int refine,
                             size_t *work_bytes);
 int calu_gesv_mixed(int n, int nrhs, const double *A, int lda, int b, const ca_tree_t *tree,
-                    int slices, int exact, double *LU, int ldlu, int *ipiv, const double *B, int ldb,
-                    double *X, int ldx, void *work, size_t lwork, int max_iter, double tol,
-                    int *iters, double *berr, int *dev_info, cudaStream_t stream);
+                    int slices, int exact, int refine, double *LU, int ldlu, int *ipiv, const double *B,
+                    int ldb, double *X, int ldx, void *work, size_t lwork, int max_iter, double tol,
+                    int *dev_iters, double *dev_berr, int *dev_info, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batched factorizations: many small matrices of uneven shapes, each with   */

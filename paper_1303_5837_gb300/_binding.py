@@ -26,6 +26,12 @@ CA_ERR_LAUNCH = -1003
 CA_ERR_TREE = -1004
 CA_ERR_BATCH_ITEM = -1005
 CA_STATUS_NONFINITE = 1
+CA_STATUS_SOLVE_TIMEOUT = 16
+CA_STATUS_REFACTORED = 32
+CA_REFINE_CLASSIC = 0
+CA_REFINE_GMRES = 1
+CA_REFINE_AUTO = 2
+REFINE = {"classic": CA_REFINE_CLASSIC, "gmres": CA_REFINE_GMRES, "auto": CA_REFINE_AUTO}
 CA_BATCH_CALU = 0
 CA_BATCH_CAQR = 1
 CA_DTYPE_F64 = 0
@@ -96,7 +102,8 @@ SYMBOLS = ("ca_strerror", "ca_calu_workspace", "ca_caqr_workspace", "ca_geqrs_wo
            "ca_prof_enable", "ca_prof_read", "ca_launch_count", "ca_kernel_class_name",
            "ca_gemm_mixed_workspace", "ca_gemm_minus_mixed", "ca_calu_mixed_workspace",
            "calu_factor_mixed", "ca_gesv_mixed_workspace", "calu_gesv_mixed", "ca_caqr_mixed_workspace",
-           "caqr_factor_mixed", "ca_batched_plan", "ca_batched_factor", "ca_solve_status")
+           "caqr_factor_mixed", "ca_batched_plan", "ca_batched_factor", "ca_solve_status",
+           "ca_getrs_workspace", "ca_test_solve_hook", "tslu_noalloc")
 KERNEL_CLASSES = ("tslu_node", "laswp", "lu_finish", "trsm_u12", "gemm_fp64", "tsqr_node",
                   "tree_apply", "solve", "split_bf16", "gemm_tc", "refine", "batched",
                   "tree_narrow")
@@ -127,7 +134,10 @@ def load(build_if_missing: bool = True):
     L.ca_geqrs_workspace.argtypes = [I, I, I, I, T, PS]
     L.calu_factor.argtypes = [I, I, P, I, I, T, P, P, S, P, P]
     L.tslu.argtypes = [I, I, P, I, T, P, P, S, P, P]
-    L.calu_getrs.argtypes = [I, I, P, I, P, P, I, P]
+    L.calu_getrs.argtypes = [I, I, P, I, P, P, I, P, S, P]
+    L.ca_getrs_workspace.argtypes = [I, I, PS]
+    L.ca_test_solve_hook.argtypes = [ctypes.c_longlong, I]
+    L.ca_test_solve_hook.restype = None
     L.caqr_factor.argtypes = [I, I, P, I, I, T, P, S, P, S, P, P]
     L.tsqr.argtypes = [I, I, P, I, T, P, S, P, S, P, P]
     L.caqr_geqrs.argtypes = [I, I, I, P, I, I, T, P, S, P, I, P, S, P]
@@ -135,14 +145,14 @@ def load(build_if_missing: bool = True):
     L.ca_gemm_minus_mixed.argtypes = [I, I, I, P, I, P, I, P, I, I, I, P, S, P, P]
     L.ca_calu_mixed_workspace.argtypes = [I, I, I, T, I, I, PS]
     L.calu_factor_mixed.argtypes = [I, I, P, I, I, T, I, I, P, P, S, P, P]
-    L.ca_gesv_mixed_workspace.argtypes = [I, I, I, T, I, I, PS]
-    L.calu_gesv_mixed.argtypes = [I, I, P, I, I, T, I, I, P, I, P, P, I, P, I, P, S, I,
-                                  ctypes.c_double, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_double), P, P]
+    L.ca_gesv_mixed_workspace.argtypes = [I, I, I, T, I, I, I, PS]
+    L.calu_gesv_mixed.argtypes = [I, I, P, I, I, T, I, I, I, P, I, P, P, I, P, I, P, S, I,
+                                  ctypes.c_double, P, P, P, P]
     L.ca_caqr_mixed_workspace.argtypes = [I, I, I, T, I, I, PS, PS]
     L.caqr_factor_mixed.argtypes = [I, I, P, I, I, T, I, I, P, S, P, S, P, P]
     L.ca_batched_plan.argtypes = [I, ctypes.POINTER(ca_batch_item_t), I, P, PS, PS]
     L.ca_batched_factor.argtypes = [P, P, P, S, P]
-    L.ca_solve_status.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+    L.ca_solve_status.argtypes = [P, ctypes.POINTER(ctypes.c_int), P]
     L.ca_prof_enable.argtypes = [I, I]
     L.ca_prof_read.argtypes = [I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)]
@@ -247,10 +257,21 @@ def tslu(A: torch.Tensor, tree: ca_tree_t, ipiv=None, work=None, dev_info=None, 
     return ipiv[: min(m, n)], dev_info
 
 
-def calu_getrs(LU: torch.Tensor, ipiv: torch.Tensor, B: torch.Tensor, stream=None):
+def ca_getrs_workspace(n: int, nrhs: int) -> int:
+    w = ctypes.c_size_t(0)
+    _check("ca_getrs_workspace", load().ca_getrs_workspace(n, nrhs, ctypes.byref(w)))
+    return w.value
+
+
+def calu_getrs(LU: torch.Tensor, ipiv: torch.Tensor, B: torch.Tensor, work=None, stream=None):
+    """Solve from CALU factors; B (n x nrhs) is overwritten with X.  work: the
+    solve workspace (ca_getrs_workspace bytes; made here when None)."""
     n, _, lda = _mat(LU, "LU")
     nb, nrhs, ldb = _mat(B, "B")
-    rc = load().calu_getrs(n, nrhs, _ptr(LU), lda, _ptr(ipiv), _ptr(B), ldb, _stream(stream))
+    if work is None:
+        work = _buf(ca_getrs_workspace(n, nrhs), LU.device)
+    rc = load().calu_getrs(n, nrhs, _ptr(LU), lda, _ptr(ipiv), _ptr(B), ldb, _ptr(work),
+                           work.numel() * work.element_size(), _stream(stream))
     _check("calu_getrs", rc)
     return B
 
@@ -304,13 +325,19 @@ def caqr_geqrs(QR: torch.Tensor, b: int, tree: ca_tree_t, qtree: torch.Tensor, B
     return B
 
 
-def ca_solve_status(stream=None) -> bool:
-    """Synchronizes the stream; True if a triangular solve on it gave up
-    waiting for a block's ready flag since the previous call (its
-    right-hand sides are then only partly solved).  Clears the record."""
+def ca_solve_status(work: torch.Tensor, stream=None) -> bool:
+    """Synchronizes the stream; True if the last solve that used this solve
+    workspace (of calu_getrs or caqr_geqrs) gave up waiting for a block's
+    ready flag (its right-hand sides are then only partly solved)."""
     t = ctypes.c_int(0)
-    _check("ca_solve_status", load().ca_solve_status(_stream(stream), ctypes.byref(t)))
+    _check("ca_solve_status", load().ca_solve_status(_ptr(work), ctypes.byref(t), _stream(stream)))
     return bool(t.value)
+
+
+def ca_test_solve_hook(wait_cycles: int = 0, withhold: bool = False):
+    """Test hook: withhold=True makes the next dependency-ordered solves leave
+    their first block unpublished, so their waits run out after wait_cycles."""
+    load().ca_test_solve_hook(int(wait_cycles), 1 if withhold else 0)
 
 
 # ---------------------------------------------------------------------------
@@ -405,19 +432,26 @@ def calu_factor_mixed(A: torch.Tensor, b: int, tree: ca_tree_t, slices: int = 3,
     return ipiv[: min(m, n)], dev_info
 
 
-def ca_gesv_mixed_workspace(n: int, nrhs: int, b: int, tree: ca_tree_t, slices: int, exact: bool) -> int:
+def _refine(refine) -> int:
+    return REFINE[refine] if isinstance(refine, str) else int(refine)
+
+
+def ca_gesv_mixed_workspace(n: int, nrhs: int, b: int, tree: ca_tree_t, slices: int, exact: bool,
+                            refine="classic") -> int:
     w = ctypes.c_size_t(0)
     _check("ca_gesv_mixed_workspace",
            load().ca_gesv_mixed_workspace(n, nrhs, b, ctypes.byref(tree), slices, 1 if exact else 0,
-                                          ctypes.byref(w)))
+                                          _refine(refine), ctypes.byref(w)))
     return w.value
 
 
 def calu_gesv_mixed(A: torch.Tensor, B: torch.Tensor, b: int, tree: ca_tree_t, slices: int = 3,
-                    exact: bool = False, max_iter: int = 30, tol: float = 1e-14, LU=None, X=None,
-                    ipiv=None, work=None, dev_info=None, stream=None):
-    """Mixed-precision CALU + FP64 iterative refinement.
-    Returns (X, iterations, backward error, dev_info); waits for the stream."""
+                    exact: bool = False, max_iter: int = 30, tol: float = 1e-14, refine="classic", LU=None,
+                    X=None, ipiv=None, work=None, dev_info=None, iters=None, berr=None, stream=None):
+    """Mixed-precision CALU + FP64 iterative refinement (refine: "classic",
+    "gmres" or "auto").  Returns (X, iterations, backward error, dev_info);
+    iterations (int32[1]) and backward error (float64[1]) are device tensors
+    written on the stream (the call does not wait)."""
     n, n2, lda = _mat(A, "A")
     nb, nrhs, ldb = _mat(B, "B")
     dev = A.device
@@ -429,18 +463,20 @@ def calu_gesv_mixed(A: torch.Tensor, B: torch.Tensor, b: int, tree: ca_tree_t, s
         ipiv = torch.empty(max(1, n), dtype=torch.int32, device=dev)
     if dev_info is None:
         dev_info = torch.zeros(2, dtype=torch.int32, device=dev)
+    if iters is None:
+        iters = torch.zeros(1, dtype=torch.int32, device=dev)
+    if berr is None:
+        berr = torch.zeros(1, dtype=torch.float64, device=dev)
     if work is None:
-        work = _buf(ca_gesv_mixed_workspace(n, nrhs, b, tree, slices, exact), dev)
+        work = _buf(ca_gesv_mixed_workspace(n, nrhs, b, tree, slices, exact, refine), dev)
     _, _, ldlu = _mat(LU, "LU")
     _, _, ldx = _mat(X, "X")
-    it = ctypes.c_int(0)
-    be = ctypes.c_double(0)
     rc = load().calu_gesv_mixed(n, nrhs, _ptr(A), lda, b, ctypes.byref(tree), slices, 1 if exact else 0,
-                                _ptr(LU), ldlu, _ptr(ipiv), _ptr(B), ldb, _ptr(X), ldx, _ptr(work),
-                                work.numel() * 8, max_iter, tol, ctypes.byref(it), ctypes.byref(be),
+                                _refine(refine), _ptr(LU), ldlu, _ptr(ipiv), _ptr(B), ldb, _ptr(X), ldx,
+                                _ptr(work), work.numel() * 8, max_iter, tol, _ptr(iters), _ptr(berr),
                                 _ptr(dev_info), _stream(stream))
     _check("calu_gesv_mixed", rc)
-    return X, it.value, be.value, dev_info
+    return X, iters, berr, dev_info
 
 
 def ca_caqr_mixed_workspace(m: int, n: int, b: int, tree: ca_tree_t, slices: int, exact: bool):

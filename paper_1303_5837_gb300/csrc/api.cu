@@ -10,9 +10,6 @@
 
 namespace cagb {
 
-// solve.cu: whether a dependency-ordered solve on `st` gave up waiting
-cudaError_t solve_timeout_read(cudaStream_t st, int *timed_out);
-
 // NVTX range around a host-side step (a panel of CALU / CAQR): visible in a
 // timeline profiler, a null operation when none is attached.
 struct NvtxRange {
@@ -42,7 +39,6 @@ using namespace cagb;
 namespace {
 
 constexpr int kMaxB = 128;
-constexpr int kMaxRhsHost = 256;  // right-hand sides whose backward error is checked
 
 int check_tree(const ca_tree_t *t, int b) {
   if (!t) return 1;
@@ -144,7 +140,7 @@ Lookahead *lookahead_for(cudaStream_t user) {
 // trailing update runs in FP64 (tcws == nullptr) or on the tensor cores with
 // `slices` digits (reduced precision, exact = per-diagonal accumulators).
 int calu_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int *ipiv, void *work, int nl,
-             void *tcws, int slices, int exact, int *dev_info, cudaStream_t stream) {
+             void *tcws, int slices, int exact, int *dev_info, cudaStream_t stream, const int *skip = nullptr) {
   if (cudaMemsetAsync(dev_info, 0, 2 * sizeof(int), stream) != cudaSuccess) return CA_ERR_LAUNCH;
   const int K = m < n ? m : n;
   if (K == 0) return CA_OK;
@@ -157,8 +153,9 @@ int calu_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int
   auto update = [&](int mrows, int ncols, int kdim, const double *L21, const double *U12, double *C) -> cudaError_t {
     if (mrows <= 0 || ncols <= 0) return cudaSuccess;
     if (tcws)
-      return gemm_minus_tc(mrows, ncols, kdim, L21, lda, U12, lda, C, lda, slices, exact, tcws, dev_info + 1, stream);
-    return gemm_minus_f64(mrows, ncols, kdim, L21, lda, U12, lda, C, lda, stream);
+      return gemm_minus_tc(mrows, ncols, kdim, L21, lda, U12, lda, C, lda, slices, exact, tcws, dev_info + 1, stream,
+                           skip);
+    return gemm_minus_f64(mrows, ncols, kdim, L21, lda, U12, lda, C, lda, stream, skip);
   };
   for (int kb = 0; kb < K; kb += b) {
     NvtxRange range("calu panel");
@@ -170,20 +167,20 @@ int calu_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int
     cudaStream_t ps = la ? la->helper : stream;
     if (la && cudaStreamWaitEvent(ps, la->ev_next, 0) != cudaSuccess) return CA_ERR_LAUNCH;
     // 1. tournament pivoting over the tree (TSLU)
-    if (tslu_panel(mk, bk, P, lda, L, plan, ws, ipiv + kb, kb, dev_info, ps) != cudaSuccess)
+    if (tslu_panel(mk, bk, P, lda, L, plan, ws, ipiv + kb, kb, dev_info, ps, skip) != cudaSuccess)
       return CA_ERR_LAUNCH;
     if (la && (cudaEventRecord(la->ev_panel, ps) != cudaSuccess ||
                cudaStreamWaitEvent(stream, la->ev_panel, 0) != cudaSuccess))
       return CA_ERR_LAUNCH;
     // 2. swap rows at left and right of the panel
-    if (laswp_apply(n, A, lda, kb, ws, bk, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+    if (laswp_apply(n, A, lda, kb, ws, bk, stream, skip) != cudaSuccess) return CA_ERR_LAUNCH;
     // 3. L11 \\ U11 into place, L21 = A21 U11^-1
-    if (lu_panel_finish(mk, bk, P, lda, ws, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+    if (lu_panel_finish(mk, bk, P, lda, ws, stream, skip) != cudaSuccess) return CA_ERR_LAUNCH;
     const int nt = n - kb - bk;
     if (nt > 0) {
       double *A12 = A + kb + (size_t)(kb + bk) * lda;
       // 4. U12 = L11^-1 A12
-      if (trsm_u12(bk, nt, ws.lu11, bk, A12, lda, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+      if (trsm_u12(bk, nt, ws.lu11, bk, A12, lda, stream, skip) != cudaSuccess) return CA_ERR_LAUNCH;
       // 5. A22 -= L21 U12: first the next panel's columns, then the rest
       //    (the next tournament starts in between)
       const int nnext = (kb + bk < K) ? ((K - kb - bk < b) ? K - kb - bk : b) : 0;
@@ -258,6 +255,16 @@ int caqr_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, dou
   return CA_OK;
 }
 
+// P A = L U solve on `stream`: swaps, unit-lower and upper substitution.
+// Given-up waits of the dependency-ordered solves go to status |= bit.
+cudaError_t getrs_run(int n, int nrhs, const double *LU, int lda, const int *ipiv, double *B, int ldb,
+                      const SolveWs &sw, int *status, int bit, const int *skip, cudaStream_t stream) {
+  cudaError_t e = getrs_swap(n, nrhs, ipiv, B, ldb, stream, skip);
+  if (e != cudaSuccess) return e;
+  if ((e = trsm_left(true, true, n, nrhs, LU, lda, B, ldb, sw, status, bit, skip, stream)) != cudaSuccess) return e;
+  return trsm_left(false, false, n, nrhs, LU, lda, B, ldb, sw, status, bit, skip, stream);
+}
+
 size_t caqr_mixed_ws(int m, int n, int b, const ca_tree_t *tree, int nl, int slices) {
   const int bk = b < n ? b : n;
   return 2 * align256(qr_panel_ws_bytes(nl)) +
@@ -326,7 +333,15 @@ int ca_geqrs_workspace(int m, int n, int nrhs, int b, const ca_tree_t *tree, siz
   int rc = qr_shape(m, n, b, tree, &nl, &q);
   if (rc == -5 || rc == -6) rc = (rc == -5) ? -4 : -5;
   if (rc != CA_OK) return rc;
-  *work_bytes = qr_panel_ws_bytes(nl);
+  *work_bytes = align256(solve_ws_bytes(n)) + qr_panel_ws_bytes(nl);
+  return CA_OK;
+}
+
+int ca_getrs_workspace(int n, int nrhs, size_t *work_bytes) {
+  if (n < 0) return -1;
+  if (nrhs < 0) return -2;
+  if (!work_bytes) return -3;
+  *work_bytes = solve_ws_bytes(n);
   return CA_OK;
 }
 
@@ -356,8 +371,8 @@ int tslu(int m, int n, double *A, int lda, const ca_tree_t *tree, int *ipiv, voi
   return rc;
 }
 
-int calu_getrs(int n, int nrhs, const double *LU, int lda, const int *ipiv, double *B, int ldb,
-               cudaStream_t stream) {
+int calu_getrs(int n, int nrhs, const double *LU, int lda, const int *ipiv, double *B, int ldb, void *work,
+               size_t lwork, cudaStream_t stream) {
   if (n < 0) return -1;
   if (nrhs < 0) return -2;
   if (n > 0 && !LU) return -3;
@@ -366,9 +381,12 @@ int calu_getrs(int n, int nrhs, const double *LU, int lda, const int *ipiv, doub
   if (n > 0 && nrhs > 0 && !B) return -6;
   if (ldb < (n > 1 ? n : 1)) return -7;
   if (n == 0 || nrhs == 0) return CA_OK;
-  if (getrs_swap(n, nrhs, ipiv, B, ldb, stream) != cudaSuccess) return CA_ERR_LAUNCH;
-  if (trsm_left(true, true, n, nrhs, LU, lda, B, ldb, stream) != cudaSuccess) return CA_ERR_LAUNCH;
-  if (trsm_left(false, false, n, nrhs, LU, lda, B, ldb, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if (!work || lwork < solve_ws_bytes(n)) return CA_ERR_WORKSPACE;
+  SolveWs sw;
+  solve_ws_carve(work, n, sw);
+  if (cudaMemsetAsync(sw.status, 0, sizeof(int), stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if (getrs_run(n, nrhs, LU, lda, ipiv, B, ldb, sw, sw.status, 1, nullptr, stream) != cudaSuccess)
+    return CA_ERR_LAUNCH;
   return CA_OK;
 }
 
@@ -413,9 +431,13 @@ int caqr_geqrs(int m, int n, int nrhs, const double *QR, int lda, int b, const c
   if (n == 0 || nrhs == 0) return CA_OK;
   if (!B) return -10;
   if (!qtree || qtree_bytes < qneed) return CA_ERR_WORKSPACE;
-  if (!work || lwork < qr_panel_ws_bytes(nl)) return CA_ERR_WORKSPACE;
+  const size_t swb = align256(solve_ws_bytes(n));
+  if (!work || lwork < swb + qr_panel_ws_bytes(nl)) return CA_ERR_WORKSPACE;
+  SolveWs sw;
+  solve_ws_carve(work, n, sw);
+  if (cudaMemsetAsync(sw.status, 0, sizeof(int), stream) != cudaSuccess) return CA_ERR_LAUNCH;
   QrPanelWs ws;
-  qr_panel_ws_carve(work, nl, ws);
+  qr_panel_ws_carve((char *)work + swb, nl, ws);
   const int L = tree->leaf_rows;
   size_t off = 0;
   for (int kb = 0; kb < n; kb += b) {
@@ -428,14 +450,22 @@ int caqr_geqrs(int m, int n, int nrhs, const double *QR, int lda, int b, const c
       return CA_ERR_LAUNCH;
     off += (size_t)(plan.nleaves + plan.nmerges) * b * b;
   }
-  if (trsm_left(false, false, n, nrhs, QR, lda, B, ldb, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if (trsm_left(false, false, n, nrhs, QR, lda, B, ldb, sw, sw.status, 1, nullptr, stream) != cudaSuccess)
+    return CA_ERR_LAUNCH;
   return CA_OK;
 }
 
-int ca_solve_status(cudaStream_t stream, int *timed_out) {
+int ca_solve_status(const void *work, int *timed_out, cudaStream_t stream) {
+  if (!work) return -1;
   if (!timed_out) return -2;
-  return cagb::solve_timeout_read(stream, timed_out) == cudaSuccess ? CA_OK : CA_ERR_LAUNCH;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  int word = 0;
+  if (cudaMemcpy(&word, work, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CA_ERR_LAUNCH;
+  *timed_out = word != 0;
+  return CA_OK;
 }
+
+void ca_test_solve_hook(long long wait_cycles, int withhold) { solve_test_hook(wait_cycles, withhold ? 0 : -1); }
 
 int ca_gemm_mixed_workspace(int m, int n, int k, int slices, int exact, size_t *work_bytes) {
   if (m < 0) return -1;
@@ -502,22 +532,28 @@ int calu_factor_mixed(int m, int n, double *A, int lda, int b, const ca_tree_t *
   return calu_run(m, n, A, lda, b, tree, ipiv, work, nl, tcws, slices, exact, dev_info, stream);
 }
 
-int ca_gesv_mixed_workspace(int n, int nrhs, int b, const ca_tree_t *tree, int slices, int exact,
+int ca_gesv_mixed_workspace(int n, int nrhs, int b, const ca_tree_t *tree, int slices, int exact, int refine,
                             size_t *work_bytes) {
   if (nrhs < 0) return -2;
   size_t w = 0;
   int rc = ca_calu_mixed_workspace(n, n, b, tree, slices, exact, &w);
   if (rc == -1 || rc == -2) return -1;
   if (rc != CA_OK) return rc;  // b, tree, slices are arguments 3, 4, 5 in both calls
-  if (!work_bytes) return -7;
-  *work_bytes = align256(w) + ir_ws_bytes(n, nrhs > 0 ? nrhs : 1);
+  if (refine < CA_REFINE_CLASSIC || refine > CA_REFINE_AUTO) return -7;
+  if (!work_bytes) return -8;
+  if (refine == CA_REFINE_AUTO) {  // room for the fallback factorization with 7 exact digits
+    size_t w7 = 0;
+    if (ca_calu_mixed_workspace(n, n, b, tree, 7, 1, &w7) == CA_OK && w7 > w) w = w7;
+  }
+  *work_bytes = align256(w) + align256(ir_ws_bytes(n, nrhs > 0 ? nrhs : 1)) + align256(solve_ws_bytes(n)) +
+                (refine != CA_REFINE_CLASSIC ? gm_ws_bytes(n) : 0);
   return CA_OK;
 }
 
 int calu_gesv_mixed(int n, int nrhs, const double *A, int lda, int b, const ca_tree_t *tree, int slices,
-                    int exact, double *LU, int ldlu, int *ipiv, const double *B, int ldb, double *X, int ldx,
-                    void *work, size_t lwork, int max_iter, double tol, int *iters, double *berr,
-                    int *dev_info, cudaStream_t stream) {
+                    int exact, int refine, double *LU, int ldlu, int *ipiv, const double *B, int ldb, double *X,
+                    int ldx, void *work, size_t lwork, int max_iter, double tol, int *dev_iters,
+                    double *dev_berr, int *dev_info, cudaStream_t stream) {
   if (n < 0) return -1;
   if (nrhs < 0) return -2;
   if (n > 0 && !A) return -3;
@@ -526,67 +562,113 @@ int calu_gesv_mixed(int n, int nrhs, const double *A, int lda, int b, const ca_t
   if (check_tree(tree, b)) return -6;
   if (tree->op_depth != 0) return CA_ERR_UNSUPPORTED;
   if (slices < 1 || slices > 8) return -7;
-  if (n > 0 && !LU) return -9;
-  if (ldlu < (n > 1 ? n : 1)) return -10;
-  if (n > 0 && !ipiv) return -11;
-  if (n > 0 && nrhs > 0 && !B) return -12;
-  if (ldb < (n > 1 ? n : 1)) return -13;
-  if (n > 0 && nrhs > 0 && !X) return -14;
-  if (ldx < (n > 1 ? n : 1)) return -15;
-  if (max_iter < 0) return -18;
-  if (nrhs > kMaxRhsHost) return CA_ERR_UNSUPPORTED;
-  if (!dev_info) return -22;
+  if (refine < CA_REFINE_CLASSIC || refine > CA_REFINE_AUTO) return -9;
+  if (n > 0 && !LU) return -10;
+  if (ldlu < (n > 1 ? n : 1)) return -11;
+  if (n > 0 && !ipiv) return -12;
+  if (n > 0 && nrhs > 0 && !B) return -13;
+  if (ldb < (n > 1 ? n : 1)) return -14;
+  if (n > 0 && nrhs > 0 && !X) return -15;
+  if (ldx < (n > 1 ? n : 1)) return -16;
+  if (max_iter < 0) return -19;
+  if (!dev_info) return -23;
   size_t need = 0;
-  int rc = ca_gesv_mixed_workspace(n, nrhs, b, tree, slices, exact, &need);
+  int rc = ca_gesv_mixed_workspace(n, nrhs, b, tree, slices, exact, refine, &need);
+  if (rc == -7) return -9;
   if (rc != CA_OK) return rc;
   if (n > 0 && (!work || lwork < need)) return CA_ERR_WORKSPACE;
-  if (iters) *iters = 0;
-  if (berr) *berr = 0.0;
+  if (dev_iters && cudaMemsetAsync(dev_iters, 0, sizeof(int), stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if (dev_berr && cudaMemsetAsync(dev_berr, 0, sizeof(double), stream) != cudaSuccess) return CA_ERR_LAUNCH;
   if (n == 0) return cudaMemsetAsync(dev_info, 0, 2 * sizeof(int), stream) == cudaSuccess ? CA_OK : CA_ERR_LAUNCH;
-  size_t wf = 0;
+  size_t wf = 0, w7 = 0;
   ca_calu_mixed_workspace(n, n, b, tree, slices, exact, &wf);
+  const size_t wfact = wf;  // the first factorization's part
+  if (refine == CA_REFINE_AUTO && ca_calu_mixed_workspace(n, n, b, tree, 7, 1, &w7) == CA_OK && w7 > wf) wf = w7;
+  const int nr = nrhs > 0 ? nrhs : 1;
+  char *p = (char *)work + align256(wf);
   IrWs iw;
-  ir_ws_carve((char *)work + align256(wf), n, nrhs > 0 ? nrhs : 1, iw);
+  ir_ws_carve(p, n, nr, iw);
+  p += align256(ir_ws_bytes(n, nr));
+  SolveWs sw;
+  solve_ws_carve(p, n, sw);
+  p += align256(solve_ws_bytes(n));
+  GmWs gw{};
+  if (refine != CA_REFINE_CLASSIC) gm_ws_carve(p, n, gw);
+  int *status = dev_info + 1;  // given-up waits of the solves: CA_STATUS_SOLVE_TIMEOUT
+  const int sbit = CA_STATUS_SOLVE_TIMEOUT;
   // 1. LU <- A, reduced-precision factorization (FP64 panels and pivots)
   if (cudaMemcpy2DAsync(LU, (size_t)ldlu * 8, A, (size_t)lda * 8, (size_t)n * 8, n, cudaMemcpyDeviceToDevice,
                         stream) != cudaSuccess)
     return CA_ERR_LAUNCH;
-  rc = calu_factor_mixed(n, n, LU, ldlu, b, tree, slices, exact, ipiv, work, wf, dev_info, stream);
+  rc = calu_factor_mixed(n, n, LU, ldlu, b, tree, slices, exact, ipiv, work, wfact, dev_info, stream);
   if (rc != CA_OK) return rc;
   if (nrhs == 0) return CA_OK;
   // 2. X = (LU)^-1 B
   if (cudaMemcpy2DAsync(X, (size_t)ldx * 8, B, (size_t)ldb * 8, (size_t)n * 8, nrhs, cudaMemcpyDeviceToDevice,
                         stream) != cudaSuccess)
     return CA_ERR_LAUNCH;
-  if (calu_getrs(n, nrhs, LU, ldlu, ipiv, X, ldx, stream) != CA_OK) return CA_ERR_LAUNCH;
+  if (getrs_run(n, nrhs, LU, ldlu, ipiv, X, ldx, sw, status, sbit, nullptr, stream) != cudaSuccess)
+    return CA_ERR_LAUNCH;
   if (ir_anorm(n, A, lda, iw, stream) != cudaSuccess) return CA_ERR_LAUNCH;
-  // 3. refinement: R = B - A X in FP64, stop at berr <= tol, on stagnation or
-  //    after max_iter corrections; each step solves with the same factors
-  double prev = 0.0;
-  int stall = 0;
-  double host_berr[kMaxRhsHost];
-  const int nb = nrhs < kMaxRhsHost ? nrhs : kMaxRhsHost;
-  for (int it = 0;; ++it) {
-    if (ir_residual(n, nrhs, A, lda, X, ldx, B, ldb, iw, stream) != cudaSuccess) return CA_ERR_LAUNCH;
-    if (ir_berr(n, nrhs, X, ldx, B, ldb, iw, stream) != cudaSuccess) return CA_ERR_LAUNCH;
-    if (cudaMemcpyAsync(host_berr, iw.berr, (size_t)nb * 8, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-        cudaStreamSynchronize(stream) != cudaSuccess)
-      return CA_ERR_LAUNCH;
-    double be = 0.0;
-    for (int j = 0; j < nb; ++j) be = host_berr[j] > be ? host_berr[j] : be;
-    if (berr) *berr = be;
-    if (iters) *iters = it;
-    if (be <= tol || it >= max_iter) break;
-    if (it > 0 && be > 0.5 * prev) {
-      if (++stall >= 2) break;
-    } else {
-      stall = 0;
+  // 3. refinement phases, enqueued in full; each step: R = B - A X in FP64,
+  //    the stop test on the device, then the correction (one solve with the
+  //    factors, or GMRES preconditioned by them).  The kernels of steps after
+  //    a phase's stop do nothing.
+  auto run_phase = [&](const IrWs &w, bool gmres, int steps) -> int {
+    for (int it = 0;; ++it) {
+      if (ir_residual(n, nrhs, A, lda, X, ldx, B, ldb, w, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+      if (ir_berr(n, nrhs, X, ldx, B, ldb, w, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+      if (ir_decide(it, steps, tol, nrhs, w, dev_berr, dev_iters, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+      if (it >= steps) break;
+      if (!gmres) {
+        if (getrs_run(n, nrhs, LU, ldlu, ipiv, w.R, n, sw, status, sbit, &w.ctl->done, stream) != cudaSuccess)
+          return CA_ERR_LAUNCH;
+        if (ir_update(n, nrhs, w, X, ldx, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+      } else {
+        for (int j = 0; j < nrhs; ++j)
+          if (ir_gmres_correction(n, A, lda, LU, ldlu, ipiv, w, gw, j, X, ldx, sw, status, sbit, stream) !=
+              cudaSuccess)
+            return CA_ERR_LAUNCH;
+      }
     }
-    prev = be;
-    if (calu_getrs(n, nrhs, LU, ldlu, ipiv, iw.R, n, stream) != CA_OK) return CA_ERR_LAUNCH;
-    if (ir_update(n, nrhs, iw, X, ldx, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+    return CA_OK;
+  };
+  constexpr double kNever = 1e308;     // no slow-step rule: stop after two non-halving steps
+  constexpr double kSlowAuto = 0.1;    // AUTO: a classic step gaining less than 10x hands over to GMRES
+  constexpr int kAutoGmresSteps = 3;   // AUTO: GMRES corrections before the refactorization
+  constexpr int kAutoRefactorSteps = 3;
+  IrWs ph[kIrPhases];
+  for (int i = 0; i < kIrPhases; ++i) {
+    ph[i] = iw;
+    ph[i].ctl = iw.phase[i];
   }
-  return CA_OK;
+  if (refine != CA_REFINE_AUTO) {
+    if (ir_begin(ph[0], kNever, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+    return run_phase(ph[0], refine == CA_REFINE_GMRES, max_iter);
+  }
+  // AUTO: classic corrections while each gains 10x or more
+  if (ir_begin(ph[0], kSlowAuto, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if ((rc = run_phase(ph[0], false, max_iter)) != CA_OK) return rc;
+  // then GMRES corrections, if the classic phase stopped above tol
+  if (ir_begin_next(ph[0].ctl, ph[1], kNever, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if ((rc = run_phase(ph[1], true, kAutoGmresSteps)) != CA_OK) return rc;
+  // then, if GMRES stopped above tol too (the reduced-precision factors are
+  // too far from A), A factored again with 7 exact digits (FP64-accurate
+  // update), X from those factors, classic corrections
+  if (ir_begin_next(ph[1].ctl, ph[2], kNever, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  const int *noref = &ph[2].ctl->done;  // set: the phase does not run
+  int nl = 1;
+  if (lu_shape(n, n, b, tree, &nl) != CA_OK) return CA_ERR_UNSUPPORTED;
+  const int bw = b < kMaxB ? b : kMaxB;
+  char *tcws = (char *)work + align256(lu_panel_ws_bytes(nl, bw));
+  if (copy_matrix(n, n, A, lda, LU, ldlu, noref, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if ((rc = calu_run(n, n, LU, ldlu, b, tree, ipiv, work, nl, tcws, 7, 1, iw.info2, stream, noref)) != CA_OK)
+    return rc;
+  if (copy_matrix(n, nrhs, B, ldb, X, ldx, noref, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if (getrs_run(n, nrhs, LU, ldlu, ipiv, X, ldx, sw, status, sbit, noref, stream) != cudaSuccess)
+    return CA_ERR_LAUNCH;
+  if ((rc = run_phase(ph[2], false, kAutoRefactorSteps)) != CA_OK) return rc;
+  return ir_merge_info(ph[2], iw.info2, dev_info, stream) == cudaSuccess ? CA_OK : CA_ERR_LAUNCH;
 }
 
 int ca_caqr_mixed_workspace(int m, int n, int b, const ca_tree_t *tree, int slices, int exact,

@@ -16,6 +16,7 @@ namespace cg = cooperative_groups;
 constexpr int kMaxRounds = 64;
 constexpr int kMaxPanel = 256;  // widest panel any kernel here accepts
 
+// @region tree_plan
 // ---------------------------------------------------------------------------
 // Reduction tree plan (Sec. 3.1 / 3.2: leaves of the panel, then log Pr
 // pairwise reduction steps per level).  A round merges groups of consecutive
@@ -118,6 +119,7 @@ __host__ __device__ inline bool build_plan(int nleaves, const ca_tree_t &t, Plan
   }
   return cur == 1;
 }
+// @endregion tree_plan
 
 // ---------------------------------------------------------------------------
 // Argmax helpers: |x| compared through the bit pattern (an integer compare,
@@ -213,19 +215,25 @@ struct LuPanelWs {
 size_t lu_panel_ws_bytes(int nleaves_max, int b);
 void lu_panel_ws_carve(void *work, int nleaves_max, int b, LuPanelWs &ws);
 
+// skip (all launchers below that take it): when not null, the kernels do
+// nothing if *skip != 0 at the time they run -- a stage enqueued ahead whose
+// need is decided on the device (the refactorization fallback of the mixed
+// solve).
 cudaError_t tslu_panel(int mk, int bk, double *P, int lda, int leaf_rows, const Plan &plan,
                        const LuPanelWs &ws, int *ipiv_k, int ipiv_base, int *dev_info,
-                       cudaStream_t st);
+                       cudaStream_t st, const int *skip = nullptr);
 cudaError_t laswp_apply(int ncols, double *A, int lda, int row0, const LuPanelWs &ws, int bk,
-                        cudaStream_t st);
+                        cudaStream_t st, const int *skip = nullptr);
 cudaError_t lu_panel_finish(int mk, int bk, double *P, int lda, const LuPanelWs &ws,
-                            cudaStream_t st);
+                            cudaStream_t st, const int *skip = nullptr);
 cudaError_t trsm_u12(int bk, int nt, const double *L11, int ldl, double *A12, int lda,
-                     cudaStream_t st);
+                     cudaStream_t st, const int *skip = nullptr);
 
-// FP64 GEMM C -= A B (gemm_fp64.cu); A m x k, B k x n, column-major.
+// FP64 GEMM C -= A B (gemm_fp64.cu); A m x k, B k x n, column-major.  With
+// skip != null the kernel does nothing when *skip != 0 (a refinement loop
+// enqueued ahead whose stop test has fired).
 cudaError_t gemm_minus_f64(int m, int n, int k, const double *A, int lda, const double *B,
-                           int ldb, double *C, int ldc, cudaStream_t st);
+                           int ldb, double *C, int ldc, cudaStream_t st, const int *skip = nullptr);
 
 // QR panel and tree update (panel_qr.cu)
 struct QrPanelWs {
@@ -267,13 +275,15 @@ struct TcGemm {
   const int *coff;
   double sign;
   int S, exact;
+  const int *skip;      // as for the LU launchers (null: always run)
 };
 cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st);
 size_t tc_gemm_ws_bytes_batched(int m, int n, int k, int S, int nbatch);
 size_t tc_gemm_ws_bytes(int m, int n, int k, int S);
 bool tc_gemm_supported(int k, int S, int exact);
 cudaError_t gemm_minus_tc(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
-                          int ldc, int S, int exact, void *ws, int *status, cudaStream_t st);
+                          int ldc, int S, int exact, void *ws, int *status, cudaStream_t st,
+                          const int *skip = nullptr);
 
 // CAQR tree update on the tensor cores (update_tc.cu)
 size_t tree_tc_ws_bytes(int mk, int bk, int ncols, int leaf_rows, int nleaves, int S);
@@ -281,22 +291,93 @@ cudaError_t tree_apply_qt_tc(int mk, int bk, int b, const double *P, int lda, in
                              const double *Tp, double *C, int ldc, int ncols, const QrPanelWs &ws, void *tcws,
                              int S, int exact, int *status, cudaStream_t st);
 
-// iterative refinement pieces (ir.cu)
+// triangular solves (solve.cu).  The dependency-ordered solve keeps its
+// ready flags in caller memory (SolveWs, solve_ws_bytes(n) bytes): word 0
+// records a wait that gave up, the flags follow.  status / status_bit: where
+// a given-up wait is recorded (the workspace's word 0, or a dev_info word);
+// skip: as for gemm_minus_f64.
+struct SolveWs {
+  int *status;
+  int *flags;
+};
+size_t solve_ws_bytes(int n);
+void solve_ws_carve(void *w, int n, SolveWs &s);
+void solve_test_hook(long long wait_cycles, int withhold_blk);
+cudaError_t getrs_swap(int n, int nrhs, const int *ipiv, double *B, int ldb, cudaStream_t st,
+                       const int *skip = nullptr);
+cudaError_t trsm_left(bool lower, bool unit, int n, int nrhs, const double *T, int ldt, double *B, int ldb,
+                      const SolveWs &ws, int *status, int status_bit, const int *skip, cudaStream_t st);
+
+// iterative refinement pieces (ir.cu).  Every kernel of a refinement step
+// takes the loop's stop word (IrWs::ctl) and does nothing once it is set, so
+// the whole loop is enqueued without waiting on the host.
+struct IrCtl {
+  int done;       // the phase has stopped (or never started): its kernels do nothing
+  int ok;         // it stopped at berr <= tol
+  int ran;        // it started
+  int stall;      // consecutive steps whose backward error did not halve
+  int iters;      // corrections applied in this phase
+  int iter_base;  // corrections of the phases before it
+  double slow;    // a step reducing the error by less than 1/slow ends the phase
+  double prev;    // backward error of the previous step
+  double berr;    // latest backward error (largest over the right-hand sides)
+};
+constexpr int kIrPhases = 3;  // AUTO: classic, GMRES, refactorization with 7 exact digits
 struct IrWs {
   double *partial, *R, *rowsum, *anorm, *berr;
+  IrCtl *ctl;                // the control block of the phase these calls drive
+  IrCtl *phase[kIrPhases];   // all phases' control blocks
+  int *info2;                // dev_info of the refactorization
 };
 size_t ir_ws_bytes(int n, int nrhs);
 void ir_ws_carve(void *ws, int n, int nrhs, IrWs &w);
 cudaError_t ir_anorm(int n, const double *A, int lda, const IrWs &w, cudaStream_t st);
+cudaError_t ir_begin(const IrWs &w, double slow, cudaStream_t st);
+// a phase after `prev`: it runs only if prev did not reach tol
+cudaError_t ir_begin_next(const IrCtl *prev, const IrWs &w, double slow, cudaStream_t st);
+// dst = src (m x n) unless *skip
+cudaError_t copy_matrix(int m, int n, const double *src, int lds, double *dst, int ldd, const int *skip,
+                        cudaStream_t st);
+// after the refactorization phase (w.ctl): if it ran, its dev_info replaces
+// the first factorization's, plus the CA_STATUS_REFACTORED bit
+cudaError_t ir_merge_info(const IrWs &w, const int *info2, int *dev_info, cudaStream_t st);
 cudaError_t ir_residual(int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B,
                         int ldb, const IrWs &w, cudaStream_t st);
 cudaError_t ir_berr(int n, int nrhs, const double *X, int ldx, const double *B, int ldb, const IrWs &w,
                     cudaStream_t st);
+// the stop test of step `it` of the phase (device): berr <= tol, it ==
+// max_iter, a slow step, or two steps in a row that failed to halve the
+// backward error; writes the latest backward error and the corrections so far
+// to *berr_out / *iters_out when not null.
+cudaError_t ir_decide(int it, int max_iter, double tol, int nrhs, const IrWs &w, double *berr_out,
+                      int *iters_out, cudaStream_t st);
 cudaError_t ir_update(int n, int nrhs, const IrWs &w, double *X, int ldx, cudaStream_t st);
 
-// triangular solves (solve.cu)
-cudaError_t getrs_swap(int n, int nrhs, const int *ipiv, double *B, int ldb, cudaStream_t st);
-cudaError_t trsm_left(bool lower, bool unit, int n, int nrhs, const double *T, int ldt, double *B,
-                      int ldb, cudaStream_t st);
+// GMRES corrections (ir.cu): at most kGmMax Arnoldi steps per correction,
+// stopped when the preconditioned residual has dropped by kGmTol.
+constexpr int kGmMax = 20;
+constexpr double kGmTol = 1e-6;
+struct GmCtl {
+  int stop;    // Arnoldi finished (converged, breakdown, kGmMax) or not running
+  int active;  // this correction runs at all
+  int k;       // Arnoldi steps taken
+  int pad;
+  double beta, scale;
+  double h[kGmMax + 1];
+  double H[(kGmMax + 1) * kGmMax];
+  double cs[kGmMax], sn[kGmMax], g[kGmMax + 1], y[kGmMax];
+};
+struct GmWs {
+  double *V;        // n x (kGmMax + 1) Arnoldi vectors
+  double *w;        // n
+  double *partial;  // dot-product partial sums
+  double *mv;       // matrix-vector partial sums
+  GmCtl *ctl;
+};
+size_t gm_ws_bytes(int n);
+void gm_ws_carve(void *ws, int n, GmWs &g);
+cudaError_t ir_gmres_correction(int n, const double *A, int lda, const double *LU, int ldlu, const int *ipiv,
+                                const IrWs &w, const GmWs &g, int j, double *X, int ldx, const SolveWs &sw,
+                                int *status, int status_bit, cudaStream_t st);
 
 }  // namespace cagb

@@ -12,10 +12,11 @@ namespace cagb {
 template <int BM, int BN, int BK>
 __global__ void __launch_bounds__(256) gemm_minus_kernel(int m, int n, int k, const double *__restrict__ A,
                                                          int lda, const double *__restrict__ B, int ldb,
-                                                         double *__restrict__ C, int ldc) {
+                                                         double *__restrict__ C, int ldc, const int *skip) {
   constexpr int TM = BM / 16, TN = BN / 16;
   __shared__ double As[BK][BM];
   __shared__ double Bs[BK][BN];
+  if (skip && *skip) return;  // a refinement loop that has already stopped
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
@@ -92,16 +93,16 @@ __global__ void __launch_bounds__(256) gemm_minus_kernel(int m, int n, int k, co
 }
 
 cudaError_t gemm_minus_f64(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
-                           double *C, int ldc, cudaStream_t st) {
+                           double *C, int ldc, cudaStream_t st, const int *skip) {
   if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
   ProfScope ps(kClsGemm, st, 2.0 * m * (double)n * k);
   long long big = (long long)((m + 127) / 128) * ((n + 127) / 128);
   if (big >= 2 * 152) {
     dim3 grid((m + 127) / 128, (n + 127) / 128);
-    gemm_minus_kernel<128, 128, 16><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
+    gemm_minus_kernel<128, 128, 16><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, skip);
   } else {
     dim3 grid((m + 63) / 64, (n + 63) / 64);
-    gemm_minus_kernel<64, 64, 16><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc);
+    gemm_minus_kernel<64, 64, 16><<<grid, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, skip);
   }
   return cudaGetLastError();
 }

@@ -240,6 +240,7 @@ struct TcArgs {
   const int *coff;
   int sign;            // C -= sign * A B, sign = +1 or -1
   int *status;
+  const int *skip;     // nonzero: a stage enqueued ahead that is not needed, do nothing
 };
 
 // Operand tiles for one K block: S boxes of A digits (128 x bk) then S boxes
@@ -252,6 +253,7 @@ __global__ void __launch_bounds__(256, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
+  if (a.skip && *a.skip) return;  // before any barrier, copy or tensor-memory allocation
   uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const size_t stage_bytes = tc_stage_bytes(a.S, a.bn, a.bk);
   const int boxA = kTcBM * a.bk * 2;
@@ -438,7 +440,9 @@ __global__ void __launch_bounds__(256, 1)
 // Output: out[((b * S + s) * vpad + v) * kpad + k], exponent ex[b * vpad + v].
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) split_kernel(TcOperand o, int nbatch, int S, int vpad, int kpad, int exact,
-                                                    __nv_bfloat16 *__restrict__ out, int *__restrict__ ex) {
+                                                    __nv_bfloat16 *__restrict__ out, int *__restrict__ ex,
+                                                    const int *skip) {
+  if (skip && *skip) return;
   const int lane = threadIdx.x & 31;
   const int v = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int b = blockIdx.y;
@@ -621,11 +625,13 @@ cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st) {
   int *eb = (int *)p;
   {
     ProfScope ps(kClsSplit, st, 0.0);
-    split_kernel<<<dim3((mp + 7) / 8, g.nbatch), 256, 0, st>>>(g.A, g.nbatch, S, mp, kp, exact, sa, ea);
+    split_kernel<<<dim3((mp + 7) / 8, g.nbatch), 256, 0, st>>>(g.A, g.nbatch, S, mp, kp, exact, sa, ea,
+                                                                g.skip);
   }
   {
     ProfScope ps(kClsSplit, st, 0.0);
-    split_kernel<<<dim3((np + 7) / 8, g.nbatch), 256, 0, st>>>(g.B, g.nbatch, S, np, kp, exact, sb, eb);
+    split_kernel<<<dim3((np + 7) / 8, g.nbatch), 256, 0, st>>>(g.B, g.nbatch, S, np, kp, exact, sb, eb,
+                                                                g.skip);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -660,6 +666,7 @@ cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st) {
   a.coff = g.coff;
   a.sign = g.sign > 0 ? 1 : -1;
   a.status = status;
+  a.skip = g.skip;
   const size_t smem = cfg.smem;
   static std::atomic<unsigned long long> init{0};
   e = once_per_device(init, [] {
@@ -674,8 +681,9 @@ cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st) {
 }
 
 cudaError_t gemm_minus_tc(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C,
-                          int ldc, int S, int exact, void *ws, int *status, cudaStream_t st) {
+                          int ldc, int S, int exact, void *ws, int *status, cudaStream_t st, const int *skip) {
   TcGemm g = {};
+  g.skip = skip;
   g.A.X = A;  // rows of A: element (i, k) at A[i + k lda]
   g.A.sv = 1;
   g.A.sk = lda;

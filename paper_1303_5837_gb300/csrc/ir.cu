@@ -4,6 +4,9 @@
 // The residual is the one place refinement needs full FP64 (Sec. 5.1 measures
 // the normwise backward error ||b - A x|| / (||A|| ||x|| + ||b||), infinity
 // norms): one pass over A, FP64 DFMA, column blocks reduced in a fixed order.
+// The stop test runs on the device (ir_decide); every kernel of a later step
+// reads the stop word first and returns at once when it is set, so a caller
+// enqueues the whole loop without waiting for the GPU.
 #include "ca_internal.cuh"
 
 namespace cagb {
@@ -15,8 +18,9 @@ constexpr int kResMaxRhs = 16;
 // partial[cb][j][i] = sum_{c in block cb} A(i, c) X(c, j)
 __global__ void __launch_bounds__(kResRows) resid_partial_kernel(int n, int ncols, int nrhs, const double *A,
                                                                  int lda, const double *X, int ldx,
-                                                                 double *partial) {
+                                                                 double *partial, const int *skip) {
   __shared__ double xs[kResCols * 4];
+  if (*skip) return;
   const int i = blockIdx.x * kResRows + threadIdx.x;
   const int c0 = blockIdx.y * kResCols;
   const int nc = min(kResCols, ncols - c0);
@@ -46,7 +50,8 @@ __global__ void __launch_bounds__(kResRows) resid_partial_kernel(int n, int ncol
 
 // R = B - sum_cb partial[cb]
 __global__ void resid_reduce_kernel(int n, int nrhs, int ncb, const double *partial, const double *B, int ldb,
-                                    double *R, int ldr) {
+                                    double *R, int ldr, const int *skip) {
+  if (*skip) return;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n * nrhs) return;
   const int i = (int)(t % n), j = (int)(t / n);
@@ -86,7 +91,8 @@ __global__ void max_kernel(int n, const double *v, double *out) {
 
 // berr[j] = ||R_j||_inf / (||A||_inf ||X_j||_inf + ||B_j||_inf), one CTA per column
 __global__ void berr_kernel(int n, const double *R, int ldr, const double *X, int ldx, const double *B, int ldb,
-                            const double *anorm, double *berr) {
+                            const double *anorm, double *berr, const int *skip) {
+  if (*skip) return;
   const int j = blockIdx.x;
   double r = 0.0, x = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -103,17 +109,104 @@ __global__ void berr_kernel(int n, const double *R, int ldr, const double *X, in
   }
 }
 
-__global__ void axpy_kernel(int n, int nrhs, const double *D, int ldd, double *X, int ldx) {
+__global__ void axpy_kernel(int n, int nrhs, const double *D, int ldd, double *X, int ldx, const int *skip) {
+  if (*skip) return;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n * nrhs) return;
   const int i = (int)(t % n), j = (int)(t / n);
   X[i + (size_t)j * ldx] += D[i + (size_t)j * ldd];
 }
 
+// A refinement phase: a loop of steps (residual, stop test, correction)
+// with its own control block.  Phases run one after the other in stream
+// order; a phase starts only if the phases before it stopped above tol.
+
+// First phase: control cleared.  slow < 0.5 (AUTO's classic phase): a step
+// that reduces the backward error by less than 1/slow ends the phase (the
+// next one takes over); otherwise two steps in a row that fail to halve it
+// end the loop.
+__global__ void begin_kernel(IrCtl *ctl, double slow) {
+  ctl->done = 0;
+  ctl->ok = 0;
+  ctl->ran = 1;
+  ctl->stall = 0;
+  ctl->iters = 0;
+  ctl->iter_base = 0;
+  ctl->slow = slow;
+  ctl->prev = 0.0;
+  ctl->berr = 0.0;
+}
+
+// A later phase: runs (ran = 1) only if the previous one ran or was skipped
+// without reaching tol; counts corrections on from it.
+__global__ void begin_next_kernel(const IrCtl *prev, IrCtl *ctl, double slow) {
+  const int skip = prev->ok;
+  ctl->done = skip;
+  ctl->ok = skip;
+  ctl->ran = !skip;
+  ctl->stall = 0;
+  ctl->iters = 0;
+  ctl->iter_base = prev->iter_base + prev->iters;
+  ctl->slow = slow;
+  ctl->prev = 0.0;
+  ctl->berr = prev->berr;
+}
+
+__global__ void copy_matrix_kernel(int m, int n, const double *src, int lds, double *dst, int ldd,
+                                   const int *skip) {
+  if (skip && *skip) return;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)m * n) return;
+  const int i = (int)(t % m), j = (int)(t / m);
+  dst[i + (size_t)j * ldd] = src[i + (size_t)j * lds];
+}
+
+// after a refactorization phase that ran: its dev_info replaces the first
+// factorization's, with CA_STATUS_REFACTORED
+__global__ void merge_info_kernel(const IrCtl *c, const int *info2, int *dev_info) {
+  if (!c->ran) return;
+  dev_info[0] = info2[0];
+  dev_info[1] |= info2[1] | CA_STATUS_REFACTORED;
+}
+
+// The stop test of step `it` of a phase (one thread): the largest backward
+// error over the right-hand sides; the phase ends at <= tol (ok), at
+// it == max_iter, on a slow step (see begin_kernel) or on the second step in
+// a row that did not halve the error.
+__global__ void decide_kernel(int it, int max_iter, double tol, int nrhs, const double *berr, IrCtl *ctl,
+                              double *berr_out, int *iters_out) {
+  if (ctl->done) return;
+  double be = 0.0;
+  for (int j = 0; j < nrhs; ++j) be = berr[j] > be ? berr[j] : be;
+  if (be != be) be = berr[0];  // keep a NaN visible
+  for (int j = 0; j < nrhs; ++j)
+    if (berr[j] != berr[j]) be = berr[j];
+  ctl->berr = be;
+  ctl->iters = it;
+  if (berr_out) *berr_out = be;
+  if (iters_out) *iters_out = ctl->iter_base + it;
+  bool stop = false;
+  if (be <= tol) {
+    stop = true;
+    ctl->ok = 1;
+  } else if (it >= max_iter) {
+    stop = true;
+  } else if (it > 0 && be > ctl->slow * ctl->prev) {
+    stop = true;
+  } else if (it > 0 && be > 0.5 * ctl->prev) {
+    if (++ctl->stall >= 2) stop = true;
+  } else {
+    ctl->stall = 0;
+  }
+  if (!(be == be)) stop = true;  // NaN: nothing more to gain
+  ctl->prev = be;
+  ctl->done = stop ? 1 : 0;
+}
+
 size_t ir_ws_bytes(int n, int nrhs) {
   const int ncb = (n + kResCols - 1) / kResCols;
   return align256((size_t)ncb * nrhs * n * 8) + align256((size_t)n * nrhs * 8) + align256((size_t)n * 8) +
-         align256(8) + align256((size_t)nrhs * 8) + 256;
+         align256(8) + align256((size_t)nrhs * 8) + kIrPhases * align256(sizeof(IrCtl)) + align256(8) + 256;
 }
 
 void ir_ws_carve(void *ws, int n, int nrhs, IrWs &w) {
@@ -128,6 +221,13 @@ void ir_ws_carve(void *ws, int n, int nrhs, IrWs &w) {
   w.anorm = (double *)p;
   p += align256(8);
   w.berr = (double *)p;
+  p += align256((size_t)nrhs * 8);
+  for (int i = 0; i < kIrPhases; ++i) {
+    w.phase[i] = (IrCtl *)p;
+    p += align256(sizeof(IrCtl));
+  }
+  w.ctl = w.phase[0];
+  w.info2 = (int *)p;
 }
 
 cudaError_t ir_anorm(int n, const double *A, int lda, const IrWs &w, cudaStream_t st) {
@@ -140,6 +240,33 @@ cudaError_t ir_anorm(int n, const double *A, int lda, const IrWs &w, cudaStream_
   return cudaGetLastError();
 }
 
+cudaError_t ir_begin(const IrWs &w, double slow, cudaStream_t st) {
+  ProfScope ps(kClsRefine, st, 0.0);
+  begin_kernel<<<1, 1, 0, st>>>(w.ctl, slow);
+  return cudaGetLastError();
+}
+
+cudaError_t ir_begin_next(const IrCtl *prev, const IrWs &w, double slow, cudaStream_t st) {
+  ProfScope ps(kClsRefine, st, 0.0);
+  begin_next_kernel<<<1, 1, 0, st>>>(prev, w.ctl, slow);
+  return cudaGetLastError();
+}
+
+cudaError_t copy_matrix(int m, int n, const double *src, int lds, double *dst, int ldd, const int *skip,
+                        cudaStream_t st) {
+  const long long tot = (long long)m * n;
+  if (tot <= 0) return cudaSuccess;
+  ProfScope ps(kClsRefine, st, 0.0);
+  copy_matrix_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m, n, src, lds, dst, ldd, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t ir_merge_info(const IrWs &w, const int *info2, int *dev_info, cudaStream_t st) {
+  ProfScope ps(kClsRefine, st, 0.0);
+  merge_info_kernel<<<1, 1, 0, st>>>(w.ctl, info2, dev_info);  // w.ctl: the refactorization phase
+  return cudaGetLastError();
+}
+
 cudaError_t ir_residual(int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B,
                         int ldb, const IrWs &w, cudaStream_t st) {
   if (nrhs > kResMaxRhs) {
@@ -147,31 +274,279 @@ cudaError_t ir_residual(int n, int nrhs, const double *A, int lda, const double 
     cudaError_t e = cudaMemcpy2DAsync(w.R, (size_t)n * 8, B, (size_t)ldb * 8, (size_t)n * 8, nrhs,
                                       cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
-    return gemm_minus_f64(n, nrhs, n, A, lda, X, ldx, w.R, n, st);
+    return gemm_minus_f64(n, nrhs, n, A, lda, X, ldx, w.R, n, st, &w.ctl->done);
   }
   const int ncb = (n + kResCols - 1) / kResCols;
   {
     ProfScope ps(kClsRefine, st, 2.0 * n * (double)n * nrhs);
     resid_partial_kernel<<<dim3((n + kResRows - 1) / kResRows, ncb), kResRows, 0, st>>>(n, n, nrhs, A, lda, X,
-                                                                                         ldx, w.partial);
+                                                                                         ldx, w.partial,
+                                                                                         &w.ctl->done);
   }
   ProfScope ps(kClsRefine, st, 0.0);
   const long long tot = (long long)n * nrhs;
-  resid_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, nrhs, ncb, w.partial, B, ldb, w.R, n);
+  resid_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, nrhs, ncb, w.partial, B, ldb, w.R, n,
+                                                                      &w.ctl->done);
   return cudaGetLastError();
 }
 
 cudaError_t ir_berr(int n, int nrhs, const double *X, int ldx, const double *B, int ldb, const IrWs &w,
                     cudaStream_t st) {
   ProfScope ps(kClsRefine, st, 0.0);
-  berr_kernel<<<nrhs, 256, 0, st>>>(n, w.R, n, X, ldx, B, ldb, w.anorm, w.berr);
+  berr_kernel<<<nrhs, 256, 0, st>>>(n, w.R, n, X, ldx, B, ldb, w.anorm, w.berr, &w.ctl->done);
+  return cudaGetLastError();
+}
+
+cudaError_t ir_decide(int it, int max_iter, double tol, int nrhs, const IrWs &w, double *berr_out,
+                      int *iters_out, cudaStream_t st) {
+  ProfScope ps(kClsRefine, st, 0.0);
+  decide_kernel<<<1, 1, 0, st>>>(it, max_iter, tol, nrhs, w.berr, w.ctl, berr_out, iters_out);
   return cudaGetLastError();
 }
 
 cudaError_t ir_update(int n, int nrhs, const IrWs &w, double *X, int ldx, cudaStream_t st) {
   ProfScope ps(kClsRefine, st, (double)n * nrhs);
   const long long tot = (long long)n * nrhs;
-  axpy_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, nrhs, w.R, n, X, ldx);
+  axpy_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, nrhs, w.R, n, X, ldx, &w.ctl->done);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// GMRES on the preconditioned correction equation (M^-1 A) d = M^-1 r with
+// M = P^T L U the reduced-precision factors (GMRES-based iterative
+// refinement): x0 = 0, Arnoldi with classical Gram-Schmidt applied twice,
+// Givens rotations on the Hessenberg matrix, stop when the preconditioned
+// residual has dropped by kGmTol or after kGmMax steps; then d = V y and
+// x += d.  All in FP64.  The control block lives in device memory; every
+// kernel reads gm->stop (or gm->active) first, so the host enqueues kGmMax
+// Arnoldi steps and the ones after convergence do nothing.
+// ---------------------------------------------------------------------------
+constexpr int kGmRows = 256;  // rows per CTA of the dot-product kernels
+
+__global__ void gm_begin_kernel(const IrCtl *ctl, GmCtl *gm) {
+  gm->active = !ctl->done;
+  gm->stop = !gm->active;
+  gm->k = 0;
+  gm->beta = 0.0;
+}
+
+// dst = column j of R (the current residual)
+__global__ void gm_copy_kernel(int n, const double *src, double *dst, const GmCtl *gm) {
+  if (gm->stop) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i];
+}
+
+__device__ double block_sum(double v, double *red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+// partial[blk * (kGmMax + 1) + c] = sum over this CTA's rows of V(:, c) w,
+// c < ncols (the columns of V, or w itself when V == w and ncols == 1)
+__global__ void __launch_bounds__(kGmRows) gm_dots_kernel(int n, int ncols, const double *V, int ldv,
+                                                          const double *w, double *partial, const GmCtl *gm) {
+  __shared__ double red[kGmRows / 32];
+  if (gm->stop) return;
+  const int i = blockIdx.x * kGmRows + threadIdx.x;
+  const double wi = i < n ? w[i] : 0.0;
+  for (int c = 0; c < ncols; ++c) {
+    const double v = i < n ? V[i + (size_t)c * ldv] : 0.0;
+    const double s = block_sum(v * wi, red);
+    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * (kGmMax + 1) + c] = s;
+  }
+}
+
+// h[c] = sum_blk partial[blk][c] in a fixed order; accumulate: H(:, j) += h
+// (second Gram-Schmidt pass) or H(:, j) = h (first); norm: h is ||w||^2.
+__global__ void gm_finish_kernel(int nblk, int ncols, const double *partial, GmCtl *gm, int j, int pass) {
+  if (gm->stop) return;
+  const int c = threadIdx.x;
+  if (c >= ncols) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * (kGmMax + 1) + c];
+  gm->h[c] = s;
+  if (pass == 1) gm->H[c + j * (kGmMax + 1)] = s;
+  if (pass == 2) gm->H[c + j * (kGmMax + 1)] += s;
+}
+
+// w -= V(:, 0:ncols) h
+__global__ void gm_axpy_kernel(int n, int ncols, const double *V, int ldv, double *w, const GmCtl *gm) {
+  if (gm->stop) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = w[i];
+  for (int c = 0; c < ncols; ++c) s = fma(-V[i + (size_t)c * ldv], gm->h[c], s);
+  w[i] = s;
+}
+
+// beta = ||M^-1 r|| (from gm->h[0] = its square), g = beta e1; nothing to do
+// for a zero residual
+__global__ void gm_start_kernel(GmCtl *gm) {
+  if (gm->stop) return;
+  const double beta = sqrt(gm->h[0]);
+  gm->beta = beta;
+  for (int i = 0; i <= kGmMax; ++i) gm->g[i] = 0.0;
+  gm->g[0] = beta;
+  gm->scale = beta > 0.0 ? 1.0 / beta : 0.0;
+  if (!(beta > 0.0)) gm->stop = 1;
+}
+
+// Arnoldi step j done: H(j+1, j) = ||w|| (gm->h[0] = its square); the
+// earlier rotations are applied to H(:, j), a new one zeroes H(j+1, j), g is
+// rotated; converged when |g(j+1)| <= tol beta.
+__global__ void gm_givens_kernel(GmCtl *gm, int j, double tol) {
+  if (gm->stop) return;
+  double *H = gm->H + j * (kGmMax + 1);
+  const double hn = sqrt(gm->h[0]);
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i], b = H[i + 1];
+    H[i] = gm->cs[i] * a + gm->sn[i] * b;
+    H[i + 1] = -gm->sn[i] * a + gm->cs[i] * b;
+  }
+  const double a = H[j];
+  const double r = hypot(a, hn);
+  const double c = r > 0.0 ? a / r : 1.0, s = r > 0.0 ? hn / r : 0.0;
+  gm->cs[j] = c;
+  gm->sn[j] = s;
+  H[j] = r;
+  H[j + 1] = 0.0;
+  gm->g[j + 1] = -s * gm->g[j];
+  gm->g[j] = c * gm->g[j];
+  gm->k = j + 1;
+  gm->scale = hn > 0.0 ? 1.0 / hn : 0.0;
+  if (fabs(gm->g[j + 1]) <= tol * gm->beta || j + 1 >= kGmMax || !(hn > 0.0)) gm->stop = 1;
+}
+
+// dst = scale * src (the next Arnoldi vector, or the first one)
+__global__ void gm_scale_kernel(int n, const double *src, double *dst, const GmCtl *gm) {
+  if (gm->stop) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i] * gm->scale;
+}
+
+// y = R^-1 g over the k accepted steps (R: the rotated Hessenberg matrix)
+__global__ void gm_solve_kernel(GmCtl *gm) {
+  if (!gm->active) return;
+  const int k = gm->k;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = gm->g[i];
+    for (int c = i + 1; c < k; ++c) s -= gm->H[i + c * (kGmMax + 1)] * gm->y[c];
+    gm->y[i] = s / gm->H[i + i * (kGmMax + 1)];
+  }
+}
+
+// x += V(:, 0:k) y
+__global__ void gm_xupdate_kernel(int n, const double *V, int ldv, double *x, const GmCtl *gm) {
+  if (!gm->active) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int c = 0; c < gm->k; ++c) s = fma(V[i + (size_t)c * ldv], gm->y[c], s);
+  x[i] += s;
+}
+
+// w = A v (one thread per row, column blocks reduced in a fixed order)
+__global__ void gm_gemv_reduce_kernel(int n, int ncb, const double *partial, double *w, const GmCtl *gm) {
+  if (gm->stop) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int cb = 0; cb < ncb; ++cb) s += partial[(size_t)cb * n + i];
+  w[i] = s;
+}
+
+size_t gm_ws_bytes(int n) {
+  const int nblk = (n + kGmRows - 1) / kGmRows;
+  const int ncb = (n + kResCols - 1) / kResCols;
+  return align256((size_t)n * (kGmMax + 1) * 8) + align256((size_t)n * 8) +
+         align256((size_t)nblk * (kGmMax + 1) * 8) + align256((size_t)ncb * n * 8) + align256(sizeof(GmCtl)) +
+         256;
+}
+
+void gm_ws_carve(void *ws, int n, GmWs &g) {
+  const int nblk = (n + kGmRows - 1) / kGmRows;
+  const int ncb = (n + kResCols - 1) / kResCols;
+  char *p = (char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  g.V = (double *)p;
+  p += align256((size_t)n * (kGmMax + 1) * 8);
+  g.w = (double *)p;
+  p += align256((size_t)n * 8);
+  g.partial = (double *)p;
+  p += align256((size_t)nblk * (kGmMax + 1) * 8);
+  g.mv = (double *)p;
+  p += align256((size_t)ncb * n * 8);
+  g.ctl = (GmCtl *)p;
+}
+
+// The GMRES correction of right-hand side j: x(:, j) += d with
+// (M^-1 A) d = M^-1 r_j, M the factors in LU / ipiv.
+cudaError_t ir_gmres_correction(int n, const double *A, int lda, const double *LU, int ldlu, const int *ipiv,
+                                const IrWs &w, const GmWs &g, int j, double *X, int ldx, const SolveWs &sw,
+                                int *status, int status_bit, cudaStream_t st) {
+  const int *stop = &g.ctl->stop;
+  const int nb = (n + 255) / 256;
+  const int nblk = (n + kGmRows - 1) / kGmRows;
+  const int ncb = (n + kResCols - 1) / kResCols;
+  cudaError_t e;
+  auto prec_solve = [&](double *v) -> cudaError_t {  // v <- M^-1 v
+    cudaError_t e2 = getrs_swap(n, 1, ipiv, v, n, st, stop);
+    if (e2 != cudaSuccess) return e2;
+    if ((e2 = trsm_left(true, true, n, 1, LU, ldlu, v, n, sw, status, status_bit, stop, st)) != cudaSuccess)
+      return e2;
+    return trsm_left(false, false, n, 1, LU, ldlu, v, n, sw, status, status_bit, stop, st);
+  };
+  auto norm2 = [&](const double *v) -> cudaError_t {  // gm->h[0] = ||v||^2
+    gm_dots_kernel<<<nblk, kGmRows, 0, st>>>(n, 1, v, n, v, g.partial, g.ctl);
+    gm_finish_kernel<<<1, 32, 0, st>>>(nblk, 1, g.partial, g.ctl, 0, 0);
+    return cudaGetLastError();
+  };
+  {
+    ProfScope ps(kClsRefine, st, 0.0);
+    gm_begin_kernel<<<1, 1, 0, st>>>(w.ctl, g.ctl);
+    gm_copy_kernel<<<nb, 256, 0, st>>>(n, w.R + (size_t)j * n, g.V, g.ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if ((e = prec_solve(g.V)) != cudaSuccess) return e;
+  {
+    ProfScope ps(kClsRefine, st, 2.0 * n);
+    if ((e = norm2(g.V)) != cudaSuccess) return e;
+    gm_start_kernel<<<1, 1, 0, st>>>(g.ctl);
+    gm_scale_kernel<<<nb, 256, 0, st>>>(n, g.V, g.V, g.ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  for (int s = 0; s < kGmMax; ++s) {
+    double *vs = g.V + (size_t)s * n;
+    {  // w = A v_s
+      ProfScope ps(kClsRefine, st, 2.0 * n * (double)n);
+      resid_partial_kernel<<<dim3((n + kResRows - 1) / kResRows, ncb), kResRows, 0, st>>>(n, n, 1, A, lda, vs,
+                                                                                           n, g.mv, stop);
+      gm_gemv_reduce_kernel<<<nb, 256, 0, st>>>(n, ncb, g.mv, g.w, g.ctl);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = prec_solve(g.w)) != cudaSuccess) return e;  // w = M^-1 A v_s
+    {
+      ProfScope ps(kClsRefine, st, 8.0 * n * (s + 1) + 2.0 * n);
+      for (int pass = 1; pass <= 2; ++pass) {  // classical Gram-Schmidt, twice
+        gm_dots_kernel<<<nblk, kGmRows, 0, st>>>(n, s + 1, g.V, n, g.w, g.partial, g.ctl);
+        gm_finish_kernel<<<1, 32, 0, st>>>(nblk, s + 1, g.partial, g.ctl, s, pass);
+        gm_axpy_kernel<<<nb, 256, 0, st>>>(n, s + 1, g.V, n, g.w, g.ctl);
+      }
+      if ((e = norm2(g.w)) != cudaSuccess) return e;
+      gm_givens_kernel<<<1, 1, 0, st>>>(g.ctl, s, kGmTol);
+      gm_scale_kernel<<<nb, 256, 0, st>>>(n, g.w, g.V + (size_t)(s + 1) * n, g.ctl);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  ProfScope ps(kClsRefine, st, 2.0 * n * kGmMax);
+  gm_solve_kernel<<<1, 1, 0, st>>>(g.ctl);
+  gm_xupdate_kernel<<<nb, 256, 0, st>>>(n, g.V, n, X + (size_t)j * ldx, g.ctl);
   return cudaGetLastError();
 }
 

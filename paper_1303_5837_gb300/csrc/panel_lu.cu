@@ -38,6 +38,7 @@ struct TsluNodeArgs {
   int *perm_src, *perm_dst, *perm_cnt;
   int *ipiv_k;      // ipiv + kb
   int ipiv_base;    // kb
+  const int *skip;  // nonzero: a stage enqueued ahead that is not needed, do nothing
   int *dev_info;    // [0] info, [1] status
 };
 
@@ -94,6 +95,7 @@ __device__ __forceinline__ void node_sync(cg::cluster_group &cl, int G) {
 }
 
 __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs a) {
+  if (a.skip && *a.skip) return;  // every CTA of the cluster reads the same word
   cg::cluster_group cl = cg::this_cluster();
   const int G = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -324,7 +326,8 @@ constexpr int kSwapMax = 2 * kMaxPanel;
 
 __global__ void __launch_bounds__(256) laswp_kernel(int ncols, double *A, int lda, int row0,
                                                     const int *src, const int *dst,
-                                                    const int *cnt) {
+                                                    const int *cnt, const int *skip) {
+  if (skip && *skip) return;
   const int lane = threadIdx.x & 31;
   const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (col >= ncols) return;
@@ -354,8 +357,9 @@ constexpr int kFinThreads = 256;
 
 __global__ void __launch_bounds__(kFinThreads) lu_finish_kernel(int mk, int bk, double *P, int lda,
                                                                 const double *lu11, int ldl,
-                                                                int rt) {
+                                                                int rt, const int *skip) {
   extern __shared__ __align__(16) double fsm[];
+  if (skip && *skip) return;
   double *U = fsm;                       // bk x bk (ld bk), upper part used
   double *rd = U + (size_t)bk * bk;      // reciprocals of U's diagonal
   double *T = rd + bk;                   // rt x bk tile (ld rt)
@@ -394,8 +398,9 @@ __global__ void __launch_bounds__(kFinThreads) lu_finish_kernel(int mk, int bk, 
 // U12 = L11^-1 A12 (unit lower), one CTA per tile of ct columns.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) trsm_u12_kernel(int bk, int nt, const double *L, int ldl,
-                                                       double *A, int lda, int ct) {
+                                                       double *A, int lda, int ct, const int *skip) {
   extern __shared__ __align__(16) double usm[];
+  if (skip && *skip) return;
   double *Ls = usm;                   // bk x bk, ld bk
   double *T = Ls + (size_t)bk * bk;   // bk x ct, ld bk
   const int tid = threadIdx.x;
@@ -494,8 +499,9 @@ static cudaError_t launch_tslu_node(const TsluNodeArgs &args, int nodes, int G, 
 
 cudaError_t tslu_panel(int mk, int bk, double *P, int lda, int leaf_rows, const Plan &plan,
                        const LuPanelWs &ws, int *ipiv_k, int ipiv_base, int *dev_info,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int *skip) {
   TsluNodeArgs a = {};
+  a.skip = skip;
   a.P = P;
   a.lda = lda;
   a.mk = mk;
@@ -545,17 +551,17 @@ cudaError_t tslu_panel(int mk, int bk, double *P, int lda, int leaf_rows, const 
 }
 
 cudaError_t laswp_apply(int ncols, double *A, int lda, int row0, const LuPanelWs &ws, int bk,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int *skip) {
   (void)bk;
   if (ncols <= 0) return cudaSuccess;
   ProfScope ps(kClsLaswp, st, 0.0);
   laswp_kernel<<<(ncols + 7) / 8, 256, 0, st>>>(ncols, A, lda, row0, ws.perm_src, ws.perm_dst,
-                                                ws.perm_cnt);
+                                                ws.perm_cnt, skip);
   return cudaGetLastError();
 }
 
 cudaError_t lu_panel_finish(int mk, int bk, double *P, int lda, const LuPanelWs &ws,
-                            cudaStream_t st) {
+                            cudaStream_t st, const int *skip) {
   static std::atomic<unsigned long long> init{0};
   cudaError_t e = once_per_device(init, [] {
     return cudaFuncSetAttribute(lu_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -567,12 +573,12 @@ cudaError_t lu_panel_finish(int mk, int bk, double *P, int lda, const LuPanelWs 
   int below = mk - bk;
   int nblk = 1 + (below > 0 ? (below + rt - 1) / rt : 0);
   ProfScope ps(kClsLuFinish, st, (double)(below > 0 ? below : 0) * bk * bk);
-  lu_finish_kernel<<<nblk, kFinThreads, smem, st>>>(mk, bk, P, lda, ws.lu11, bk, rt);
+  lu_finish_kernel<<<nblk, kFinThreads, smem, st>>>(mk, bk, P, lda, ws.lu11, bk, rt, skip);
   return cudaGetLastError();
 }
 
 cudaError_t trsm_u12(int bk, int nt, const double *L11, int ldl, double *A12, int lda,
-                     cudaStream_t st) {
+                     cudaStream_t st, const int *skip) {
   static std::atomic<unsigned long long> init{0};
   cudaError_t e = once_per_device(init, [] {
     return cudaFuncSetAttribute(trsm_u12_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -583,7 +589,7 @@ cudaError_t trsm_u12(int bk, int nt, const double *L11, int ldl, double *A12, in
   if (ct > 128) ct = 128;
   size_t smem = ((size_t)bk * bk + (size_t)bk * ct) * 8;
   ProfScope ps(kClsTrsmU12, st, (double)bk * bk * nt);
-  trsm_u12_kernel<<<(nt + ct - 1) / ct, 256, smem, st>>>(bk, nt, L11, ldl, A12, lda, ct);
+  trsm_u12_kernel<<<(nt + ct - 1) / ct, 256, smem, st>>>(bk, nt, L11, ldl, A12, lda, ct, skip);
   return cudaGetLastError();
 }
 

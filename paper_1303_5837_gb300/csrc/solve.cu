@@ -6,7 +6,7 @@
 // one CTA per diagonal block, ordered by ready flags; otherwise the diagonal
 // block is solved by one CTA in shared memory and the rows below (or above)
 // are updated with the FP64 GEMM, one launch per block.
-#include <mutex>
+#include <atomic>
 
 #include "ca_internal.cuh"
 #include "device_once.cuh"
@@ -18,8 +18,9 @@ constexpr int kTb = 128;
 // Row interchanges of LAPACK laswp (forward), one CTA per right-hand side;
 // the column is staged in shared memory when it fits.
 __global__ void __launch_bounds__(32) swap_rows_kernel(int n, const int *ipiv, double *B, int ldb,
-                                                       int staged) {
+                                                       int staged, const int *skip) {
   extern __shared__ __align__(16) double col[];
+  if (skip && *skip) return;
   double *b = B + (size_t)blockIdx.x * ldb;
   const int lane = threadIdx.x;
   if (staged) {
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(32) swap_rows_kernel(int n, const int *ipiv, d
   }
 }
 
-cudaError_t getrs_swap(int n, int nrhs, const int *ipiv, double *B, int ldb, cudaStream_t st) {
+cudaError_t getrs_swap(int n, int nrhs, const int *ipiv, double *B, int ldb, cudaStream_t st, const int *skip) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   static std::atomic<unsigned long long> init{0};
   cudaError_t e = once_per_device(init, [] {
@@ -57,15 +58,17 @@ cudaError_t getrs_swap(int n, int nrhs, const int *ipiv, double *B, int ldb, cud
   if (e != cudaSuccess) return e;
   int staged = ((size_t)n * 8 <= 200 * 1024) ? 1 : 0;
   ProfScope ps(kClsSolve, st, 0.0);
-  swap_rows_kernel<<<nrhs, 32, staged ? (size_t)n * 8 : 0, st>>>(n, ipiv, B, ldb, staged);
+  swap_rows_kernel<<<nrhs, 32, staged ? (size_t)n * 8 : 0, st>>>(n, ipiv, B, ldb, staged, skip);
   return cudaGetLastError();
 }
 
 // Solve the nb x nb diagonal block T11 X = B1 in place (nb <= kTb) for all
 // right-hand sides, one CTA per tile of 32 right-hand sides.
 __global__ void __launch_bounds__(256) trsm_diag_kernel(int nb, int nrhs, const double *T, int ldt,
-                                                        double *B, int ldb, int lower, int unit) {
+                                                        double *B, int ldb, int lower, int unit,
+                                                        const int *skip) {
   extern __shared__ __align__(16) double tsm[];
+  if (skip && *skip) return;
   double(*Ts)[kTb + 1] = reinterpret_cast<double(*)[kTb + 1]>(tsm);
   double(*Xs)[33] = reinterpret_cast<double(*)[33]>(tsm + kTb * (kTb + 1));
   const int tid = threadIdx.x;
@@ -114,15 +117,22 @@ __global__ void __launch_bounds__(256) trsm_diag_kernel(int nb, int nrhs, const 
 //   The chain of dependent steps is one GEMV of a 128 x 128 block and one
 //   small triangular multiply per block; the earlier GEMVs of a CTA overlap
 //   with the chain.  The cooperative launch makes every CTA resident, as the
-//   waits require; every wait is bounded (about 2 s of SM clock), after
-//   which the CTA records the timeout in the flag word after the last block
-//   and leaves.
+//   waits require; every wait is bounded (wait_limit cycles of SM clock,
+//   about 2 s by default), after which the CTA ORs status_bit into *status
+//   and leaves.  The flags live in the caller's workspace (SolveWs) and are
+//   cleared before every launch.  withhold_blk >= 0 is a test hook: that
+//   block never publishes its flag, so every wait on it runs out.
 // Needs one CTA per diagonal block: n <= SMs * kTb.
 // ---------------------------------------------------------------------------
 constexpr int kCoopMaxRhs = 16;
 constexpr int kLdI = kTb + 1;
-constexpr int kMaxFlagBlocks = 1024;            // flag words per stream (covers any SM count here)
+constexpr int kMaxFlagBlocks = 1024;            // flag words of a solve workspace (covers any SM count here)
 constexpr long long kSolveWaitLimit = 4000000000ll;
+
+// Test hook state (host): the wait limit and the withheld block of the next
+// dependency-ordered solves (kSolveWaitLimit and -1 unless a test set them).
+static std::atomic<long long> g_wait_limit{kSolveWaitLimit};
+static std::atomic<int> g_withhold{-1};
 
 __device__ __forceinline__ int ld_acquire_gpu(const int *p) {
   int v;
@@ -134,8 +144,17 @@ __device__ __forceinline__ void st_release_gpu(int *p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+struct FlagArgs {
+  int *flags;            // nblk ready flags, zero at launch
+  int *status;           // gets status_bit when a wait gives up
+  int status_bit;
+  const int *skip;       // refinement: nonzero = the loop has stopped, do nothing
+  long long wait_limit;  // cycles
+  int withhold_blk;      // test hook (-1: off)
+};
+
 __global__ void __launch_bounds__(256, 1) trsv_flag_kernel(int n, int nrhs, const double *T, int ldt, double *B,
-                                                           int ldb, int lower, int unit, int *flags) {
+                                                           int ldb, int lower, int unit, FlagArgs fa) {
   extern __shared__ __align__(16) double csm[];
   double *Ti = csm;                          // the inverted diagonal block, ld kLdI
   double *tmp = Ti + kTb * kLdI;             // kTb column buffer
@@ -143,6 +162,8 @@ __global__ void __launch_bounds__(256, 1) trsv_flag_kernel(int n, int nrhs, cons
   double *xj = sb + kTb * kCoopMaxRhs;       // kTb x nrhs: a published solution block
   double *part = xj + kTb * kCoopMaxRhs;     // 2 x kTb x nrhs: half-row partial sums
   __shared__ int abort_flag;
+  if (fa.skip && *fa.skip) return;
+  int *flags = fa.flags;
   const int tid = threadIdx.x;
   const int nblk = (n + kTb - 1) / kTb;
   const int blk = blockIdx.x;
@@ -208,9 +229,9 @@ __global__ void __launch_bounds__(256, 1) trsv_flag_kernel(int n, int nrhs, cons
       const long long tstart = clock64();
       int ok = 1;
       while (ld_acquire_gpu(flags + j) == 0) {
-        if (clock64() - tstart > kSolveWaitLimit) {
+        if (clock64() - tstart > fa.wait_limit) {
           ok = 0;
-          atomicOr(flags + kMaxFlagBlocks, 1);  // the timeout word
+          atomicOr(fa.status, fa.status_bit);  // the timeout record
           break;
         }
       }
@@ -260,64 +281,25 @@ __global__ void __launch_bounds__(256, 1) trsv_flag_kernel(int n, int nrhs, cons
   }
   __threadfence();
   __syncthreads();
-  if (tid == 0) st_release_gpu(flags + blk, 1);
+  if (tid == 0 && blk != fa.withhold_blk) st_release_gpu(flags + blk, 1);
 }
 
-// Flag words of the dependency-driven solve: one array per (device, caller
-// stream), created on first use (make the first solve on a stream before
-// capturing it in a graph) and kept until the process exits.
-struct FlagPool {
-  struct Entry {
-    int dev;
-    cudaStream_t st;
-    int *flags;
-  };
-  std::mutex mu;
-  Entry pool[64];
-  int used = 0;
-};
-
-static FlagPool &flag_pool() {
-  static FlagPool p;
-  return p;
+// Solve workspace (caller memory): word 0 is the timeout record of the
+// library's solves that use it, the ready flags start at word 32.
+size_t solve_ws_bytes(int n) {
+  const int nblk = (n + kTb - 1) / kTb;
+  return align256((size_t)(32 + (nblk < 1 ? 1 : nblk)) * sizeof(int));
 }
 
-// The flag array of (current device, st), or nullptr if none exists and
-// `create` is false (or it cannot be created).
-static int *solve_flags_lookup(cudaStream_t st, bool create) {
-  FlagPool &fp = flag_pool();
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-  std::lock_guard<std::mutex> g(fp.mu);
-  for (int i = 0; i < fp.used; ++i)
-    if (fp.pool[i].dev == dev && fp.pool[i].st == st) return fp.pool[i].flags;
-  if (!create || fp.used == 64) return nullptr;
-  int *f = nullptr;
-  if (cudaMalloc(&f, (kMaxFlagBlocks + 1) * sizeof(int)) != cudaSuccess) return nullptr;
-  if (cudaMemset(f, 0, (kMaxFlagBlocks + 1) * sizeof(int)) != cudaSuccess) return nullptr;
-  fp.pool[fp.used] = {dev, st, f};
-  return fp.pool[fp.used++].flags;
+void solve_ws_carve(void *w, int n, SolveWs &s) {
+  (void)n;
+  s.status = (int *)w;
+  s.flags = (int *)w + 32;
 }
 
-static int *solve_flags_for(cudaStream_t st) { return solve_flags_lookup(st, true); }
-
-// Whether a flag wait of a solve on `st` gave up since the last call: waits
-// for the stream, reads the timeout word and clears it.
-cudaError_t solve_timeout_read(cudaStream_t st, int *timed_out) {
-  *timed_out = 0;
-  int *flags = solve_flags_lookup(st, false);
-  if (!flags) return cudaSuccess;  // no dependency-ordered solve ran on st
-  cudaError_t e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return e;
-  int word = 0;
-  if ((e = cudaMemcpy(&word, flags + kMaxFlagBlocks, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
-    return e;
-  if (word != 0) {  // cleared in the stream's order, before its later solves
-    if ((e = cudaMemsetAsync(flags + kMaxFlagBlocks, 0, sizeof(int), st)) != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-  }
-  *timed_out = word != 0;
-  return cudaSuccess;
+void solve_test_hook(long long wait_cycles, int withhold_blk) {
+  g_wait_limit.store(wait_cycles > 0 ? wait_cycles : kSolveWaitLimit);
+  g_withhold.store(withhold_blk);
 }
 
 // one CTA per SM, one diagonal block per CTA
@@ -327,46 +309,37 @@ static int coop_max_n() {
   return (sms < kMaxFlagBlocks ? sms : kMaxFlagBlocks) * kTb;
 }
 
-// 0: launched; 1: not available here (use the per-block path); <0 error
-static int trsm_left_flags(bool lower, bool unit, int n, int nrhs, const double *T, int ldt, double *B, int ldb,
-                           cudaStream_t st, cudaError_t *err) {
+static cudaError_t trsm_left_flags(bool lower, bool unit, int n, int nrhs, const double *T, int ldt, double *B,
+                                   int ldb, const SolveWs &ws, int *status, int status_bit, const int *skip,
+                                   cudaStream_t st) {
   static std::atomic<unsigned long long> init{0};
   const size_t smem = ((size_t)kTb * kLdI + kTb + 4 * (size_t)kTb * kCoopMaxRhs) * 8;
   cudaError_t e = once_per_device(init, [smem] {
     return cudaFuncSetAttribute(trsv_flag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  if (e != cudaSuccess) {
-    *err = e;
-    return -1;
-  }
-  int *flags = solve_flags_for(st);
-  if (!flags) return 1;
+  if (e != cudaSuccess) return e;
   const int nblk = (n + kTb - 1) / kTb;
-  e = cudaMemsetAsync(flags, 0, (size_t)nblk * sizeof(int), st);
-  if (e != cudaSuccess) {
-    *err = e;
-    return -1;
-  }
+  e = cudaMemsetAsync(ws.flags, 0, (size_t)nblk * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  FlagArgs fa;
+  fa.flags = ws.flags;
+  fa.status = status;
+  fa.status_bit = status_bit;
+  fa.skip = skip;
+  fa.wait_limit = g_wait_limit.load();
+  fa.withhold_blk = g_withhold.load();
+  if (fa.withhold_blk >= 0) fa.withhold_blk = lower ? 0 : nblk - 1;  // the block nothing else precedes
   int lo = lower ? 1 : 0, un = unit ? 1 : 0;
-  void *args[] = {&n, &nrhs, (void *)&T, &ldt, &B, &ldb, &lo, &un, &flags};
+  void *args[] = {&n, &nrhs, (void *)&T, &ldt, &B, &ldb, &lo, &un, &fa};
   ProfScope ps(kClsSolve, st, (double)n * n * nrhs);
-  e = cudaLaunchCooperativeKernel((void *)trsv_flag_kernel, dim3(nblk), dim3(256), args, smem, st);
-  if (e != cudaSuccess) {
-    *err = e;
-    return -1;
-  }
-  return 0;
+  return cudaLaunchCooperativeKernel((void *)trsv_flag_kernel, dim3(nblk), dim3(256), args, smem, st);
 }
 
-cudaError_t trsm_left(bool lower, bool unit, int n, int nrhs, const double *T, int ldt, double *B,
-                      int ldb, cudaStream_t st) {
+cudaError_t trsm_left(bool lower, bool unit, int n, int nrhs, const double *T, int ldt, double *B, int ldb,
+                      const SolveWs &ws, int *status, int status_bit, const int *skip, cudaStream_t st) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
-  if (nrhs <= kCoopMaxRhs && n > kTb && n <= coop_max_n()) {
-    cudaError_t err = cudaSuccess;
-    const int rc = trsm_left_flags(lower, unit, n, nrhs, T, ldt, B, ldb, st, &err);
-    if (rc == 0) return cudaSuccess;
-    if (rc < 0) return err;
-  }
+  if (nrhs <= kCoopMaxRhs && n > kTb && n <= coop_max_n())
+    return trsm_left_flags(lower, unit, n, nrhs, T, ldt, B, ldb, ws, status, status_bit, skip, st);
   const size_t smem = ((size_t)kTb * (kTb + 1) + (size_t)kTb * 33) * 8;
   static std::atomic<unsigned long long> init{0};
   cudaError_t e = once_per_device(init, [smem] {
@@ -382,16 +355,16 @@ cudaError_t trsm_left(bool lower, bool unit, int n, int nrhs, const double *T, i
     {
       ProfScope ps(kClsSolve, st, (double)nb * nb * nrhs);
       trsm_diag_kernel<<<g, 256, smem, st>>>(nb, nrhs, T + r0 + (size_t)r0 * ldt, ldt, B + r0, ldb,
-                                          lower ? 1 : 0, unit ? 1 : 0);
+                                             lower ? 1 : 0, unit ? 1 : 0, skip);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (lower) {
       const int rest = n - r0 - nb;
       e = gemm_minus_f64(rest, nrhs, nb, T + (r0 + nb) + (size_t)r0 * ldt, ldt, B + r0, ldb,
-                         B + r0 + nb, ldb, st);
+                         B + r0 + nb, ldb, st, skip);
     } else {
-      e = gemm_minus_f64(r0, nrhs, nb, T + (size_t)r0 * ldt, ldt, B + r0, ldb, B, ldb, st);
+      e = gemm_minus_f64(r0, nrhs, nb, T + (size_t)r0 * ldt, ldt, B + r0, ldb, B, ldb, st, skip);
     }
     if (e != cudaSuccess) return e;
   }

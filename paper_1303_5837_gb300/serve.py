@@ -39,6 +39,8 @@ class Request:
     X: np.ndarray | None = None
     t_done: float = 0.0
     error: str = ""
+    berr: float = 0.0           # mixed LU: backward error reached by refinement
+    gpu_ms: tuple = ()          # (start, end) on the device, ms after the server's reference event
     done: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -51,9 +53,10 @@ def footprint(kind: str, m: int, n: int, nrhs: int, b: int, tree, form: str = "f
     mats = 8 * (m * n + 2 * m * nrhs)
     if kind == LU:
         if form == "mixed":
-            w = B.ca_gesv_mixed_workspace(n, nrhs, b, tree, 4, True)
+            w = B.ca_gesv_mixed_workspace(n, nrhs, b, tree, 4, True, "auto")
             return mats + 8 * n * n + w + 4 * n + 4096
-        return mats + B.ca_calu_workspace(m, n, b, tree) + 4 * n + 4096
+        w = B.ca_calu_workspace(m, n, b, tree) + B.ca_getrs_workspace(n, nrhs)
+        return mats + w + 4 * n + 4096
     if form == "mixed":
         q, w = B.ca_caqr_mixed_workspace(m, n, b, tree, 7, True)
     else:
@@ -79,6 +82,8 @@ class SolveServer:
         self._pending: queue.Queue = queue.Queue()
         self._cv = threading.Condition()
         self._used = 0
+        self._running = 0
+        self.max_running = 0
         self._free_slots = list(range(slots))
         self._work = [queue.Queue() for _ in range(slots)]
         self.max_used = 0
@@ -163,7 +168,23 @@ class SolveServer:
         return {"completed": len(lat), "rejected": len(self.rejected),
                 "cancelled": len(self.cancelled), "p50_s": pct(0.50),
                 "p99_s": pct(0.99), "solves_per_s": len(lat) / span if span > 0 else float("inf"),
-                "max_hbm_in_use": self.max_used, "budget": self.budget}
+                "max_hbm_in_use": self.max_used, "budget": self.budget,
+                "max_running": self.max_running, "max_on_device": self.max_on_device()}
+
+    def max_on_device(self) -> int:
+        """Most requests whose device intervals (CUDA events on their streams)
+        overlapped at one instant: > 1 means their kernels ran concurrently."""
+        ev = []
+        for r in self.completed:
+            if r.gpu_ms:
+                ev.append((r.gpu_ms[0], 1))
+                ev.append((r.gpu_ms[1], -1))
+        ev.sort(key=lambda e: (e[0], e[1]))
+        cur = best = 0
+        for _, d in ev:
+            cur += d
+            best = max(best, cur)
+        return best
 
     # ---- scheduler: admission by HBM footprint, arrival order ---------------
     def _schedule(self):
@@ -191,12 +212,15 @@ class SolveServer:
                 slot = self._free_slots.pop(0)
                 self._used += r.footprint
                 self.max_used = max(self.max_used, self._used)
+                self._running += 1
+                self.max_running = max(self.max_running, self._running)
                 r.status = "running"
             self._work[slot].put(r)
 
     def _release(self, slot: int, r: Request):
         with self._cv:
             self._used -= r.footprint
+            self._running -= 1
             self._free_slots.append(slot)
             self._cv.notify_all()
 
@@ -226,6 +250,12 @@ class SolveServer:
             return None
         import torch
         torch.cuda.set_device(self.device)
+        with self._cv:
+            if not hasattr(self, "_ref_event"):
+                # reference instant of the device intervals (recorded once, before any request)
+                self._ref_event = torch.cuda.Event(enable_timing=True)
+                self._ref_event.record(torch.cuda.current_stream(self.device))
+                self._ref_event.synchronize()
         return torch.cuda.Stream(device=self.device)
 
     def _run_on_gpu(self, r: Request, stream):
@@ -234,26 +264,55 @@ class SolveServer:
         m, n = r.A.shape
         nrhs = r.B.shape[1]
         tree = self.tree()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        berr = None
         with torch.cuda.stream(stream):
+            t0.record(stream)
             A = torch.from_numpy(np.ascontiguousarray(r.A.T)).to(dev, non_blocking=True).t()
             Bm = torch.from_numpy(np.ascontiguousarray(r.B.T)).to(dev, non_blocking=True).t()
+            swork = None
             if r.kind == LU and self.form == "mixed":
-                X, it, be, info = B.calu_gesv_mixed(A, Bm, self.b, tree, slices=4, exact=True, tol=1e-14,
-                                                     stream=stream)
+                X, it, berr, info = B.calu_gesv_mixed(A, Bm, self.b, tree, slices=4, exact=True, tol=1e-14,
+                                                      refine="auto", stream=stream)
             elif r.kind == LU:
                 ipiv, info = B.calu_factor(A, self.b, tree, stream=stream)
-                B.calu_getrs(A, ipiv, Bm, stream=stream)
+                swork = B._buf(B.ca_getrs_workspace(n, nrhs), dev)
+                B.calu_getrs(A, ipiv, Bm, work=swork, stream=stream)
                 X = Bm
             else:
                 if self.form == "mixed":
                     qtree, info = B.caqr_factor_mixed(A, self.b, tree, slices=7, exact=True, stream=stream)
                 else:
                     qtree, info = B.caqr_factor(A, self.b, tree, stream=stream)
-                B.caqr_geqrs(A, self.b, tree, qtree, Bm, stream=stream)
+                swork = B._buf(B.ca_geqrs_workspace(m, n, nrhs, self.b, tree), dev)
+                B.caqr_geqrs(A, self.b, tree, qtree, Bm, work=swork, stream=stream)
                 X = Bm[:n]
             out = X.cpu()  # waits for this request's stream only
+            t1.record(stream)
             stream.synchronize()
+        r.gpu_ms = (self._ref_event.elapsed_time(t0), self._ref_event.elapsed_time(t1))
+        check_result(info.cpu().tolist(), B.ca_solve_status(swork, stream) if swork is not None else False,
+                     None if berr is None else float(berr.item()))
+        if berr is not None:
+            r.berr = float(berr.item())
         return np.asfortranarray(out.numpy())
+
+
+def check_result(info, solve_timed_out: bool, berr=None):
+    """Raises (the request fails) when the library reported a problem: a zero
+    pivot (info[0]), a NaN / Inf in a panel or a tensor-core or solve timeout
+    (info[1]), a triangular solve that gave up waiting, or a refinement that
+    ended with a non-finite backward error."""
+    if info[0] != 0:
+        raise RuntimeError(f"U({info[0] - 1}, {info[0] - 1}) is exactly zero: the matrix is singular")
+    if info[1] != 0:
+        raise RuntimeError(f"status bits {info[1]:#x} (1: NaN/Inf in a panel, 2/4/8: tensor-core wait "
+                           "timeout, 16: triangular-solve wait timeout)")
+    if solve_timed_out:
+        raise RuntimeError("a triangular solve gave up waiting for a block (result only partly solved)")
+    if berr is not None and not math.isfinite(berr):
+        raise RuntimeError(f"refinement ended with backward error {berr}")
 
 
 def poisson_workload(rate: float, duration: float, seed: int, nmin: int = 64, nmax: int = 2048,

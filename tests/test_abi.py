@@ -59,16 +59,26 @@ def test_argument_errors_without_gpu(lib):
     assert lib.calu_factor(-1, 4, None, 4, 4, ctypes.byref(t), None, None, 0, None, None) == -1
     assert lib.calu_factor(4, 4, None, 4, 4, ctypes.byref(t), None, None, 0, None, None) == -3
     assert lib.calu_factor(8, 8, ctypes.c_void_p(16), 4, 4, ctypes.byref(t), None, None, 0, None, None) == -4
-    assert lib.calu_getrs(-3, 1, None, 1, None, None, 1, None) == -1
+    assert lib.calu_getrs(-3, 1, None, 1, None, None, 1, None, 0, None) == -1
+    # the solve workspace is the caller's: too small is refused before any launch
+    assert lib.calu_getrs(300, 1, ctypes.c_void_p(256), 300, ctypes.c_void_p(256), ctypes.c_void_p(256), 300,
+                          ctypes.c_void_p(256), 4, None) == -1001
+    assert lib.ca_getrs_workspace(300, 1, ctypes.byref(size)) == 0 and 0 < size.value <= 4096
+    assert lib.ca_getrs_workspace(-1, 1, ctypes.byref(size)) == -1
     assert lib.caqr_factor(4, 8, None, 4, 4, ctypes.byref(t), None, 0, None, 0, None, None) == -2
     assert lib.ca_strerror(-1001).decode().startswith("workspace")
     wide = B.make_tree(512)
     assert lib.ca_calu_workspace(4096, 4096, 256, ctypes.byref(wide), ctypes.byref(size)) == -1002
-    # solve status: a NULL result pointer is an argument error; with no solve
-    # run on the stream (here: no device at all) nothing timed out
-    assert lib.ca_solve_status(None, None) == -2
+    # solve status: NULL workspace or result pointers are argument errors
     flag = ctypes.c_int(7)
-    assert lib.ca_solve_status(None, ctypes.byref(flag)) == 0 and flag.value == 0
+    assert lib.ca_solve_status(None, ctypes.byref(flag), None) == -1
+    assert lib.ca_solve_status(ctypes.c_void_p(256), None, None) == -2
+    # refinement: an unknown correction method is refused (argument 7 of the query)
+    assert lib.ca_gesv_mixed_workspace(512, 1, 64, ctypes.byref(t), 4, 1, 9, ctypes.byref(size)) == -7
+    assert lib.ca_gesv_mixed_workspace(512, 1, 64, ctypes.byref(t), 4, 1, 2, ctypes.byref(size)) == 0
+    classic = ctypes.c_size_t()
+    assert lib.ca_gesv_mixed_workspace(512, 1, 64, ctypes.byref(t), 4, 1, 0, ctypes.byref(classic)) == 0
+    assert size.value > classic.value      # the GMRES correction's Krylov basis
 
 
 def test_workspace_matches_tree_counts(lib):

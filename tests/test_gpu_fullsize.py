@@ -177,7 +177,7 @@ def test_calu_bench_configuration(ca, big):
     assert berr(A0, X7, B0) < 1e-15
     Xm, iters, be, infom = ca.calu_gesv_mixed(A0, B0, b, tree, slices=4, exact=True, tol=1e-14)
     torch.cuda.synchronize()
-    assert be <= 1e-14 and berr(A0, Xm, B0) < 1e-14
+    assert float(be.item()) <= 1e-14 and berr(A0, Xm, B0) < 1e-14
     # forward errors: kappa_2 (1e6) times the backward error, with a factor
     # sqrt(n) between the infinity-norm backward error and the 2-norm bound
     fwd = lambda Y: float(torch.linalg.norm(Y - x) / torch.linalg.norm(x))

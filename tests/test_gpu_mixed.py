@@ -114,9 +114,102 @@ def test_gesv_mixed_refinement(ca, n, cond, slices, exact):
                                               exact=exact, max_iter=30, tol=1e-14)
     torch.cuda.synchronize()
     assert info.cpu().tolist()[1] == 0
-    assert berr <= 1e-14, (iters, berr)
+    assert float(berr.item()) <= 1e-14, (int(iters.item()), float(berr.item()))
     x = to_host(X)
     # both solutions are backward stable (<= 1e-14): they agree to cond * 1e-14
+    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) < max(1e-12, cond * 1e-14)
+
+
+def host_refinement_reference(ca, A, B, b, L, slices, exact, max_iter, tol):
+    """The classic refinement loop driven from the host (one wait per step),
+    from the same calls: the device-side stop test must take the same steps."""
+    n = A.shape[0]
+    Ad, Bd = to_dev(A), to_dev(B)
+    LU = Ad.clone()
+    ipiv, info = ca.calu_factor_mixed(LU, b, ca.make_tree(L), slices=slices, exact=exact)
+    X = Bd.clone()
+    ca.calu_getrs(LU, ipiv, X)
+    anorm = float(Ad.abs().sum(1).amax())
+    prev, stall, hist = 0.0, 0, []
+    for it in range(max_iter + 1):
+        R = Bd - Ad @ X
+        be = float((R.abs().amax(0) / (anorm * X.abs().amax(0) + Bd.abs().amax(0))).max())
+        hist.append(be)
+        if be <= tol or it >= max_iter:
+            break
+        if it > 0 and be > 0.5 * prev:
+            stall += 1
+            if stall >= 2:
+                break
+        else:
+            stall = 0
+        prev = be
+        ca.calu_getrs(LU, ipiv, R)
+        X = X + R
+    return it, hist
+
+
+@pytest.mark.parametrize("cond,slices", [(1e6, 3), (1e10, 4)])
+def test_device_stop_test_takes_the_host_loops_steps(ca, cond, slices):
+    """The stop test runs on the device (the call never waits): it stops at
+    the same step as the same loop driven from the host."""
+    n, b, L = 1024, 128, 256
+    A = inputs.conditioned(n, cond, 11)
+    B = A @ inputs.rhs(n, 1, 12)
+    it_h, hist = host_refinement_reference(ca, A, B, b, L, slices, True, 12, 1e-14)
+    X, iters, berr, info = ca.calu_gesv_mixed(to_dev(A), to_dev(B), b, ca.make_tree(L), slices=slices,
+                                              exact=True, max_iter=12, tol=1e-14)
+    torch.cuda.synchronize()
+    assert int(iters.item()) == it_h, (int(iters.item()), hist)
+    assert abs(float(berr.item()) - hist[-1]) <= 1e-3 * hist[-1] + 1e-300
+
+
+@pytest.mark.parametrize("n,cond,slices,nrhs,max_iter", [(1024, 1e10, 4, 1, 10), (1024, 1e10, 4, 3, 10),
+                                                          (4096, 1e6, 3, 1, 6)])
+def test_gmres_refinement_where_classic_stalls(ca, n, cond, slices, nrhs, max_iter):
+    """GMRES-based refinement (FP64 GMRES on the system preconditioned by the
+    reduced-precision factors) reaches backward error 1e-14 with digit counts
+    for which the classic correction stalls or is too slow.  The solution
+    agrees with the oracle's FP64 CALU solution to cond * 1e-14."""
+    A = inputs.conditioned(n, cond, 21)
+    B = A @ inputs.rhs(n, nrhs, 22)
+    b, L = 128, 256
+    t = ca.make_tree(L)
+    LU_o, ipiv_o, _, _ = oracle.calu(A, b, oracle.make_tree(L))
+    x_o = oracle.getrs(LU_o, ipiv_o, B)
+    _, it_c, be_c, _ = ca.calu_gesv_mixed(to_dev(A), to_dev(B), b, t, slices=slices, exact=True,
+                                          max_iter=max_iter, tol=1e-14, refine="classic")
+    X, it, be, info = ca.calu_gesv_mixed(to_dev(A), to_dev(B), b, t, slices=slices, exact=True,
+                                         max_iter=max_iter, tol=1e-14, refine="gmres")
+    torch.cuda.synchronize()
+    assert float(be_c.item()) > 1e-14, "the classic correction converged: the case does not need GMRES"
+    assert info.cpu().tolist() == [0, 0]
+    assert float(be.item()) <= 1e-14, (int(it.item()), float(be.item()))
+    x = to_host(X)
+    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) < cond * 1e-14
+
+
+@pytest.mark.parametrize("n,cond,slices,expect", [(1024, 1e6, 4, "classic"), (1024, 1e10, 4, "gmres"),
+                                                  (4096, 1e6, 3, "gmres"), (2048, 1e10, 4, "refactor"),
+                                                  (1536, 1e8, 3, "refactor")])
+def test_auto_refinement_reaches_tol(ca, n, cond, slices, expect):
+    """refine="auto": classic corrections, GMRES where they are slow, a
+    refactorization with 7 exact digits where GMRES stalls too (reported by
+    CA_STATUS_REFACTORED); every case reaches backward error 1e-14 and the
+    oracle's solution to cond * 1e-14."""
+    A = inputs.conditioned(n, cond, 21)
+    B = A @ inputs.rhs(n, 1, 22)
+    b, L = 128, 256
+    LU_o, ipiv_o, _, _ = oracle.calu(A, b, oracle.make_tree(L))
+    x_o = oracle.getrs(LU_o, ipiv_o, B)
+    X, it, be, info = ca.calu_gesv_mixed(to_dev(A), to_dev(B), b, ca.make_tree(L), slices=slices, exact=True,
+                                         max_iter=10, tol=1e-14, refine="auto")
+    torch.cuda.synchronize()
+    inf = info.cpu().tolist()
+    assert inf[0] == 0 and (inf[1] & ~ca.CA_STATUS_REFACTORED) == 0, inf
+    assert bool(inf[1] & ca.CA_STATUS_REFACTORED) == (expect == "refactor"), (inf, expect)
+    assert float(be.item()) <= 1e-14, (int(it.item()), float(be.item()), expect)
+    x = to_host(X)
     assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) < max(1e-12, cond * 1e-14)
 
 

@@ -102,3 +102,48 @@ def test_cancel_a_pending_request():
     assert second not in seen and seen == [first, third]
     st = srv.stats()
     assert st["completed"] == 2 and st["cancelled"] == 1 and st["rejected"] == 0
+
+
+def test_library_status_fails_the_request():
+    """A zero pivot, a status bit of dev_info (NaN/Inf, tensor-core or solve
+    timeout), a triangular solve that gave up, or a non-finite backward
+    error turns the request into a failure with the reason; the server
+    keeps serving."""
+    import pytest
+    with pytest.raises(RuntimeError, match="singular"):
+        serve.check_result([5, 0], False)
+    with pytest.raises(RuntimeError, match="0x10"):
+        serve.check_result([0, 16], False)
+    with pytest.raises(RuntimeError, match="gave up"):
+        serve.check_result([0, 0], True)
+    with pytest.raises(RuntimeError, match="backward error"):
+        serve.check_result([0, 0], False, float("nan"))
+    serve.check_result([0, 0], False, 1e-15)
+
+    def execute(r, ctx):
+        serve.check_result([0, int(r.B[0, 0])], bool(r.B[1, 0]))
+        return np.zeros((r.A.shape[1], 1))
+
+    srv = serve.SolveServer(hbm_budget=1 << 40, slots=2, execute=execute)
+    try:
+        timeout_bit = srv.submit("lu", np.eye(8), np.r_[16.0, 0.0, np.zeros(6)])
+        gave_up = srv.submit("lu", np.eye(8), np.r_[0.0, 1.0, np.zeros(6)])
+        ok = srv.submit("lu", np.eye(8), np.zeros(8))
+        srv.drain(timeout=30)
+    finally:
+        srv.close()
+    assert timeout_bit.status == "failed" and "0x10" in timeout_bit.error
+    assert gave_up.status == "failed" and "gave up" in gave_up.error
+    assert ok.status == "done" and srv.stats()["completed"] == 1
+
+
+def test_max_on_device_counts_overlapping_intervals():
+    srv = serve.SolveServer(hbm_budget=1 << 40, slots=1, execute=lambda r, c: np.zeros((1, 1)))
+    try:
+        for iv in [(0.0, 5.0), (1.0, 2.0), (1.5, 6.0), (7.0, 8.0)]:
+            r = serve.Request("lu", np.eye(2), np.ones((2, 1)))
+            r.gpu_ms = iv
+            srv.completed.append(r)
+        assert srv.max_on_device() == 3
+    finally:
+        srv.close()
