@@ -36,7 +36,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "CALU/CAQR GFLOP/s & % roofline (n=16384, FP64 vs mixed+IR); solves/s, p99 lat"
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # SMs x DFMA/clk/SM x flops/DFMA x max GHz = 1258.6
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07    # SMs x DFMA/clk/SM x flops/DFMA x max GHz = 1258.6 GFLOP/s
+FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.07  # SMs x FP32 lanes/SM x flops/FFMA x max GHz = 80548 GFLOP/s
+# The FP64 / FP32 denominators: the FMA peak probe measured at the start of
+# the run (measure_fma_peaks), the derived figures until then.
+PEAKS = {"fp64": FP64_PEAK_DERIVED, "fp32": FP32_PEAK_DERIVED, "source": "derived"}
 # Leaves of the n = 16384 step's tree.  Measured on GB300 (FP64 step, b = 128):
 # 256 rows 747 GFLOP/s, 512 rows 844, 1024 rows 881 -- bigger leaves mean
 # fewer merges, whose tree update executes more flops than the standard count.
@@ -70,6 +74,10 @@ def parse():
     p.add_argument("--cond", type=float, default=1e6)
     p.add_argument("--nrhs", type=int, default=1)
     p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--c3-sizes", default="4096,8192,16384")
+    p.add_argument("--c3-conds", default="1e2,1e6,1e10")
+    p.add_argument("--no-c3", action="store_true")
+    p.add_argument("--only-c3", action="store_true", help="diagnostic: run only the n x cond grid")
     p.add_argument("--aux-steps", type=int, default=2,
                    help="timed runs of each secondary measurement (LU forms, C3 grid), after one warm-up")
     p.add_argument("--cpu-n", type=int, default=2048,
@@ -80,9 +88,10 @@ def parse():
     p.add_argument("--mixed-slices", type=int, default=4)
     p.add_argument("--mixed-exact", type=int, default=1)
     p.add_argument("--no-mixed", action="store_true")
-    p.add_argument("--serve-rate", type=float, default=100.0)
-    p.add_argument("--serve-duration", type=float, default=3.0)
-    p.add_argument("--serve-nmax", type=int, default=2048)
+    p.add_argument("--serve-rates", default="100,1000,10000", help="arrival rates of the sweep (requests/s)")
+    p.add_argument("--serve-count", type=int, default=24, help="requests per rate (the same shapes at every rate)")
+    p.add_argument("--serve-nmax", type=int, default=8192)
+    p.add_argument("--serve-cond-max", type=float, default=1e8)
     p.add_argument("--serve-slots", type=int, default=4, help="concurrent requests (one stream each)")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--batch-count", type=int, default=4096, help="matrices of the batched workload")
@@ -511,6 +520,139 @@ def traffic_for(kernel: str, plan: str):
     return None
 
 
+def haar_device(n, seed, dev):
+    """A Haar-distributed orthogonal n x n matrix on the device: Q of the QR
+    of a seeded N(0, 1) matrix with the signs of R's diagonal folded in
+    (input generation, untimed; torch's QR)."""
+    import torch
+    g = torch.Generator(device=dev).manual_seed(seed)
+    Z = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+    Q, R = torch.linalg.qr(Z)
+    Q *= torch.sign(torch.diagonal(R))[None, :]
+    return Q
+
+
+def c3_grid(a, ca, torch, dev, world):
+    """Square CALU solves over the grid n x cond (b = 128, the benchmark's
+    leaves and tree, one right-hand side): plain FP64 (calu_factor +
+    calu_getrs) against the mixed form (calu_gesv_mixed: a.mixed_slices
+    digits on the tensor cores, refinement "auto" to backward error 1e-14);
+    each one warm-up and a.aux_steps timed runs.  A = U diag(s) V^T with
+    s_i = cond^(-i/(n-1)); U, V Haar (QR of a Gaussian) for n <= 8192, the
+    Kronecker Haar factors of the main step at n = 16384."""
+    from paper_1303_5837_gb300 import inputs
+    st = torch.cuda.current_stream()
+    b, S = a.b, a.mixed_slices
+    tree = ca.make_tree(a.leaf, parse_tree(a.tree))
+    sizes = [int(x) for x in a.c3_sizes.split(",") if x]
+    conds = [float(x) for x in a.c3_conds.split(",") if x]
+    out = {"slices": S, "refine": "auto", "tol": 1e-14, "cells": []}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = max(1, a.aux_steps)
+        e0.record(st)
+        r = None
+        for _ in range(reps):
+            r = fn()
+        e1.record(st)
+        e1.synchronize()
+        return allreduce_max(e0.elapsed_time(e1), world) / reps, r
+
+    for n in sizes:
+        lu_flops = 2.0 * n ** 3 / 3.0 + 2.0 * n * n
+        if n <= 8192:
+            U, V = haar_device(n, 31 + n, dev), haar_device(n, 37 + n, dev)
+            family = "Haar U, V (QR of a Gaussian)"
+        else:
+            U = V = None
+            family = "Kronecker products of Haar factors (as the main step)"
+        A = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+        LU = torch.empty_like(A)
+        X = torch.empty((n, 1), dtype=torch.float64, device=dev)
+        ipiv = torch.empty(n, dtype=torch.int32, device=dev)
+        info = torch.zeros(2, dtype=torch.int32, device=dev)
+        work = torch.empty((ca.ca_calu_workspace(n, n, b, tree) + 7) // 8, dtype=torch.float64, device=dev)
+        swork = torch.empty((ca.ca_getrs_workspace(n, 1) + 7) // 8, dtype=torch.float64, device=dev)
+        wmix = torch.empty((ca.ca_gesv_mixed_workspace(n, 1, b, tree, S, True, "auto") + 7) // 8,
+                           dtype=torch.float64, device=dev)
+        for cond in conds:
+            if U is not None:
+                s_ = torch.from_numpy(inputs.singular_values(n, cond)).to(dev)
+                A0 = ((U * s_) @ V.t()).t().contiguous().t()
+            else:
+                A0 = conditioned_device(n, cond, 2026, dev)
+            x_true = torch.randn(n, 1, dtype=torch.float64, device=dev,
+                                 generator=torch.Generator(device=dev).manual_seed(5))
+            B0 = A0 @ x_true
+            anorm = float(A0.abs().sum(1).amax())
+
+            def berr_of(Xs):
+                R = B0 - A0 @ Xs
+                return float(R.abs().amax() / (anorm * Xs.abs().amax() + B0.abs().amax()))
+
+            def plain():
+                A.copy_(A0)
+                X.copy_(B0)
+                ca.calu_factor(A, b, tree, ipiv=ipiv, work=work, dev_info=info)
+                ca.calu_getrs(A, ipiv, X, work=swork)
+
+            ms_p, _ = timed(plain)
+            be_p = berr_of(X)
+            info_p = info.cpu().tolist()
+
+            def mixed():
+                return ca.calu_gesv_mixed(A0, B0, b, tree, slices=S, exact=True, max_iter=10, tol=1e-14,
+                                          refine="auto", LU=LU, X=X, ipiv=ipiv, work=wmix, dev_info=info)
+
+            ms_m, (_, it, be, inf) = timed(mixed)
+            be_m, it_m, inf_m = float(be.item()), int(it.item()), inf.cpu().tolist()
+            cell = {"n": n, "cond": cond, "family": family,
+                    "fp64": {"ms": ms_p, "gflops": lu_flops / ms_p / 1e6, "berr": be_p, "info": info_p},
+                    "mixed": {"ms": ms_m, "gflops": lu_flops / ms_m / 1e6, "berr": float(be_m),
+                              "berr_check": berr_of(X), "iters": it_m, "info": inf_m,
+                              "refactored": bool(inf_m[1] & ca.CA_STATUS_REFACTORED),
+                              "reaches_tol": be_m <= 1e-14},
+                    "speedup": ms_p / ms_m}
+            out["cells"].append(cell)
+            del A0, B0
+        del U, V, A, LU, X, work, wmix
+        torch.cuda.empty_cache()
+    return out
+
+
+def measure_fma_peaks(ca, torch, dev, reps: int = 5) -> dict:
+    """FP64 and FP32 FMA throughput of this GPU from the library's peak probe
+    (8 independent fused multiply-adds per thread per round, 8 CTAs of 256
+    threads per SM), best of `reps` launches timed with CUDA events; sets
+    PEAKS, the denominators of the roofline fractions."""
+    out = {}
+    st = torch.cuda.current_stream()
+    for name, dt, tdt, iters in (("fp64", 0, torch.float64, 4000), ("fp32", 1, torch.float32, 100000)):
+        blocks = 152 * 8
+        buf = torch.empty(blocks * 256, dtype=tdt, device=dev)
+        ca.ca_peak_probe(dt, blocks, iters, buf)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            ca.ca_peak_probe(dt, blocks, iters, buf)
+            e1.record(st)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        flops = 16.0 * iters * blocks * 256
+        out[name] = {"gflops": flops / (best / 1e3) / 1e9, "ms": best,
+                     "derived": FP64_PEAK_DERIVED if name == "fp64" else FP32_PEAK_DERIVED}
+        PEAKS[name] = out[name]["gflops"]
+    PEAKS["source"] = "measured (ca_peak_probe)"
+    return out
+
+
 def run_ours(a, rank: int, world: int, local: int):
     import torch
     import paper_1303_5837_gb300 as ca
@@ -519,6 +661,12 @@ def run_ours(a, rank: int, world: int, local: int):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     ca.load()
+    peaks = measure_fma_peaks(ca, torch, dev)
+    if a.only_c3:
+        res = c3_grid(a, ca, torch, dev, world)
+        if rank == 0:
+            print(json.dumps({"c3_grid": res, "fma_peaks": peaks}), flush=True)
+        return
     if a.only_serve:
         if rank == 0:
             print(json.dumps({"serving": serving_run(a)}), flush=True)
@@ -644,6 +792,11 @@ def run_ours(a, rank: int, world: int, local: int):
     if not a.no_mixed:
         lu_forms = lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world)
 
+    # ---- the n x cond grid: FP64 against mixed + refinement ----------------
+    c3 = None
+    if not a.no_c3:
+        c3 = c3_grid(a, ca, torch, dev, world)
+
     # ---- serving: continuous batching of an open-loop Poisson stream ---------
     serving = None
     if not a.no_serve and world == 1:
@@ -713,11 +866,15 @@ def run_ours(a, rank: int, world: int, local: int):
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(a, {"parallelism": f"replicas{world}" if world > 1 else "single"}),
-        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
-                     "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": PEAKS["fp64"],
+                     "unit": "GFLOP/s", "frac": achieved / PEAKS["fp64"],
+                     "peak_derived": FP64_PEAK_DERIVED, "frac_of_derived": achieved / FP64_PEAK_DERIVED,
                      "traffic": traffic_for(dom, f"{n}/{b}/{a.leaf}/{a.tree}/"
                                                  f"{round(dk['launches'] / a.steps)}"),
-                     "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+                     "peak_source": ("FP64 DFMA peak measured in this run by ca_peak_probe (8 independent "
+                                     "DFMA chains per thread, 8 CTAs per SM, best of 5); derived: 152 SMs x "
+                                     "2 DFMA/clk x 2 flop x 2.07 GHz")},
+        "fma_peaks": peaks,
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
         "e2e": e2e,
@@ -727,6 +884,7 @@ def run_ours(a, rank: int, world: int, local: int):
         "check": {"x_rel_err_calu": err_lu, "x_rel_err_caqr": err_qr, "library_status": lib_status,
                   "ok": status_ok(lib_status)},
         "lu_forms": lu_forms,
+        "c3_grid": c3,
         "serving": serving,
         "batched": batched,
         "other_configs": configs,
@@ -901,9 +1059,9 @@ def other_configs(a, ca, torch, dev):
         bq, bl = 16.0 * m * n, 24.0 * m * n
         out[f"panel_{m}x{n}"] = {
             "tsqr": {"ms": ms_q, "gflops": fq / ms_q / 1e6, "gbs": bq / ms_q / 1e6,
-                     "frac_fp64": fq / ms_q / 1e6 / FP64_PEAK_GFLOPS, "frac_hbm": bq / ms_q / 1e6 / HBM_GBS},
+                     "frac_fp64": fq / ms_q / 1e6 / PEAKS["fp64"], "frac_hbm": bq / ms_q / 1e6 / HBM_GBS},
             "tslu": {"ms": ms_l, "gflops": fl / ms_l / 1e6, "gbs": bl / ms_l / 1e6,
-                     "frac_fp64": fl / ms_l / 1e6 / FP64_PEAK_GFLOPS, "frac_hbm": bl / ms_l / 1e6 / HBM_GBS}}
+                     "frac_fp64": fl / ms_l / 1e6 / PEAKS["fp64"], "frac_hbm": bl / ms_l / 1e6 / HBM_GBS}}
         del A0, A, qt, qw, lw
     n, b = 1024, 64
     t2 = ca.make_tree(128, [(0, 0)])
@@ -1027,44 +1185,108 @@ def batched_run(a, ca, torch, dtype, dev, rank, world):
            "gflop_per_step": flops / 1e9, "launches_per_step": 1, "graph": True,
            "tuned": table is not None, "nonzero_info": bad, "bytes": tot * esz,
            "form": "ca_batched_factor: one CTA per matrix, LPT work queue, CALU + CAQR of every matrix"}
-    if dtype == torch.float64:
-        out["roofline"] = {"bound": "alu", "achieved": gflops / world, "peak": FP64_PEAK_GFLOPS,
-                           "unit": "GFLOP/s", "frac": gflops / world / FP64_PEAK_GFLOPS}
+    pk = PEAKS["fp64"] if dtype == torch.float64 else PEAKS["fp32"]
+    out["roofline"] = {"bound": "alu", "achieved": gflops / world, "peak": pk, "unit": "GFLOP/s",
+                       "frac": gflops / world / pk, "peak_source": PEAKS["source"],
+                       "note": ("FP64 DFMA pipe" if dtype == torch.float64 else
+                                "FP32 FFMA pipe (the batched FP32 form uses no tensor cores)")}
     del views, bf, graph, flat, pristine
     torch.cuda.empty_cache()
     return out
 
 
+SERVE_SIZES = [64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 6144, 8192]
+
+
+def conditioned_rect_device(m, n, cond, seed, dev):
+    """An m x n matrix (m = n or 4n) A = U diag(s) V^T with orthonormal
+    columns in U, orthogonal V and s_i = cond^(-i/(n-1)) in a seeded order, on
+    the device: U, V Haar (QR of Gaussians) up to n = 2048, above that
+    Kronecker products of Haar factors (n = 64 n2)."""
+    import torch
+    from paper_1303_5837_gb300 import inputs
+    g = torch.Generator(device=dev).manual_seed(seed)
+
+    def q_of(r, c):
+        Q, R = torch.linalg.qr(torch.randn(r, c, dtype=torch.float64, device=dev, generator=g))
+        return Q * torch.sign(torch.diagonal(R))[None, :]
+
+    if n <= 2048:
+        U, V = q_of(m, n), q_of(n, n)
+    else:
+        n1, n2 = 64, n // 64
+        U = torch.kron(q_of(m // n * n1, n1), q_of(n2, n2))
+        V = torch.kron(q_of(n1, n1), q_of(n2, n2))
+    s_ = torch.from_numpy(inputs.singular_values(n, cond)).to(dev)
+    perm = torch.randperm(n, device=dev, generator=g)
+    A = (U * s_[perm]) @ V.t()
+    return A
+
+
 def serving_run(a):
-    """Open-loop Poisson stream of A x = b (CALU) and least-squares (CAQR, m = 4n)
-    requests, n log-uniform in [64, nmax], 1-16 right-hand sides, replayed in
-    real time into the continuous-batching server; plain FP64 and mixed forms.
-    Matrices come from a pre-generated pool per size (untimed)."""
-    from paper_1303_5837_gb300 import inputs, serve
-    work = serve.poisson_workload(a.serve_rate, a.serve_duration, seed=11, nmax=a.serve_nmax)
+    """Open-loop Poisson streams of A x = b (CALU) and least-squares (CAQR,
+    m = 4n) requests: n log-uniform in [64, a.serve_nmax] snapped to a pool
+    of sizes, cond(A) log-uniform in [1, a.serve_cond_max], 1-16 right-hand
+    sides; the same a.serve_count requests at each rate of a.serve_rates,
+    replayed in real time into (1) the plain per-request loop (one stream,
+    arrival order, no overlap), (2) the continuous-batching server in FP64
+    and (3) the server with the mixed forms.  Matrices come from a
+    pre-generated pool, one per (kind, size), generated untimed."""
+    import torch
+    from paper_1303_5837_gb300 import serve
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rates = [float(x) for x in a.serve_rates.split(",") if x]
+    sizes = [s_ for s_ in SERVE_SIZES if s_ <= a.serve_nmax]
+    works = {r: serve.poisson_workload(r, 0.0, seed=11, nmax=a.serve_nmax, count=a.serve_count, sizes=sizes)
+             for r in rates}
     pool = {}
-    for _, kind, m, n, nrhs in work:
-        key = (kind, n)
-        if key not in pool:
-            pool[key] = (inputs.gaussian(m, n, n + (7 if kind == "ls" else 0)), inputs.gaussian(m, 16, n + 1))
-    out = {"rate_per_s": a.serve_rate, "duration_s": a.serve_duration, "requests": len(work),
-           "n_range": [64, a.serve_nmax], "pool_sizes": len(pool), "slots": a.serve_slots}
-    for form in ("fp64", "mixed"):
-        srv = serve.SolveServer(hbm_budget=64 << 30, slots=a.serve_slots, form=form)
-        try:
-            t0 = time.perf_counter()
-            for t, kind, m, n, nrhs in work:
-                now = time.perf_counter() - t0
-                if t > now:
-                    time.sleep(t - now)
-                A, Bm = pool[(kind, n)]
-                srv.submit(kind, A, Bm[:, :nrhs])
-            srv.drain(timeout=600)
-            st = srv.stats()
-            st["failed"] = sum(1 for r in srv.completed if r.status != "done")
-        finally:
-            srv.close()
-        out[form] = st
+    t_pool = time.perf_counter()
+    for work in works.values():
+        for _, kind, m, n, nrhs in work:
+            key = (kind, n)
+            if key in pool:
+                continue
+            g = np.random.default_rng(1000 * n + (7 if kind == "ls" else 0))
+            cond = float(10.0 ** g.uniform(0.0, np.log10(a.serve_cond_max)))
+            A = conditioned_rect_device(m, n, cond, 17 * n + (3 if kind == "ls" else 0), dev)
+            pool[key] = (np.asfortranarray(A.cpu().numpy()), g.standard_normal((m, 16)), cond)
+            del A
+    torch.cuda.empty_cache()
+    out = {"rates_per_s": rates, "requests_per_rate": a.serve_count, "n_sizes": sizes,
+           "m": "n (LU) or 4n (least squares)", "cond_range": [1.0, a.serve_cond_max],
+           "pool_matrices": len(pool), "pool_seconds": time.perf_counter() - t_pool, "slots": a.serve_slots,
+           "forms": {"plain": "one stream, one request at a time in arrival order, FP64 "
+                              "(calu_factor + calu_getrs / caqr_factor + caqr_geqrs)",
+                     "fp64": "continuous-batching server, FP64 factorizations",
+                     "mixed": "continuous-batching server, LU by calu_gesv_mixed (4 digits, refine auto), "
+                              "least squares by the 7-digit tensor-core CAQR"},
+           "sweep": {}}
+    for rate, work in works.items():
+        row = {}
+        items = [(t, kind, pool[(kind, n)][0], pool[(kind, n)][1][:, :nrhs]) for t, kind, m, n, nrhs in work]
+        done = serve.run_plain(items, form="fp64", device=dev.index)
+        st = serve.latency_stats([r for r in done if r.status == "done"])
+        st["failed"] = sum(1 for r in done if r.status != "done")
+        row["plain"] = st
+        for form in ("fp64", "mixed"):
+            srv = serve.SolveServer(hbm_budget=64 << 30, slots=a.serve_slots, form=form, device=dev.index)
+            try:
+                t0 = time.perf_counter()
+                reqs = []
+                for t, kind, A, Bm in items:
+                    now = time.perf_counter() - t0
+                    if t > now:
+                        time.sleep(t - now)
+                    reqs.append(srv.submit(kind, A, Bm))
+                srv.drain(timeout=900)
+                st = srv.stats()
+                st["failed"] = sum(1 for r in reqs if r.status == "failed")
+            finally:
+                srv.close()
+            row[form] = st
+        row["speedup_solves_per_s"] = {f: row[f]["solves_per_s"] / row["plain"]["solves_per_s"]
+                                      for f in ("fp64", "mixed") if row["plain"].get("solves_per_s")}
+        out["sweep"][str(int(rate))] = row
     return out
 
 

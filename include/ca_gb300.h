@@ -423,6 +423,16 @@ long long ca_launch_count(int cls);
 /* Name of a kernel class ("" when out of range). */
 const char *ca_kernel_class_name(int cls);
 
+/* ca_peak_probe: the FMA throughput of one precision on this GPU, the
+ * measured denominator of the roofline fractions (no counterpart in the
+ * paper).  Launches `blocks` CTAs of 256 threads; every thread does `iters`
+ * rounds of 8 independent fused multiply-adds in FP64 (dtype CA_DTYPE_F64)
+ * or FP32 (CA_DTYPE_F32) and writes one value to dev_out (blocks * 256
+ * elements of that type, device).  The caller times it on `stream`; flops =
+ * 16 * iters * blocks * 256.  Errors: -1 dtype, -2 blocks, -3 iters,
+ * -4 dev_out NULL, CA_ERR_LAUNCH. */
+int ca_peak_probe(int dtype, int blocks, int iters, void *dev_out, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

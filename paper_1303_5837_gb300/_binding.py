@@ -103,7 +103,7 @@ SYMBOLS = ("ca_strerror", "ca_calu_workspace", "ca_caqr_workspace", "ca_geqrs_wo
            "ca_gemm_mixed_workspace", "ca_gemm_minus_mixed", "ca_calu_mixed_workspace",
            "calu_factor_mixed", "ca_gesv_mixed_workspace", "calu_gesv_mixed", "ca_caqr_mixed_workspace",
            "caqr_factor_mixed", "ca_batched_plan", "ca_batched_factor", "ca_solve_status",
-           "ca_getrs_workspace", "ca_test_solve_hook", "tslu_noalloc")
+           "ca_getrs_workspace", "ca_test_solve_hook", "tslu_noalloc", "ca_peak_probe")
 KERNEL_CLASSES = ("tslu_node", "laswp", "lu_finish", "trsm_u12", "gemm_fp64", "tsqr_node",
                   "tree_apply", "solve", "split_bf16", "gemm_tc", "refine", "batched",
                   "tree_narrow")
@@ -138,6 +138,7 @@ def load(build_if_missing: bool = True):
     L.ca_getrs_workspace.argtypes = [I, I, PS]
     L.ca_test_solve_hook.argtypes = [ctypes.c_longlong, I]
     L.ca_test_solve_hook.restype = None
+    L.ca_peak_probe.argtypes = [I, I, I, P, P]
     L.caqr_factor.argtypes = [I, I, P, I, I, T, P, S, P, S, P, P]
     L.tsqr.argtypes = [I, I, P, I, T, P, S, P, S, P, P]
     L.caqr_geqrs.argtypes = [I, I, I, P, I, I, T, P, S, P, I, P, S, P]
@@ -332,6 +333,11 @@ def ca_solve_status(work: torch.Tensor, stream=None) -> bool:
     t = ctypes.c_int(0)
     _check("ca_solve_status", load().ca_solve_status(_ptr(work), ctypes.byref(t), _stream(stream)))
     return bool(t.value)
+
+
+def ca_peak_probe(dtype: int, blocks: int, iters: int, out: torch.Tensor, stream=None):
+    """Enqueue the FMA peak probe (16 * iters * blocks * 256 flops)."""
+    _check("ca_peak_probe", load().ca_peak_probe(int(dtype), int(blocks), int(iters), _ptr(out), _stream(stream)))
 
 
 def ca_test_solve_hook(wait_cycles: int = 0, withhold: bool = False):

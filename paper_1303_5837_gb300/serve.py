@@ -160,31 +160,17 @@ class SolveServer:
             w.join(timeout=10)
 
     def stats(self) -> dict:
-        lat = sorted(r.latency for r in self.completed)
-        if not lat:
-            return {"completed": 0, "rejected": len(self.rejected), "cancelled": len(self.cancelled)}
-        pct = lambda p: lat[min(len(lat) - 1, int(math.ceil(p * len(lat))) - 1)]
-        span = max(r.t_done for r in self.completed) - min(r.arrival for r in self.completed)
-        return {"completed": len(lat), "rejected": len(self.rejected),
-                "cancelled": len(self.cancelled), "p50_s": pct(0.50),
-                "p99_s": pct(0.99), "solves_per_s": len(lat) / span if span > 0 else float("inf"),
-                "max_hbm_in_use": self.max_used, "budget": self.budget,
-                "max_running": self.max_running, "max_on_device": self.max_on_device()}
+        out = latency_stats(self.completed)
+        out.update({"rejected": len(self.rejected), "cancelled": len(self.cancelled)})
+        if self.completed:
+            out.update({"max_hbm_in_use": self.max_used, "budget": self.budget,
+                        "max_running": self.max_running, "max_on_device": self.max_on_device()})
+        return out
 
     def max_on_device(self) -> int:
         """Most requests whose device intervals (CUDA events on their streams)
         overlapped at one instant: > 1 means their kernels ran concurrently."""
-        ev = []
-        for r in self.completed:
-            if r.gpu_ms:
-                ev.append((r.gpu_ms[0], 1))
-                ev.append((r.gpu_ms[1], -1))
-        ev.sort(key=lambda e: (e[0], e[1]))
-        cur = best = 0
-        for _, d in ev:
-            cur += d
-            best = max(best, cur)
-        return best
+        return max_overlap(self.completed)
 
     # ---- scheduler: admission by HBM footprint, arrival order ---------------
     def _schedule(self):
@@ -259,44 +245,114 @@ class SolveServer:
         return torch.cuda.Stream(device=self.device)
 
     def _run_on_gpu(self, r: Request, stream):
-        import torch
-        dev = torch.device("cuda", self.device)
-        m, n = r.A.shape
-        nrhs = r.B.shape[1]
-        tree = self.tree()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        berr = None
-        with torch.cuda.stream(stream):
-            t0.record(stream)
-            A = torch.from_numpy(np.ascontiguousarray(r.A.T)).to(dev, non_blocking=True).t()
-            Bm = torch.from_numpy(np.ascontiguousarray(r.B.T)).to(dev, non_blocking=True).t()
-            swork = None
-            if r.kind == LU and self.form == "mixed":
-                X, it, berr, info = B.calu_gesv_mixed(A, Bm, self.b, tree, slices=4, exact=True, tol=1e-14,
-                                                      refine="auto", stream=stream)
-            elif r.kind == LU:
-                ipiv, info = B.calu_factor(A, self.b, tree, stream=stream)
-                swork = B._buf(B.ca_getrs_workspace(n, nrhs), dev)
-                B.calu_getrs(A, ipiv, Bm, work=swork, stream=stream)
-                X = Bm
+        return solve_request(r, stream, self.form, self.b, self.tree(), self.device, self._ref_event)
+
+
+def latency_stats(completed) -> dict:
+    """p50 / p99 latency (arrival to result on the host) and goodput (completed
+    requests over the span from the first arrival to the last result)."""
+    lat = sorted(r.latency for r in completed)
+    if not lat:
+        return {"completed": 0}
+    pct = lambda p: lat[min(len(lat) - 1, int(math.ceil(p * len(lat))) - 1)]
+    span = max(r.t_done for r in completed) - min(r.arrival for r in completed)
+    return {"completed": len(lat), "p50_s": pct(0.50), "p99_s": pct(0.99),
+            "solves_per_s": len(lat) / span if span > 0 else float("inf")}
+
+
+def max_overlap(completed) -> int:
+    """Most requests whose device intervals (gpu_ms) overlap at one instant."""
+    ev = []
+    for r in completed:
+        if r.gpu_ms:
+            ev.append((r.gpu_ms[0], 1))
+            ev.append((r.gpu_ms[1], -1))
+    ev.sort(key=lambda e: (e[0], e[1]))
+    cur = best = 0
+    for _, d in ev:
+        cur += d
+        best = max(best, cur)
+    return best
+
+
+def solve_request(r: Request, stream, form: str, b: int, tree, device: int, ref_event=None):
+    """One request on `stream` through the C-ABI: the matrix and right-hand
+    sides to the device, the factorization and solve of the form ("fp64":
+    calu_factor + calu_getrs / caqr_factor + caqr_geqrs; "mixed": LU by
+    calu_gesv_mixed with 4 digits and automatic refinement, least squares by
+    the 7-digit tensor-core CAQR), the solution back to the host.  Raises
+    when the library reports a problem (check_result)."""
+    import torch
+    dev = torch.device("cuda", device)
+    m, n = r.A.shape
+    nrhs = r.B.shape[1]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    berr = None
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        A = torch.from_numpy(np.ascontiguousarray(r.A.T)).to(dev, non_blocking=True).t()
+        Bm = torch.from_numpy(np.ascontiguousarray(r.B.T)).to(dev, non_blocking=True).t()
+        swork = None
+        if r.kind == LU and form == "mixed":
+            X, it, berr, info = B.calu_gesv_mixed(A, Bm, b, tree, slices=4, exact=True, tol=1e-14,
+                                                  refine="auto", stream=stream)
+        elif r.kind == LU:
+            ipiv, info = B.calu_factor(A, b, tree, stream=stream)
+            swork = B._buf(B.ca_getrs_workspace(n, nrhs), dev)
+            B.calu_getrs(A, ipiv, Bm, work=swork, stream=stream)
+            X = Bm
+        else:
+            if form == "mixed":
+                qtree, info = B.caqr_factor_mixed(A, b, tree, slices=7, exact=True, stream=stream)
             else:
-                if self.form == "mixed":
-                    qtree, info = B.caqr_factor_mixed(A, self.b, tree, slices=7, exact=True, stream=stream)
-                else:
-                    qtree, info = B.caqr_factor(A, self.b, tree, stream=stream)
-                swork = B._buf(B.ca_geqrs_workspace(m, n, nrhs, self.b, tree), dev)
-                B.caqr_geqrs(A, self.b, tree, qtree, Bm, work=swork, stream=stream)
-                X = Bm[:n]
-            out = X.cpu()  # waits for this request's stream only
-            t1.record(stream)
-            stream.synchronize()
-        r.gpu_ms = (self._ref_event.elapsed_time(t0), self._ref_event.elapsed_time(t1))
-        check_result(info.cpu().tolist(), B.ca_solve_status(swork, stream) if swork is not None else False,
-                     None if berr is None else float(berr.item()))
-        if berr is not None:
-            r.berr = float(berr.item())
-        return np.asfortranarray(out.numpy())
+                qtree, info = B.caqr_factor(A, b, tree, stream=stream)
+            swork = B._buf(B.ca_geqrs_workspace(m, n, nrhs, b, tree), dev)
+            B.caqr_geqrs(A, b, tree, qtree, Bm, work=swork, stream=stream)
+            X = Bm[:n]
+        out = X.cpu()  # waits for this request's stream only
+        t1.record(stream)
+        stream.synchronize()
+    if ref_event is not None:
+        r.gpu_ms = (ref_event.elapsed_time(t0), ref_event.elapsed_time(t1))
+    check_result(info.cpu().tolist(), B.ca_solve_status(swork, stream) if swork is not None else False,
+                 None if berr is None else float(berr.item()))
+    if berr is not None:
+        r.berr = float(berr.item())
+    return np.asfortranarray(out.numpy())
+
+
+def run_plain(items, form: str = "fp64", b: int = 128, leaf_rows: int = 256, levels=((4, 0), (0, 0)),
+              device: int = 0):
+    """The plain per-request form the server is compared with: one thread, one
+    stream, requests taken in arrival order as they arrive (no admission, no
+    overlap), each solved to completion before the next starts.  items:
+    (arrival in seconds after the start, kind, A, B).  Returns the requests
+    with their results and latencies."""
+    import torch
+    torch.cuda.set_device(device)
+    stream = torch.cuda.Stream(device=device)
+    tree = B.make_tree(leaf_rows, levels)
+    done = []
+    t_start = time.perf_counter()
+    for t_arr, kind, A, Bm in items:
+        now = time.perf_counter() - t_start
+        if t_arr > now:
+            time.sleep(t_arr - now)
+        if Bm.ndim == 1:
+            Bm = Bm[:, None]
+        r = Request(kind, np.asfortranarray(A), np.asfortranarray(Bm), arrival=t_start + t_arr)
+        r.status = "running"
+        try:
+            r.X = solve_request(r, stream, form, b, tree, device)
+            r.status = "done"
+        except Exception as e:  # noqa: BLE001 -- the request fails, the loop goes on
+            r.status = "failed"
+            r.error = repr(e)
+        r.t_done = time.perf_counter()
+        r.done.set()
+        done.append(r)
+    return done
 
 
 def check_result(info, solve_timed_out: bool, berr=None):
@@ -316,16 +372,20 @@ def check_result(info, solve_timed_out: bool, berr=None):
 
 
 def poisson_workload(rate: float, duration: float, seed: int, nmin: int = 64, nmax: int = 2048,
-                     ls_fraction: float = 0.5, max_rhs: int = 16):
+                     ls_fraction: float = 0.5, max_rhs: int = 16, count: int | None = None, sizes=None):
     """Arrival times and shapes of an open-loop Poisson stream: n log-uniform in
-    [nmin, nmax], LU (m = n) or LS (m = 4n) requests, 1..max_rhs right-hand sides."""
+    [nmin, nmax] (snapped to the nearest of `sizes` in log scale, when given),
+    LU (m = n) or LS (m = 4n) requests, 1..max_rhs right-hand sides; the
+    arrivals of `duration` seconds, or the first `count` arrivals."""
     g = np.random.Generator(np.random.PCG64(seed))
     t, out = 0.0, []
     while True:
         t += g.exponential(1.0 / rate)
-        if t > duration:
+        if (count is None and t > duration) or (count is not None and len(out) >= count):
             return out
         n = int(round(math.exp(g.uniform(math.log(nmin), math.log(nmax)))))
+        if sizes:
+            n = min(sizes, key=lambda s_: abs(math.log(s_) - math.log(n)))
         kind = LS if g.uniform() < ls_fraction else LU
         m = 4 * n if kind == LS else n
         out.append((t, kind, m, n, int(g.integers(1, max_rhs + 1))))

@@ -1,7 +1,9 @@
 """The serving loop on the GPU: a mix of LU and least-squares requests of
-uneven sizes runs concurrently on several streams; every result equals the
-same request solved alone (the kernels are deterministic, so exactly), and
-matches the CPU oracle."""
+uneven sizes runs concurrently on several streams -- requests admitted
+while others run overlap on the device (their CUDA-event intervals
+intersect) -- every result equals the same request solved alone (the
+kernels are deterministic, so exactly), and matches the CPU oracle; the
+plain per-request loop gives the same answers."""
 import numpy as np
 import pytest
 
@@ -53,6 +55,8 @@ def test_results_same_alone_and_in_the_mix(serve, form):
     finally:
         mix.close()
     assert st["completed"] == len(reqs), [r.error for r in got if r.status != "done"][:3]
+    # continuous batching, not a queue: requests ran on the device at the same time
+    assert st["max_running"] >= 2 and st["max_on_device"] >= 2, st
     for r, x in zip(got, ref):
         assert r.status == "done", r.error
         assert np.array_equal(r.X, x)
@@ -65,3 +69,22 @@ def test_results_same_alone_and_in_the_mix(serve, form):
             QR, T = oracle.caqr(A, 128, oracle.make_tree(256, [(4, 0), (0, 0)]))
             xo = oracle.geqrs(QR, T, 128, oracle.make_tree(256, [(4, 0), (0, 0)]), Bm)
         assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-10
+
+
+def test_plain_loop_matches_the_server(serve):
+    """The plain per-request form (one stream, in arrival order, no admission)
+    that the server is measured against gives the same answers."""
+    reqs = make_requests(2)[:8]
+    srv = serve.SolveServer(hbm_budget=1 << 34, slots=1, form="fp64")
+    try:
+        ref = []
+        for kind, A, Bm in reqs:
+            r = srv.submit(kind, A, Bm)
+            r.done.wait(120)
+            ref.append(r.X)
+    finally:
+        srv.close()
+    done = serve.run_plain([(0.0, kind, A, Bm) for kind, A, Bm in reqs], form="fp64")
+    assert all(r.status == "done" for r in done), [r.error for r in done]
+    for r, x in zip(done, ref):
+        assert np.array_equal(r.X, x)
