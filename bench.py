@@ -1010,6 +1010,24 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
                                "speedup_vs_fp64": out["qr_fp64"]["ms"] / ms,
                                "form": "caqr_factor_mixed(7 exact digits) + caqr_geqrs: FP64-accurate tree "
                                        "update on the tensor cores"}
+    del qwmix
+    torch.cuda.empty_cache()
+    qg, wg = ca.ca_gels_mixed_workspace(n, n, a.nrhs, b, tree, S, ex)
+    qtg = torch.empty((qg + 7) // 8, dtype=torch.float64, device=A0.device)
+    wgl = torch.empty((wg + 7) // 8, dtype=torch.float64, device=A0.device)
+
+    def qr_mixed():
+        return ca.caqr_gels_mixed(A0, B0, b, tree, slices=S, exact=ex, max_iter=10, tol=1e-14, QR=A, qtree=qtg,
+                                  X=X, work=wgl, dev_info=info)
+
+    ms, (_, it, be, _) = timed(qr_mixed, "qr_mixed_ir")
+    out["qr_mixed_ir"] = {"ms": ms, "gflops": qr_flops / ms / 1e6, "iters": int(it.item()),
+                          "ls_measure": float(be.item()), "berr": berr_of(X),
+                          "x_rel_err": float(torch.linalg.norm(X - x_true) / torch.linalg.norm(x_true)),
+                          "speedup_vs_fp64": out["qr_fp64"]["ms"] / ms,
+                          "form": (f"caqr_gels_mixed: {S}-digit bf16 tensor-core tree update + refinement of "
+                                   "the corrected semi-normal equations (double-double residual)")}
+    del qtg, wgl
     for k, v in kernels_of.items():
         out[k]["kernels"] = v
     return out
@@ -1259,7 +1277,7 @@ def serving_run(a):
                               "(calu_factor + calu_getrs / caqr_factor + caqr_geqrs)",
                      "fp64": "continuous-batching server, FP64 factorizations",
                      "mixed": "continuous-batching server, LU by calu_gesv_mixed (4 digits, refine auto), "
-                              "least squares by the 7-digit tensor-core CAQR"},
+                              "least squares by caqr_gels_mixed (4 digits, refinement)"},
            "sweep": {}}
     for rate, work in works.items():
         row = {}

@@ -344,6 +344,35 @@ int calu_gesv_mixed(int n, int nrhs, const double *A, int lda, int b, const ca_t
                     int ldb, double *X, int ldx, void *work, size_t lwork, int max_iter, double tol,
                     int *dev_iters, double *dev_berr, int *dev_info, cudaStream_t stream);
 
+/* caqr_gels_mixed: least squares min ||A X - B|| (m x n, m >= n) by the
+ * reduced-precision CAQR plus FP64 refinement: QR <- A (copy in the caller's
+ * QR buffer), caqr_factor_mixed with `slices` digits and the `exact` mode
+ * (TSQR in FP64, the tree update on the tensor cores), X = R^-1 (Q^T B)(0:n)
+ * (as caqr_geqrs), then repeat R = B - A X (accumulated in double-double,
+ * rounded once to FP64), S = A^T R in FP64 and X += R^-1 R^-T S
+ * (refinement of the corrected semi-normal equations with the computed
+ * triangular factor; its fixed point satisfies the least-squares condition
+ * A^T (B - A X) = 0 to FP64 rounding, Sec. 3.1: A = QR), until the last
+ * correction is below 4 unit roundoffs of X, fails to halve twice in a row,
+ * or max_iter corrections.  Each step gains about a factor
+ * cond(A) 2^(-8 slices); the stop test runs on the device and the call
+ * returns without waiting.  The reported measure (dev_berr) is
+ * max_j ||A^T R_j||inf / (||A||_1 (||A||inf ||X_j||inf + ||B_j||inf)) and tol
+ * is its target (the least-squares solution of the FP64 problem has it at a
+ * few unit roundoffs).
+ * qtree receives the T factors as in caqr_factor.  dev_iters / dev_berr
+ * (device, may be NULL): corrections and final value of the stop measure.
+ * dev_info as calu_gesv_mixed.  Arguments: 1 m, 2 n, 3 nrhs, 4 A, 5 lda, 6 b,
+ * 7 tree, 8 slices, 9 exact, 10 QR, 11 ldqr, 12 qtree, 13 qtree_bytes, 14 B,
+ * 15 ldb, 16 X (n x nrhs), 17 ldx, 18 work, 19 lwork, 20 max_iter, 21 tol,
+ * 22 dev_iters, 23 dev_berr, 24 dev_info, 25 stream. */
+int ca_gels_mixed_workspace(int m, int n, int nrhs, int b, const ca_tree_t *tree, int slices, int exact,
+                            size_t *qtree_bytes, size_t *work_bytes);
+int caqr_gels_mixed(int m, int n, int nrhs, const double *A, int lda, int b, const ca_tree_t *tree, int slices,
+                    int exact, double *QR, int ldqr, double *qtree, size_t qtree_bytes, const double *B, int ldb,
+                    double *X, int ldx, void *work, size_t lwork, int max_iter, double tol, int *dev_iters,
+                    double *dev_berr, int *dev_info, cudaStream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batched factorizations: many small matrices of uneven shapes, each with   */
 /* its own panel width and tree, in one persistent launch                    */

@@ -16,7 +16,8 @@ _BINDING_NAMES = {
     "caqr_factor_mixed", "ca_batched_plan", "ca_batched_factor", "BatchedFactor", "ca_batch_item_t",
     "CA_BATCH_CALU", "CA_BATCH_CAQR", "CA_DTYPE_F64", "CA_DTYPE_F32", "ca_solve_status",
     "ca_getrs_workspace", "ca_test_solve_hook", "CA_REFINE_CLASSIC", "CA_REFINE_GMRES", "CA_REFINE_AUTO",
-    "CA_STATUS_SOLVE_TIMEOUT", "CA_STATUS_REFACTORED", "ca_peak_probe",
+    "CA_STATUS_SOLVE_TIMEOUT", "CA_STATUS_REFACTORED", "ca_peak_probe", "ca_gels_mixed_workspace",
+    "caqr_gels_mixed",
 }
 
 

@@ -103,7 +103,8 @@ SYMBOLS = ("ca_strerror", "ca_calu_workspace", "ca_caqr_workspace", "ca_geqrs_wo
            "ca_gemm_mixed_workspace", "ca_gemm_minus_mixed", "ca_calu_mixed_workspace",
            "calu_factor_mixed", "ca_gesv_mixed_workspace", "calu_gesv_mixed", "ca_caqr_mixed_workspace",
            "caqr_factor_mixed", "ca_batched_plan", "ca_batched_factor", "ca_solve_status",
-           "ca_getrs_workspace", "ca_test_solve_hook", "tslu_noalloc", "ca_peak_probe")
+           "ca_getrs_workspace", "ca_test_solve_hook", "tslu_noalloc", "ca_peak_probe",
+           "ca_gels_mixed_workspace", "caqr_gels_mixed")
 KERNEL_CLASSES = ("tslu_node", "laswp", "lu_finish", "trsm_u12", "gemm_fp64", "tsqr_node",
                   "tree_apply", "solve", "split_bf16", "gemm_tc", "refine", "batched",
                   "tree_narrow")
@@ -139,6 +140,9 @@ def load(build_if_missing: bool = True):
     L.ca_test_solve_hook.argtypes = [ctypes.c_longlong, I]
     L.ca_test_solve_hook.restype = None
     L.ca_peak_probe.argtypes = [I, I, I, P, P]
+    L.ca_gels_mixed_workspace.argtypes = [I, I, I, I, T, I, I, PS, PS]
+    L.caqr_gels_mixed.argtypes = [I, I, I, P, I, I, T, I, I, P, I, P, S, P, I, P, I, P, S, I, ctypes.c_double,
+                                  P, P, P, P]
     L.caqr_factor.argtypes = [I, I, P, I, I, T, P, S, P, S, P, P]
     L.tsqr.argtypes = [I, I, P, I, T, P, S, P, S, P, P]
     L.caqr_geqrs.argtypes = [I, I, I, P, I, I, T, P, S, P, I, P, S, P]
@@ -482,6 +486,49 @@ def calu_gesv_mixed(A: torch.Tensor, B: torch.Tensor, b: int, tree: ca_tree_t, s
                                 _ptr(work), work.numel() * 8, max_iter, tol, _ptr(iters), _ptr(berr),
                                 _ptr(dev_info), _stream(stream))
     _check("calu_gesv_mixed", rc)
+    return X, iters, berr, dev_info
+
+
+def ca_gels_mixed_workspace(m: int, n: int, nrhs: int, b: int, tree: ca_tree_t, slices: int, exact: bool):
+    q = ctypes.c_size_t(0)
+    w = ctypes.c_size_t(0)
+    _check("ca_gels_mixed_workspace",
+           load().ca_gels_mixed_workspace(m, n, nrhs, b, ctypes.byref(tree), slices, 1 if exact else 0,
+                                          ctypes.byref(q), ctypes.byref(w)))
+    return q.value, w.value
+
+
+def caqr_gels_mixed(A: torch.Tensor, B: torch.Tensor, b: int, tree: ca_tree_t, slices: int = 4,
+                    exact: bool = True, max_iter: int = 10, tol: float = 1e-14, QR=None, qtree=None, X=None,
+                    work=None, dev_info=None, iters=None, berr=None, stream=None):
+    """Least squares by the reduced-precision CAQR + FP64 refinement.  Returns
+    (X n x nrhs, iterations int32[1], stop measure float64[1], dev_info); the
+    device tensors are written on the stream (the call does not wait)."""
+    m, n, lda = _mat(A, "A")
+    mb, nrhs, ldb = _mat(B, "B")
+    dev = A.device
+    qb, wb = ca_gels_mixed_workspace(m, n, nrhs, b, tree, slices, exact)
+    if QR is None:
+        QR = torch.empty((m, n), dtype=torch.float64, device=dev).t().contiguous().t()
+    if qtree is None:
+        qtree = _buf(qb, dev)
+    if X is None:
+        X = torch.empty((n, nrhs), dtype=torch.float64, device=dev).t().contiguous().t()
+    if work is None:
+        work = _buf(wb, dev)
+    if dev_info is None:
+        dev_info = torch.zeros(2, dtype=torch.int32, device=dev)
+    if iters is None:
+        iters = torch.zeros(1, dtype=torch.int32, device=dev)
+    if berr is None:
+        berr = torch.zeros(1, dtype=torch.float64, device=dev)
+    _, _, ldqr = _mat(QR, "QR")
+    _, _, ldx = _mat(X, "X")
+    rc = load().caqr_gels_mixed(m, n, nrhs, _ptr(A), lda, b, ctypes.byref(tree), slices, 1 if exact else 0,
+                                _ptr(QR), ldqr, _ptr(qtree), qtree.numel() * 8, _ptr(B), ldb, _ptr(X), ldx,
+                                _ptr(work), work.numel() * 8, max_iter, tol, _ptr(iters), _ptr(berr),
+                                _ptr(dev_info), _stream(stream))
+    _check("caqr_gels_mixed", rc)
     return X, iters, berr, dev_info
 
 

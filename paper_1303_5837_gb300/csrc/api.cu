@@ -705,4 +705,106 @@ int caqr_factor_mixed(int m, int n, double *A, int lda, int b, const ca_tree_t *
   return caqr_run(m, n, A, lda, b, tree, qtree, work, nl, tcws, slices, exact, dev_info, stream);
 }
 
+int ca_gels_mixed_workspace(int m, int n, int nrhs, int b, const ca_tree_t *tree, int slices, int exact,
+                            size_t *qtree_bytes, size_t *work_bytes) {
+  if (nrhs < 0) return -3;
+  size_t q = 0, wf = 0, wg = 0;
+  int rc = ca_caqr_mixed_workspace(m, n, b, tree, slices, exact, &q, &wf);
+  if (rc == -1 || rc == -2) return rc;
+  if (rc == -3 || rc == -4) return rc - 1;  // b, tree are arguments 4, 5 here
+  if (rc == -5) return -6;
+  if (rc != CA_OK) return rc;
+  rc = ca_geqrs_workspace(m, n, nrhs > 0 ? nrhs : 1, b, tree, &wg);
+  if (rc != CA_OK) return rc;
+  if (!qtree_bytes) return -8;
+  if (!work_bytes) return -9;
+  const int nr = nrhs > 0 ? nrhs : 1;
+  *qtree_bytes = q;
+  *work_bytes = align256(wf) + align256(wg) + align256((size_t)m * nr * 8) + align256(solve_ws_bytes(n)) +
+                ls_ws_bytes(m, n, nr);
+  return CA_OK;
+}
+
+int caqr_gels_mixed(int m, int n, int nrhs, const double *A, int lda, int b, const ca_tree_t *tree, int slices,
+                    int exact, double *QR, int ldqr, double *qtree, size_t qtree_bytes, const double *B, int ldb,
+                    double *X, int ldx, void *work, size_t lwork, int max_iter, double tol, int *dev_iters,
+                    double *dev_berr, int *dev_info, cudaStream_t stream) {
+  if (m < 0) return -1;
+  if (n < 0 || n > m) return -2;
+  if (nrhs < 0) return -3;
+  if (n > 0 && !A) return -4;
+  if (lda < (m > 1 ? m : 1)) return -5;
+  if (b < 1) return -6;
+  if (check_tree(tree, b)) return -7;
+  if (slices < 1 || slices > 8) return -8;
+  if (n > 0 && !QR) return -10;
+  if (ldqr < (m > 1 ? m : 1)) return -11;
+  if (n > 0 && nrhs > 0 && !B) return -14;
+  if (ldb < (m > 1 ? m : 1)) return -15;
+  if (n > 0 && nrhs > 0 && !X) return -16;
+  if (ldx < (n > 1 ? n : 1)) return -17;
+  if (max_iter < 0) return -20;
+  if (!dev_info) return -24;
+  size_t qneed = 0, need = 0;
+  int rc = ca_gels_mixed_workspace(m, n, nrhs, b, tree, slices, exact, &qneed, &need);
+  if (rc != CA_OK) return rc;
+  if (n > 0 && (!qtree || qtree_bytes < qneed)) return CA_ERR_WORKSPACE;
+  if (n > 0 && (!work || lwork < need)) return CA_ERR_WORKSPACE;
+  if (dev_iters && cudaMemsetAsync(dev_iters, 0, sizeof(int), stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if (dev_berr && cudaMemsetAsync(dev_berr, 0, sizeof(double), stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if (n == 0) return cudaMemsetAsync(dev_info, 0, 2 * sizeof(int), stream) == cudaSuccess ? CA_OK : CA_ERR_LAUNCH;
+  size_t qb = 0, wf = 0, wg = 0;
+  ca_caqr_mixed_workspace(m, n, b, tree, slices, exact, &qb, &wf);
+  const int nr = nrhs > 0 ? nrhs : 1;
+  ca_geqrs_workspace(m, n, nr, b, tree, &wg);
+  char *p = (char *)work;
+  void *wfact = p;
+  p += align256(wf);
+  void *wgeq = p;
+  p += align256(wg);
+  double *W = (double *)p;  // m x nrhs: Q^T B
+  p += align256((size_t)m * nr * 8);
+  SolveWs sw;
+  solve_ws_carve(p, n, sw);
+  p += align256(solve_ws_bytes(n));
+  LsWs lw;
+  ls_ws_carve(p, m, n, nr, lw);
+  int *status = dev_info + 1;
+  const int sbit = CA_STATUS_SOLVE_TIMEOUT;
+  // 1. QR <- A, CAQR with the tree update on the tensor cores (TSQR in FP64)
+  if (cudaMemcpy2DAsync(QR, (size_t)ldqr * 8, A, (size_t)lda * 8, (size_t)m * 8, n, cudaMemcpyDeviceToDevice,
+                        stream) != cudaSuccess)
+    return CA_ERR_LAUNCH;
+  rc = caqr_factor_mixed(m, n, QR, ldqr, b, tree, slices, exact, qtree, qtree_bytes, wfact, wf, dev_info, stream);
+  if (rc != CA_OK) return rc;
+  if (nrhs == 0) return CA_OK;
+  // 2. X = R^-1 (Q^T B)(0:n) with the reduced-precision factors
+  if (cudaMemcpy2DAsync(W, (size_t)m * 8, B, (size_t)ldb * 8, (size_t)m * 8, nrhs, cudaMemcpyDeviceToDevice,
+                        stream) != cudaSuccess)
+    return CA_ERR_LAUNCH;
+  rc = caqr_geqrs(m, n, nrhs, QR, ldqr, b, tree, qtree, qtree_bytes, W, m, wgeq, wg, stream);
+  if (rc != CA_OK) return rc;
+  if (cudaMemcpy2DAsync(X, (size_t)ldx * 8, W, (size_t)m * 8, (size_t)n * 8, nrhs, cudaMemcpyDeviceToDevice,
+                        stream) != cudaSuccess)
+    return CA_ERR_LAUNCH;
+  // 3. refinement on the corrected semi-normal equations, enqueued in full:
+  //    R = B - A X and S = A^T R in FP64, the stop test on the device, then
+  //    X += R^-1 R^-T S with the triangular factor
+  if (ls_norms(m, n, A, lda, lw, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if (ls_transpose_r(n, QR, ldqr, lw, nullptr, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  if (ls_begin(lw, nullptr, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  const int *stop = &lw.ctl->done;
+  for (int it = 0;; ++it) {
+    if (ls_residual(m, n, nrhs, A, lda, X, ldx, B, ldb, lw, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+    if (ls_normal_residual(m, n, nrhs, A, lda, X, ldx, B, ldb, lw, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+    if (ls_decide(it, max_iter, tol, nrhs, lw, dev_berr, dev_iters, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+    if (it >= max_iter) break;
+    if (trsm_left(true, false, n, nrhs, lw.Rt, n, lw.S, n, sw, status, sbit, stop, stream) != cudaSuccess ||
+        trsm_left(false, false, n, nrhs, QR, ldqr, lw.S, n, sw, status, sbit, stop, stream) != cudaSuccess)
+      return CA_ERR_LAUNCH;
+    if (ls_update(n, nrhs, lw, X, ldx, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  }
+  return CA_OK;
+}
+
 }  // extern "C"

@@ -319,8 +319,9 @@ struct IrCtl {
   int iters;      // corrections applied in this phase
   int iter_base;  // corrections of the phases before it
   double slow;    // a step reducing the error by less than 1/slow ends the phase
-  double prev;    // backward error of the previous step
+  double prev;    // backward error (least squares: correction size) of the previous step
   double berr;    // latest backward error (largest over the right-hand sides)
+  double dx;      // least squares: relative size of the last correction
 };
 constexpr int kIrPhases = 3;  // AUTO: classic, GMRES, refactorization with 7 exact digits
 struct IrWs {
@@ -352,6 +353,29 @@ cudaError_t ir_berr(int n, int nrhs, const double *X, int ldx, const double *B, 
 cudaError_t ir_decide(int it, int max_iter, double tol, int nrhs, const IrWs &w, double *berr_out,
                       int *iters_out, cudaStream_t st);
 cudaError_t ir_update(int n, int nrhs, const IrWs &w, double *X, int ldx, cudaStream_t st);
+
+// least-squares refinement (ir.cu): corrected semi-normal equations with the
+// triangular factor R; r = b - A x (m x nrhs), s = A^T r, x += R^-1 R^-T s
+struct LsWs {
+  double *partial, *R, *S, *Rt, *sums, *anorm, *a1, *berr;
+  IrCtl *ctl;
+  IrCtl *phase[kIrPhases];
+  int *info2;
+};
+size_t ls_ws_bytes(int m, int n, int nrhs);
+void ls_ws_carve(void *ws, int m, int n, int nrhs, LsWs &w);
+cudaError_t ls_norms(int m, int n, const double *A, int lda, const LsWs &w, cudaStream_t st);
+cudaError_t ls_residual(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B,
+                        int ldb, const LsWs &w, cudaStream_t st);
+// s = A^T r and the backward error ||s|| / (||A||_1 (||A||inf ||x|| + ||b||)) per right-hand side
+cudaError_t ls_normal_residual(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx,
+                               const double *B, int ldb, const LsWs &w, cudaStream_t st);
+cudaError_t ls_transpose_r(int n, const double *QR, int ldq, const LsWs &w, const int *skip, cudaStream_t st);
+cudaError_t ls_update(int n, int nrhs, const LsWs &w, double *X, int ldx, cudaStream_t st);
+cudaError_t ls_decide(int it, int max_iter, double tol, int nrhs, const LsWs &w, double *berr_out, int *iters_out,
+                      cudaStream_t st);
+cudaError_t ls_begin(const LsWs &w, const IrCtl *prev, cudaStream_t st);
+cudaError_t ls_merge_info(const LsWs &w, int *dev_info, cudaStream_t st);
 
 // GMRES corrections (ir.cu): at most kGmMax Arnoldi steps per correction,
 // stopped when the preconditioned residual has dropped by kGmTol.

@@ -312,6 +312,341 @@ cudaError_t ir_update(int n, int nrhs, const IrWs &w, double *X, int ldx, cudaSt
 }
 
 // ---------------------------------------------------------------------------
+// Least-squares refinement on the corrected semi-normal equations: with R
+// the (reduced-precision) triangular factor of A, each step computes
+// r = b - A x in double-double (rounded once to FP64), s = A^T r in FP64, and
+// corrects x += R^-1 R^-T s.  The contraction per step is about cond(A)
+// times the factorization's relative error, as for the LU refinement; the
+// fixed point satisfies the least-squares condition A^T (b - A x) = 0 to the
+// rounding of s, so its error is of the order of the problem's own
+// sensitivity (cond eps + cond^2 eps ||r|| / (||A|| ||x||)), which an FP64
+// residual (rounding errors of order eps ||A|| ||x||) would raise to
+// cond^2 eps.
+// ---------------------------------------------------------------------------
+constexpr int kAtrWarps = 8;
+
+// Double-double arithmetic for the least-squares residual (r = b - A x with a
+// relative error of order eps^2 (|A||x| + |b|) before its final rounding, so
+// that the fixed point of the refinement is governed by the problem's own
+// sensitivity and not by the rounding of r).  Knuth's TwoSum and the FMA
+// TwoProduct; the _rn intrinsics are never contracted into FMAs.
+struct DD {
+  double hi, lo;
+};
+__device__ __forceinline__ DD two_sum(double a, double b) {
+  const double s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  const double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+  return DD{s, e};
+}
+__device__ __forceinline__ DD dd_add_prod(DD acc, double a, double b) {  // acc + a b
+  const double p = __dmul_rn(a, b);
+  const double pe = fma(a, b, -p);
+  const DD s = two_sum(acc.hi, p);
+  return DD{s.hi, __dadd_rn(__dadd_rn(acc.lo, pe), s.lo)};
+}
+__device__ __forceinline__ DD dd_add(DD a, DD b) {
+  const DD s = two_sum(a.hi, b.hi);
+  return DD{s.hi, __dadd_rn(__dadd_rn(a.lo, b.lo), s.lo)};
+}
+
+// partial[(cb * nrhs + j) * m + i] = (hi, lo) of sum_{c in block cb} A(i, c) X(c, j)
+__global__ void __launch_bounds__(kResRows) resid_partial_dd_kernel(int m, int ncols, int nrhs, const double *A,
+                                                                    int lda, const double *X, int ldx, DD *partial,
+                                                                    const int *skip) {
+  __shared__ double xs[kResCols * 4];
+  if (*skip) return;
+  const int i = blockIdx.x * kResRows + threadIdx.x;
+  const int c0 = blockIdx.y * kResCols;
+  const int nc = min(kResCols, ncols - c0);
+  for (int j0 = 0; j0 < nrhs; j0 += 4) {
+    const int nj = min(4, nrhs - j0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nc * 4; idx += kResRows) {
+      int c = idx % nc, j = idx / nc;
+      xs[j * kResCols + c] = (j < nj) ? X[(c0 + c) + (size_t)(j0 + j) * ldx] : 0.0;
+    }
+    __syncthreads();
+    DD acc[4] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+    if (i < m) {
+      const double *a = A + i + (size_t)c0 * lda;
+      for (int c = 0; c < nc; ++c) {
+        const double v = a[(size_t)c * lda];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j] = dd_add_prod(acc[j], v, xs[j * kResCols + c]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < nj) partial[((size_t)blockIdx.y * nrhs + j0 + j) * m + i] = acc[j];
+    }
+  }
+}
+
+// R = B - sum_cb partial[cb], summed and subtracted in double-double, rounded once
+__global__ void resid_reduce_dd_kernel(int m, int nrhs, int ncb, const DD *partial, const double *B, int ldb,
+                                       double *R, int ldr, const int *skip) {
+  if (*skip) return;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)m * nrhs) return;
+  const int i = (int)(t % m), j = (int)(t / m);
+  DD s{0.0, 0.0};
+  for (int cb = 0; cb < ncb; ++cb) s = dd_add(s, partial[((size_t)cb * nrhs + j) * m + i]);
+  const DD r = dd_add(DD{B[i + (size_t)j * ldb], 0.0}, DD{-s.hi, -s.lo});
+  R[i + (size_t)j * ldr] = __dadd_rn(r.hi, r.lo);
+}
+
+// colsum[j] = sum_i |A(i, j)| (one warp per column)
+__global__ void __launch_bounds__(256) colsum_abs_kernel(int m, int n, const double *A, int lda, double *colsum) {
+  const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int i = lane; i < m; i += 32) s += fabs(A[i + (size_t)j * lda]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) colsum[j] = s;
+}
+
+// rowsum[i] = sum_j |A(i, j)|, i < m
+__global__ void rowsum_abs_rect_kernel(int m, int n, const double *A, int lda, double *rowsum) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int c = 0; c < n; ++c) s += fabs(A[i + (size_t)c * lda]);
+  rowsum[i] = s;
+}
+
+// S(j, c) = sum_i A(i, j) R(i, c): one warp per column j of A, lanes down the
+// rows (coalesced), every right-hand side accumulated per lane, then summed
+// across the warp in a fixed order
+__global__ void __launch_bounds__(kAtrWarps * 32) atr_kernel(int m, int n, int nrhs, const double *A, int lda,
+                                                             const double *R, int ldr, double *S, int lds,
+                                                             const int *skip) {
+  if (*skip) return;
+  const int j = blockIdx.x * kAtrWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (j >= n) return;
+  const double *a = A + (size_t)j * lda;
+  for (int c0 = 0; c0 < nrhs; c0 += kResMaxRhs) {
+    const int nc = min(kResMaxRhs, nrhs - c0);
+    double acc[kResMaxRhs];
+#pragma unroll
+    for (int c = 0; c < kResMaxRhs; ++c) acc[c] = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      const double v = a[i];
+#pragma unroll
+      for (int c = 0; c < kResMaxRhs; ++c)
+        if (c < nc) acc[c] = fma(v, R[i + (size_t)(c0 + c) * ldr], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kResMaxRhs; ++c) {
+      double v = acc[c];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0 && c < nc) S[j + (size_t)(c0 + c) * lds] = v;
+    }
+  }
+}
+
+// berr[c] = ||S_c||inf / (||A||_1 (||A||inf ||X_c||inf + ||B_c||inf)), one CTA per column
+__global__ void ls_berr_kernel(int m, int n, const double *S, int lds, const double *X, int ldx, const double *B,
+                               int ldb, const double *anorm, const double *a1, double *berr, const int *skip) {
+  if (*skip) return;
+  const int c = blockIdx.x;
+  double sv = 0.0, x = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sv = fmax(sv, fabs(S[i + (size_t)c * lds]));
+    x = fmax(x, fabs(X[i + (size_t)c * ldx]));
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) b = fmax(b, fabs(B[i + (size_t)c * ldb]));
+  sv = block_max(sv);
+  x = block_max(x);
+  b = block_max(b);
+  if (threadIdx.x == 0) {
+    const double den = a1[0] * (anorm[0] * x + b);
+    berr[c] = den > 0.0 ? sv / den : 0.0;
+  }
+}
+
+// Rt = R^T (n x n, the upper triangle of QR's top n rows, lower triangular)
+__global__ void transpose_upper_kernel(int n, const double *QR, int ldq, double *Rt, int ldt, const int *skip) {
+  __shared__ double t[32][33];
+  if (skip && *skip) return;
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 256 threads: 8 rows per pass
+  for (int r = ty; r < 32; r += 8) {
+    const int i = by + r, j = bx + tx;  // read R(i, j), i <= j
+    t[r][tx] = (i < n && j < n && i <= j) ? QR[i + (size_t)j * ldq] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bx + r, j = by + tx;  // write Rt(i, j) = R(j, i)
+    if (i < n && j < n) Rt[i + (size_t)j * ldt] = t[tx][r];
+  }
+}
+
+// dx = max_j ||D_j||inf / ||X_j||inf of the correction D just solved (one CTA)
+__global__ void ls_dxnorm_kernel(int n, int nrhs, const double *D, int ldd, const double *X, int ldx, IrCtl *ctl) {
+  if (ctl->done) return;
+  double best = 0.0;
+  for (int j = 0; j < nrhs; ++j) {
+    double d = 0.0, x = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      d = fmax(d, fabs(D[i + (size_t)j * ldd]));
+      x = fmax(x, fabs(X[i + (size_t)j * ldx]));
+    }
+    d = block_max(d);
+    x = block_max(x);
+    const double r = x > 0.0 ? d / x : d;
+    best = (r > best || r != r) ? r : best;
+  }
+  if (threadIdx.x == 0) ctl->dx = best;
+}
+
+// The stop test of least-squares step `it`: the optimality measure
+// ||A^T r|| / (||A||_1 (||A||inf ||x|| + ||b||)) alone can be tiny while the
+// components of x along small singular directions are still off (it weighs
+// them by sigma_min^2), so the loop runs until the corrections themselves
+// stop mattering: the last correction is below 4 unit roundoffs of x, or it
+// failed to halve twice in a row, or max_iter.  ok: the measure is <= tol.
+__global__ void ls_decide_kernel(int it, int max_iter, double tol, int nrhs, const double *berr, IrCtl *ctl,
+                                 double *berr_out, int *iters_out) {
+  if (ctl->done) return;
+  double be = 0.0;
+  for (int j = 0; j < nrhs; ++j) be = (berr[j] > be || berr[j] != berr[j]) ? berr[j] : be;
+  ctl->berr = be;
+  ctl->iters = it;
+  ctl->ok = be <= tol;
+  if (berr_out) *berr_out = be;
+  if (iters_out) *iters_out = ctl->iter_base + it;
+  bool stop = false;
+  if (it >= max_iter || !(be == be)) {
+    stop = true;
+  } else if (it > 0) {
+    const double dx = ctl->dx;
+    if (!(dx > 4.0 * 1.1102230246251565e-16)) {
+      stop = true;
+    } else if (dx > 0.5 * ctl->prev) {
+      if (++ctl->stall >= 2) stop = true;
+    } else {
+      ctl->stall = 0;
+    }
+    ctl->prev = dx;
+  } else if (be == 0.0) {
+    stop = true;
+  } else {
+    ctl->prev = 1e308;
+  }
+  ctl->done = stop ? 1 : 0;
+}
+
+size_t ls_ws_bytes(int m, int n, int nrhs) {
+  const int ncb = (n + kResCols - 1) / kResCols;
+  return align256((size_t)ncb * nrhs * m * 16) + align256((size_t)m * nrhs * 8) + align256((size_t)n * nrhs * 8) +
+         align256((size_t)n * n * 8) + align256((size_t)(m > n ? m : n) * 8) + 2 * align256(8) +
+         align256((size_t)nrhs * 8) + kIrPhases * align256(sizeof(IrCtl)) + align256(8) + 256;
+}
+
+void ls_ws_carve(void *ws, int m, int n, int nrhs, LsWs &w) {
+  const int ncb = (n + kResCols - 1) / kResCols;
+  char *p = (char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  w.partial = (double *)p;
+  p += align256((size_t)ncb * nrhs * m * 16);
+  w.R = (double *)p;
+  p += align256((size_t)m * nrhs * 8);
+  w.S = (double *)p;
+  p += align256((size_t)n * nrhs * 8);
+  w.Rt = (double *)p;
+  p += align256((size_t)n * n * 8);
+  w.sums = (double *)p;
+  p += align256((size_t)(m > n ? m : n) * 8);
+  w.anorm = (double *)p;
+  p += align256(8);
+  w.a1 = (double *)p;
+  p += align256(8);
+  w.berr = (double *)p;
+  p += align256((size_t)nrhs * 8);
+  for (int i = 0; i < kIrPhases; ++i) {
+    w.phase[i] = (IrCtl *)p;
+    p += align256(sizeof(IrCtl));
+  }
+  w.ctl = w.phase[0];
+  w.info2 = (int *)p;
+}
+
+cudaError_t ls_norms(int m, int n, const double *A, int lda, const LsWs &w, cudaStream_t st) {
+  ProfScope ps(kClsRefine, st, 2.0 * m * (double)n);
+  rowsum_abs_rect_kernel<<<(m + 255) / 256, 256, 0, st>>>(m, n, A, lda, w.sums);
+  max_kernel<<<1, 1024, 0, st>>>(m, w.sums, w.anorm);
+  colsum_abs_kernel<<<(n + 7) / 8, 256, 0, st>>>(m, n, A, lda, w.sums);
+  max_kernel<<<1, 1024, 0, st>>>(n, w.sums, w.a1);
+  return cudaGetLastError();
+}
+
+cudaError_t ls_residual(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx, const double *B,
+                        int ldb, const LsWs &w, cudaStream_t st) {
+  const int *skip = &w.ctl->done;
+  const int ncb = (n + kResCols - 1) / kResCols;
+  DD *part = (DD *)w.partial;
+  {
+    ProfScope ps(kClsRefine, st, 2.0 * m * (double)n * nrhs);
+    resid_partial_dd_kernel<<<dim3((m + kResRows - 1) / kResRows, ncb), kResRows, 0, st>>>(m, n, nrhs, A, lda, X,
+                                                                                            ldx, part, skip);
+  }
+  ProfScope ps(kClsRefine, st, 0.0);
+  const long long tot = (long long)m * nrhs;
+  resid_reduce_dd_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m, nrhs, ncb, part, B, ldb, w.R, m, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t ls_normal_residual(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx,
+                               const double *B, int ldb, const LsWs &w, cudaStream_t st) {
+  ProfScope ps(kClsRefine, st, 2.0 * m * (double)n * nrhs);
+  atr_kernel<<<(n + kAtrWarps - 1) / kAtrWarps, kAtrWarps * 32, 0, st>>>(m, n, nrhs, A, lda, w.R, m, w.S, n,
+                                                                         &w.ctl->done);
+  ls_berr_kernel<<<nrhs, 256, 0, st>>>(m, n, w.S, n, X, ldx, B, ldb, w.anorm, w.a1, w.berr, &w.ctl->done);
+  return cudaGetLastError();
+}
+
+cudaError_t ls_transpose_r(int n, const double *QR, int ldq, const LsWs &w, const int *skip, cudaStream_t st) {
+  ProfScope ps(kClsRefine, st, 0.0);
+  dim3 g((n + 31) / 32, (n + 31) / 32);
+  transpose_upper_kernel<<<g, 256, 0, st>>>(n, QR, ldq, w.Rt, n, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t ls_update(int n, int nrhs, const LsWs &w, double *X, int ldx, cudaStream_t st) {
+  {
+    ProfScope ps(kClsRefine, st, 0.0);
+    ls_dxnorm_kernel<<<1, 256, 0, st>>>(n, nrhs, w.S, n, X, ldx, w.ctl);
+  }
+  ProfScope ps(kClsRefine, st, (double)n * nrhs);
+  const long long tot = (long long)n * nrhs;
+  axpy_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, nrhs, w.S, n, X, ldx, &w.ctl->done);
+  return cudaGetLastError();
+}
+
+cudaError_t ls_decide(int it, int max_iter, double tol, int nrhs, const LsWs &w, double *berr_out, int *iters_out,
+                      cudaStream_t st) {
+  ProfScope ps(kClsRefine, st, 0.0);
+  ls_decide_kernel<<<1, 1, 0, st>>>(it, max_iter, tol, nrhs, w.berr, w.ctl, berr_out, iters_out);
+  return cudaGetLastError();
+}
+
+cudaError_t ls_begin(const LsWs &w, const IrCtl *prev, cudaStream_t st) {
+  ProfScope ps(kClsRefine, st, 0.0);
+  if (prev)
+    begin_next_kernel<<<1, 1, 0, st>>>(prev, w.ctl, 1e308);
+  else
+    begin_kernel<<<1, 1, 0, st>>>(w.ctl, 1e308);
+  return cudaGetLastError();
+}
+
+cudaError_t ls_merge_info(const LsWs &w, int *dev_info, cudaStream_t st) {
+  ProfScope ps(kClsRefine, st, 0.0);
+  merge_info_kernel<<<1, 1, 0, st>>>(w.ctl, w.info2, dev_info);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // GMRES on the preconditioned correction equation (M^-1 A) d = M^-1 r with
 // M = P^T L U the reduced-precision factors (GMRES-based iterative
 // refinement): x0 = 0, Arnoldi with classical Gram-Schmidt applied twice,

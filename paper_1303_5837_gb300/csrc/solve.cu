@@ -182,16 +182,20 @@ __global__ void __launch_bounds__(256, 1) trsv_flag_kernel(int n, int nrhs, cons
   }
   __syncthreads();
   if (lower) {
-    // unit lower: columns right to left; X(j+1:, j) = -X(j+1:, j+1:) T(j+1:, j)
+    // lower: columns right to left; X(j, j) = 1 / T(j, j) (1 when unit),
+    // X(j+1:, j) = -X(j+1:, j+1:) T(j+1:, j) X(j, j)
+    for (int i = tid; i < nb; i += blockDim.x) xj[i] = unit ? 1.0 : 1.0 / Ti[i + i * kLdI];
+    __syncthreads();
     for (int j = nb - 1; j >= 0; --j) {
+      const double djj = xj[j];
       for (int i = j + 1 + tid; i < nb; i += blockDim.x) {
         double acc = 0.0;
         for (int k = j + 1; k <= i; ++k) acc = fma(Ti[i + k * kLdI], Ti[k + j * kLdI], acc);
-        tmp[i] = -acc;
+        tmp[i] = -acc * djj;
       }
       __syncthreads();
       for (int i = j + 1 + tid; i < nb; i += blockDim.x) Ti[i + j * kLdI] = tmp[i];
-      if (tid == 0) Ti[j + j * kLdI] = 1.0;
+      if (tid == 0) Ti[j + j * kLdI] = djj;
       __syncthreads();
     }
   } else {

@@ -58,16 +58,16 @@ def footprint(kind: str, m: int, n: int, nrhs: int, b: int, tree, form: str = "f
         w = B.ca_calu_workspace(m, n, b, tree) + B.ca_getrs_workspace(n, nrhs)
         return mats + w + 4 * n + 4096
     if form == "mixed":
-        q, w = B.ca_caqr_mixed_workspace(m, n, b, tree, 7, True)
-    else:
-        q, w = B.ca_caqr_workspace(m, n, b, tree)
+        q, w = B.ca_gels_mixed_workspace(m, n, nrhs, b, tree, 4, True)
+        return mats + 8 * m * n + q + w + 4096
+    q, w = B.ca_caqr_workspace(m, n, b, tree)
     w = max(w, B.ca_geqrs_workspace(m, n, nrhs, b, tree))
     return mats + q + w + 4096
 
 
 class SolveServer:
-    """``form``: "fp64" (plain FP64 factorizations) or "mixed" (LU: tensor-core
-    update + FP64 refinement; LS: 7-digit tensor-core tree update)."""
+    """``form``: "fp64" (plain FP64 factorizations) or "mixed" (LU and least
+    squares: 4-digit tensor-core updates + FP64 refinement)."""
 
     def __init__(self, hbm_budget: int, slots: int = 4, b: int = 128, leaf_rows: int = 256,
                  levels=((4, 0), (0, 0)), form: str = "fp64", device: int = 0, execute=None):
@@ -280,8 +280,8 @@ def solve_request(r: Request, stream, form: str, b: int, tree, device: int, ref_
     sides to the device, the factorization and solve of the form ("fp64":
     calu_factor + calu_getrs / caqr_factor + caqr_geqrs; "mixed": LU by
     calu_gesv_mixed with 4 digits and automatic refinement, least squares by
-    the 7-digit tensor-core CAQR), the solution back to the host.  Raises
-    when the library reports a problem (check_result)."""
+    caqr_gels_mixed with 4 digits and refinement), the solution back to the
+    host.  Raises when the library reports a problem (check_result)."""
     import torch
     dev = torch.device("cuda", device)
     m, n = r.A.shape
@@ -302,11 +302,11 @@ def solve_request(r: Request, stream, form: str, b: int, tree, device: int, ref_
             swork = B._buf(B.ca_getrs_workspace(n, nrhs), dev)
             B.calu_getrs(A, ipiv, Bm, work=swork, stream=stream)
             X = Bm
+        elif form == "mixed":
+            X, it, berr, info = B.caqr_gels_mixed(A, Bm, b, tree, slices=4, exact=True, max_iter=10, tol=1e-14,
+                                                  stream=stream)
         else:
-            if form == "mixed":
-                qtree, info = B.caqr_factor_mixed(A, b, tree, slices=7, exact=True, stream=stream)
-            else:
-                qtree, info = B.caqr_factor(A, b, tree, stream=stream)
+            qtree, info = B.caqr_factor(A, b, tree, stream=stream)
             swork = B._buf(B.ca_geqrs_workspace(m, n, nrhs, b, tree), dev)
             B.caqr_geqrs(A, b, tree, qtree, Bm, work=swork, stream=stream)
             X = Bm[:n]

@@ -79,6 +79,16 @@ def test_argument_errors_without_gpu(lib):
     classic = ctypes.c_size_t()
     assert lib.ca_gesv_mixed_workspace(512, 1, 64, ctypes.byref(t), 4, 1, 0, ctypes.byref(classic)) == 0
     assert size.value > classic.value      # the GMRES correction's Krylov basis
+    # least squares: m < n, a bad tree, too many digits are argument errors
+    q = ctypes.c_size_t()
+    assert lib.ca_gels_mixed_workspace(10, 20, 1, 8, ctypes.byref(t), 4, 1, ctypes.byref(q),
+                                       ctypes.byref(size)) == -2
+    assert lib.ca_gels_mixed_workspace(1000, 300, 1, 64, ctypes.byref(B.make_tree(32)), 4, 1, ctypes.byref(q),
+                                       ctypes.byref(size)) == -5
+    assert lib.ca_gels_mixed_workspace(1000, 300, 1, 64, ctypes.byref(t), 9, 1, ctypes.byref(q),
+                                       ctypes.byref(size)) == -6
+    assert lib.ca_gels_mixed_workspace(1000, 300, 2, 64, ctypes.byref(t), 4, 1, ctypes.byref(q),
+                                       ctypes.byref(size)) == 0 and q.value > 0 and size.value > 0
 
 
 def test_workspace_matches_tree_counts(lib):

@@ -265,3 +265,39 @@ def test_caqr_mixed_geqrs(ca):
     ca.caqr_geqrs(Ad, b, t, qtree, Bd)
     torch.cuda.synchronize()
     check(solve_err(to_host(Bd)[:n], x_o), 1e-12)
+
+
+@pytest.mark.parametrize("m,n,cond,slices,noise", [(2048, 512, 1e4, 4, 0.0), (2048, 512, 1e4, 4, 1e-3),
+                                                   (3000, 700, 1e6, 4, 1e-6), (1500, 400, 1e2, 3, 1e-2)])
+def test_gels_mixed_refinement(ca, m, n, cond, slices, noise):
+    """Least squares after a reduced-digit CAQR, refined on the corrected
+    semi-normal equations: the stop measure (||A^T r|| over its scale)
+    reaches 1e-14 and the solution is the oracle's FP64 CAQR least-squares
+    solution within the sensitivity of the problem (cond eps, plus
+    cond^2 eps ||r|| / (||A|| ||x||) when b is not in the range of A)."""
+    g = np.random.default_rng(m + n)
+    U, _ = np.linalg.qr(g.standard_normal((m, n)))
+    V, _ = np.linalg.qr(g.standard_normal((n, n)))
+    s = cond ** (-np.arange(n) / (n - 1))
+    A = np.asfortranarray((U * s) @ V.T)
+    x_true = g.standard_normal((n, 2))
+    e = g.standard_normal((m, 2))
+    e -= U @ (U.T @ e)                             # orthogonal to range(A)
+    B = A @ x_true + noise * e / np.linalg.norm(e, axis=0) * np.linalg.norm(A @ x_true, axis=0)
+    b, L = 64, 256
+    t = oracle.make_tree(L, [(2, 0), (0, 0)])
+    QR_o, T_o = oracle.caqr(A, b, t)
+    x_o = oracle.geqrs(QR_o, T_o, b, t, B)
+    X, it, be, info = ca.caqr_gels_mixed(to_dev(A), to_dev(B), b, ca.make_tree(L, [(2, 0), (0, 0)]),
+                                         slices=slices, exact=True, max_iter=10, tol=1e-14)
+    torch.cuda.synchronize()
+    assert info.cpu().tolist() == [0, 0]
+    assert float(be.item()) <= 1e-14, (int(it.item()), float(be.item()))
+    x = to_host(X)
+    r = B - A @ x_o
+    sens = cond * 1e-15 + cond ** 2 * 1e-16 * np.linalg.norm(r) / (np.linalg.norm(A, 2) * np.linalg.norm(x_o))
+    assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) < max(1e-12, 100 * sens)
+    # the least-squares condition, in FP64 on the host
+    rr = B - A @ x
+    assert np.abs(A.T @ rr).max() / (np.abs(A).sum(0).max() * (np.abs(A).sum(1).max() * np.abs(x).max()
+                                                               + np.abs(B).max())) < 1e-14
