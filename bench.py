@@ -677,7 +677,9 @@ def run_ours(a, rank: int, world: int, local: int):
         return
     if a.only_batch:
         if a.only_batch == "ops":
-            print(json.dumps({"batched": {"operators": operator_diagnostics(a, ca, torch, dev)}}), flush=True)
+            print(json.dumps({"batched": {"operators": operator_diagnostics(a, ca, torch, dev),
+                                          "operators_8192": operator_diagnostics_large(a, ca, torch, dev)}}),
+                  flush=True)
             return
         out = batched_run(a, ca, torch, torch.float64 if a.only_batch == "f64" else torch.float32, dev, rank,
                           world)
@@ -810,6 +812,7 @@ def run_ours(a, rank: int, world: int, local: int):
             batched[tname] = batched_run(a, ca, torch, tdt, dev, rank, world)
         if rank == 0:
             batched["operators"] = operator_diagnostics(a, ca, torch, dev)
+            batched["operators_8192"] = operator_diagnostics_large(a, ca, torch, dev)
 
     # ---- the other configurations (tall-skinny panels, the small square) ----
     configs = None
@@ -1147,6 +1150,82 @@ def operator_diagnostics(a, ca, torch, dev, count=64, n=512):
                      "lmax_max": max(lmax), "tau_min": 1.0 / max(lmax),
                      "componentwise_berr_max": max(cberr),
                      "nonzero_info": int((bf.info_all != 0).sum())}
+    return out
+
+
+OPERATOR_FORMS_8192 = [  # (name, panel width, leaf rows, levels, reduction operator)
+    ("calu", 64, 256, [(0, 0)], []),
+    ("2d_ml_calu_depth1", 64, 256, [(0, 0)], [(32, 64)]),
+    ("2d_ml_calu_depth2", 64, 256, [(0, 0)], [(32, 64), (8, 16)]),
+]
+
+
+def operator_diagnostics_large(a, ca, torch, dev, n=8192):
+    """The stability experiment of the multilevel CALU (Sec. 5.1) at the
+    paper's order n = 8192 with its block sizes b = 64 / 32 / 8, in the
+    single-matrix path (calu_factor): leaves of 256 rows under a binary tree
+    (the paper's Pr3 = 16 leaves of 512 rows do not fit one CTA's shared
+    memory), each node factored by CALU with b = 32 over 4 row blocks of 64
+    (depth 1), whose nodes are factored by CALU with b = 8 over 4 blocks of 16
+    (depth 2).  For each synthetic family (Gaussian N(0,1); A = U diag(s) V^T
+    with cond 1e8, Haar U, V): growth max|U| / max|A|, ||P A - L U||_F /
+    ||A||_F, tau_min = 1 / max|L| and the componentwise backward error of a
+    solve, each also as a ratio to GEPP (torch.linalg.lu_factor, a library
+    LU used here only as the reference of the ratios)."""
+    from paper_1303_5837_gb300 import inputs
+    out = {"n": n, "forms": {f[0]: {"b": f[1], "leaf_rows": f[2], "operator": f[4]} for f in OPERATOR_FORMS_8192}}
+    g = torch.Generator(device=dev).manual_seed(58)
+    fams = {"gaussian": torch.randn(n, n, dtype=torch.float64, device=dev, generator=g).t().contiguous().t()}
+    U, V = haar_device(n, 59, dev), haar_device(n, 60, dev)
+    s_ = torch.from_numpy(inputs.singular_values(n, 1e8)).to(dev)
+    fams["cond1e8"] = ((U * s_) @ V.t()).t().contiguous().t()
+    del U, V
+    xt = torch.ones(n, 1, dtype=torch.float64, device=dev)
+
+    def metrics(A, LU, perm):
+        Lf = torch.tril(LU, -1) + torch.eye(n, dtype=LU.dtype, device=dev)
+        Uf = torch.triu(LU)
+        res = {"growth": float(Uf.abs().max() / A.abs().max()),
+               "berr": float(torch.linalg.norm(A[perm] - Lf @ Uf) / torch.linalg.norm(A)),
+               "tau_min": float(1.0 / Lf.abs().max())}
+        bb = A @ xt
+        y = torch.linalg.solve_triangular(Lf, bb[perm], upper=False, unitriangular=True)
+        x = torch.linalg.solve_triangular(Uf, y, upper=True)
+        res["componentwise_berr"] = float(((bb - A @ x).abs() / (A.abs() @ x.abs() + bb.abs())).max())
+        return res
+
+    def perm_of(ipiv):
+        perm = np.arange(n)
+        for i, p in enumerate(ipiv.cpu().numpy()):
+            perm[i], perm[p - 1] = perm[p - 1], perm[i]
+        return torch.from_numpy(perm).to(dev)
+
+    for fname, A in fams.items():
+        row = {}
+        LUg, piv = torch.linalg.lu_factor(A)
+        ref = metrics(A, LUg, perm_of(piv))
+        row["gepp"] = ref
+        del LUg
+        for name, b, L, lv, op in OPERATOR_FORMS_8192:
+            F = A.clone()
+            t = ca.make_tree(L, lv, op)
+            ca.calu_factor(F, b, t)  # warm-up of the shapes
+            F.copy_(A)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ipiv, info = ca.calu_factor(F, b, t)
+            e1.record()
+            e1.synchronize()
+            r = metrics(A, F, perm_of(ipiv))
+            r["ms"] = e0.elapsed_time(e1)
+            r["info"] = info.cpu().tolist()
+            for k in ("growth", "berr", "componentwise_berr"):
+                r[k + "_ratio_to_gepp"] = r[k] / ref[k] if ref[k] > 0 else None
+            row[name] = r
+            del F
+        out[fname] = row
+        torch.cuda.empty_cache()
     return out
 
 

@@ -74,8 +74,12 @@ typedef struct {
    * tree; its own nodes use GEPP (depth 1) or, at depth 2, CALU with
    * op_b[1] and op_leaf_rows[1] and GEPP below that.  The node's pivot rows
    * are the first rows of that factorization.  Zero-initialize for GEPP.
-   * Only the batched entry points (CALU items) accept depth > 0; the others
-   * return CA_ERR_UNSUPPORTED. */
+   * The LU entry points (calu_factor, tslu, the mixed forms, batched CALU
+   * items) accept depth 1 or 2 when every tournament node (leaf_rows rows,
+   * or fan-in x panel width rows) has at most 1024 rows and its tile with
+   * the operator's scratch tiles fits one CTA's shared memory (about
+   * 220 KB in FP64: 256 x 64 leaves, for instance); each node is then
+   * factored by one CTA.  QR entry points return CA_ERR_UNSUPPORTED. */
   int op_depth;
   int op_b[2];                /* 1 <= op_b[d] <= op_leaf_rows[d]              */
   int op_leaf_rows[2];

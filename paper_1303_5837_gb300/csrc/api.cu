@@ -60,7 +60,7 @@ int lu_shape(int m, int n, int b, const ca_tree_t *tree, int *nl_max) {
   if (n < 0) return -2;
   if (b < 1) return -5;
   if (check_tree(tree, b)) return -6;
-  if (tree->op_depth != 0) return CA_ERR_UNSUPPORTED;  // the 2D operator runs in the batched path
+  if (tree->op_depth != 0 && !op_params_ok(*tree)) return -6;  // the 2D operator's levels
   int K = m < n ? m : n;
   *nl_max = 1;
   if (K == 0) return CA_OK;
@@ -69,9 +69,17 @@ int lu_shape(int m, int n, int b, const ca_tree_t *tree, int *nl_max) {
   int nl = nleaves_of(m, tree->leaf_rows);
   Plan p;
   if (!build_plan(nl, *tree, p)) return CA_ERR_TREE;
-  if (!lu_node_feasible(max_node_rows(p, m, tree->leaf_rows, bk), bk)) return CA_ERR_UNSUPPORTED;
+  const int rows = max_node_rows(p, m, tree->leaf_rows, bk);
+  if (tree->op_depth != 0 ? !op_node_feasible(rows, bk, *tree) : !lu_node_feasible(rows, bk))
+    return CA_ERR_UNSUPPORTED;
   *nl_max = nl;
   return CA_OK;
+}
+
+// CALU panel workspace: the tournament buffers, then (2D operator) the
+// operator's candidate buffers of every node of a round
+size_t lu_ws_bytes(int nl, int bw, const ca_tree_t *tree) {
+  return align256(lu_panel_ws_bytes(nl, bw)) + op_ws_bytes(nl, *tree);
 }
 
 int qr_shape(int m, int n, int b, const ca_tree_t *tree, int *nl_max, size_t *qbytes) {
@@ -147,6 +155,7 @@ int calu_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int
   const int bw = b < kMaxB ? b : kMaxB;
   LuPanelWs ws;
   lu_panel_ws_carve(work, nl, bw, ws);
+  int *opws = (int *)((char *)work + align256(lu_panel_ws_bytes(nl, bw)));
   const int L = tree->leaf_rows;
   Lookahead *la = (K > b) ? lookahead_for(stream) : nullptr;
   if (la && cudaEventRecord(la->ev_next, stream) != cudaSuccess) return CA_ERR_LAUNCH;
@@ -167,8 +176,10 @@ int calu_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int
     cudaStream_t ps = la ? la->helper : stream;
     if (la && cudaStreamWaitEvent(ps, la->ev_next, 0) != cudaSuccess) return CA_ERR_LAUNCH;
     // 1. tournament pivoting over the tree (TSLU)
-    if (tslu_panel(mk, bk, P, lda, L, plan, ws, ipiv + kb, kb, dev_info, ps, skip) != cudaSuccess)
-      return CA_ERR_LAUNCH;
+    const cudaError_t te = tree->op_depth != 0
+                               ? tslu_panel_op(mk, bk, P, lda, *tree, plan, ws, opws, ipiv + kb, kb, dev_info, ps, skip)
+                               : tslu_panel(mk, bk, P, lda, L, plan, ws, ipiv + kb, kb, dev_info, ps, skip);
+    if (te != cudaSuccess) return CA_ERR_LAUNCH;
     if (la && (cudaEventRecord(la->ev_panel, ps) != cudaSuccess ||
                cudaStreamWaitEvent(stream, la->ev_panel, 0) != cudaSuccess))
       return CA_ERR_LAUNCH;
@@ -271,9 +282,9 @@ size_t caqr_mixed_ws(int m, int n, int b, const ca_tree_t *tree, int nl, int sli
          tree_tc_ws_bytes(m, bk, n - bk > 0 ? n - bk : 1, tree->leaf_rows, nl, slices);
 }
 
-size_t calu_mixed_ws(int m, int n, int b, int nl, int slices) {
+size_t calu_mixed_ws(int m, int n, int b, const ca_tree_t *tree, int nl, int slices) {
   const int bw = b < kMaxB ? b : kMaxB;
-  return align256(lu_panel_ws_bytes(nl, bw)) + tc_gemm_ws_bytes(m, n, bw, slices);
+  return align256(lu_ws_bytes(nl, bw, tree)) + tc_gemm_ws_bytes(m, n, bw, slices);
 }
 
 }  // namespace
@@ -307,7 +318,7 @@ int ca_calu_workspace(int m, int n, int b, const ca_tree_t *tree, size_t *work_b
   int rc = lu_shape(m, n, b, tree, &nl);
   if (rc == -5 || rc == -6) rc = (rc == -5) ? -3 : -4;  // positions in this call
   if (rc != CA_OK) return rc;
-  *work_bytes = lu_panel_ws_bytes(nl, b < kMaxB ? b : kMaxB);
+  *work_bytes = lu_ws_bytes(nl, b < kMaxB ? b : kMaxB, tree);
   return CA_OK;
 }
 
@@ -356,7 +367,7 @@ int calu_factor(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, 
   if (K > 0 && !ipiv) return -7;
   if (!dev_info) return -10;
   const int bw = b < kMaxB ? b : kMaxB;
-  if (K > 0 && (!work || lwork < lu_panel_ws_bytes(nl, bw))) return CA_ERR_WORKSPACE;
+  if (K > 0 && (!work || lwork < lu_ws_bytes(nl, bw, tree))) return CA_ERR_WORKSPACE;
   return calu_run(m, n, A, lda, b, tree, ipiv, work, nl, nullptr, 0, 0, dev_info, stream);
 }
 
@@ -509,7 +520,7 @@ int ca_calu_mixed_workspace(int m, int n, int b, const ca_tree_t *tree, int slic
   if (slices < 1 || slices > 8) return -5;
   if (!tc_gemm_supported(b < kMaxB ? b : kMaxB, slices, exact)) return CA_ERR_UNSUPPORTED;
   if (!work_bytes) return -7;
-  *work_bytes = calu_mixed_ws(m, n, b, nl, slices);
+  *work_bytes = calu_mixed_ws(m, n, b, tree, nl, slices);
   return CA_OK;
 }
 
@@ -525,10 +536,10 @@ int calu_factor_mixed(int m, int n, double *A, int lda, int b, const ca_tree_t *
   if (!tc_gemm_supported(b < kMaxB ? b : kMaxB, slices, exact)) return CA_ERR_UNSUPPORTED;
   if (K > 0 && !ipiv) return -9;
   if (!dev_info) return -12;
-  const size_t need = calu_mixed_ws(m, n, b, nl, slices);
+  const size_t need = calu_mixed_ws(m, n, b, tree, nl, slices);
   if (K > 0 && (!work || lwork < need)) return CA_ERR_WORKSPACE;
   const int bw = b < kMaxB ? b : kMaxB;
-  char *tcws = (char *)work + align256(lu_panel_ws_bytes(nl, bw));
+  char *tcws = (char *)work + align256(lu_ws_bytes(nl, bw, tree));
   return calu_run(m, n, A, lda, b, tree, ipiv, work, nl, tcws, slices, exact, dev_info, stream);
 }
 
@@ -560,7 +571,6 @@ int calu_gesv_mixed(int n, int nrhs, const double *A, int lda, int b, const ca_t
   if (lda < (n > 1 ? n : 1)) return -4;
   if (b < 1) return -5;
   if (check_tree(tree, b)) return -6;
-  if (tree->op_depth != 0) return CA_ERR_UNSUPPORTED;
   if (slices < 1 || slices > 8) return -7;
   if (refine < CA_REFINE_CLASSIC || refine > CA_REFINE_AUTO) return -9;
   if (n > 0 && !LU) return -10;
@@ -660,7 +670,7 @@ int calu_gesv_mixed(int n, int nrhs, const double *A, int lda, int b, const ca_t
   int nl = 1;
   if (lu_shape(n, n, b, tree, &nl) != CA_OK) return CA_ERR_UNSUPPORTED;
   const int bw = b < kMaxB ? b : kMaxB;
-  char *tcws = (char *)work + align256(lu_panel_ws_bytes(nl, bw));
+  char *tcws = (char *)work + align256(lu_ws_bytes(nl, bw, tree));
   if (copy_matrix(n, n, A, lda, LU, ldlu, noref, stream) != cudaSuccess) return CA_ERR_LAUNCH;
   if ((rc = calu_run(n, n, LU, ldlu, b, tree, ipiv, work, nl, tcws, 7, 1, iw.info2, stream, noref)) != CA_OK)
     return rc;

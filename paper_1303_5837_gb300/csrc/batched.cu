@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "ca_internal.cuh"
+#include "device_once.cuh"
 
 namespace cagb {
 namespace {
@@ -1179,7 +1180,230 @@ int item_needs(const ca_batch_item_t &it, size_t esz, size_t region_cap, size_t 
   return 1;
 }
 
+// ---------------------------------------------------------------------------
+// The 2D multilevel reduction operator in the single-matrix CALU
+// (calu_factor with op_depth 1 or 2): one CTA per tournament node of a
+// round; the node's rows (a leaf, or the stacked candidate sets of its
+// children) are loaded into the CTA's shared memory and factored by node_op
+// -- the same code as the batched path -- and the node's first min(rows, bk)
+// labels are its candidates.  The root also writes L11 \ U11 of its
+// selected rows and the panel's swap sequence, as tslu_node_kernel does for
+// GEPP nodes.
+// ---------------------------------------------------------------------------
+struct OpNodeArgs {
+  const double *P;
+  int lda, mk, bk, leaf_rows;
+  int is_leaf, is_root;
+  RoundDesc rd;
+  const int *cand_in, *ncand_in;
+  int *cand_out, *ncand_out;
+  int cand_ld;
+  double *lu11;
+  int ldl;
+  int *perm_src, *perm_dst, *perm_cnt, *ipiv_k;
+  int ipiv_base;
+  int *dev_info;
+  const int *skip;
+  ca_tree_t tree;
+  int *opws;           // the operator's candidate buffers, opws_stride ints per node
+  long long opws_stride;
+};
+
+__global__ void __launch_bounds__(kBT, 1) op_node_kernel(OpNodeArgs a) {
+  extern __shared__ __align__(16) char smem_op[];
+  if (a.skip && *a.skip) return;
+  Fixed<double> &F = *reinterpret_cast<Fixed<double> *>(smem_op);
+  double *R = reinterpret_cast<double *>(smem_op + fixed_bytes(CA_DTYPE_F64));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int node = blockIdx.x, bk = a.bk;
+  int rows;
+  if (a.is_leaf) {
+    const int r0 = node * a.leaf_rows;
+    rows = min(a.leaf_rows, a.mk - r0);
+    for (int p = tid; p < rows; p += kBT) F.prow[p] = r0 + p;
+  } else {
+    int start, cnt, midx;
+    round_node(a.rd, node, start, cnt, midx);
+    if (cnt == 1) {  // promotion
+      const int c = a.ncand_in[start];
+      for (int p = tid; p < c; p += kBT) a.cand_out[(size_t)node * a.cand_ld + p] = a.cand_in[(size_t)start * a.cand_ld + p];
+      if (tid == 0) a.ncand_out[node] = c;
+      return;
+    }
+    rows = 0;
+    for (int ch = 0; ch < cnt; ++ch) rows += a.ncand_in[start + ch];
+    for (int p = tid; p < rows; p += kBT) {
+      int off = 0, ch = 0;
+      while (p >= off + a.ncand_in[start + ch]) off += a.ncand_in[start + ch++];
+      F.prow[p] = a.cand_in[(size_t)(start + ch) * a.cand_ld + (p - off)];
+    }
+  }
+  if (tid == 0) {
+    F.info0 = 0;
+    F.status = 0;
+  }
+  __syncthreads();
+  const int ld = odd_ld(rows);
+  load_rows<double>(a.P, a.lda, rows, bk, R, ld, F, false);
+  const int km = node_op<double>(R, ld, rows, bk, F, a.is_root != 0, a.ipiv_base, a.tree,
+                                 a.opws + (size_t)node * a.opws_stride);
+  int *co = a.cand_out + (size_t)node * a.cand_ld;
+  for (int p = tid; p < km; p += kBT) co[p] = F.prow[p];
+  if (tid == 0) {
+    a.ncand_out[node] = km;
+    if (F.status && a.dev_info) atomicOr(a.dev_info + 1, F.status);
+  }
+  if (!a.is_root) return;
+  if (tid == 0 && F.info0 && a.dev_info) atomicCAS(a.dev_info, 0, F.info0);
+  for (int k = warp; k < bk; k += kBW)
+    for (int p = lane; p < bk; p += 32) a.lu11[p + (size_t)k * a.ldl] = R[p + (size_t)k * ld];
+  __syncthreads();
+  if (tid != 0) return;
+  // LAPACK swap sequence moving the root's rows (in selection order) to the
+  // top of the panel, and the panel's net row permutation
+  for (int t = 0; t < bk; ++t) {
+    F.sel[t] = F.prow[t];
+    F.rev_top[t] = t;
+    F.top_c[t] = t;
+    F.far_c[t] = F.sel[t];
+  }
+  for (int i = 0; i < bk; ++i) {
+    const int L = F.sel[i];
+    int pp, fslot = -1;
+    if (L < bk) {
+      const int rr = F.rev_top[L];
+      if (rr >= 0) {
+        pp = rr;
+      } else {
+        fslot = -rr - 1;
+        pp = F.sel[fslot];
+      }
+    } else {
+      pp = L;
+      fslot = i;
+    }
+    a.ipiv_k[i] = a.ipiv_base + pp + 1;
+    if (pp == i) continue;
+    const int ci = F.top_c[i];
+    F.top_c[i] = L;
+    if (pp < bk) {
+      F.top_c[pp] = ci;
+      F.rev_top[ci] = pp;
+    } else {
+      F.far_c[fslot] = ci;
+      F.rev_top[ci] = -(fslot + 1);
+    }
+    if (L < bk) F.rev_top[L] = i;
+  }
+  int n = 0;
+  for (int t = 0; t < bk; ++t)
+    if (F.top_c[t] != t) {
+      a.perm_dst[n] = t;
+      a.perm_src[n] = F.top_c[t];
+      ++n;
+    }
+  for (int t = 0; t < bk; ++t)
+    if (F.sel[t] >= bk) {
+      a.perm_dst[n] = F.sel[t];
+      a.perm_src[n] = F.far_c[t];
+      ++n;
+    }
+  *a.perm_cnt = n;
+}
+
+// shared-memory elements of a node tile of `rows` x bk with the operator's
+// scratch tiles below it (as item_needs)
+size_t op_node_elems(int rows, int bk, const ca_tree_t &t) {
+  size_t scr = 0;
+  int pr = rows, pw = bk;
+  for (int d = 0; d < t.op_depth; ++d) {
+    const int w = std::min(t.op_b[d], pw);
+    const int r = std::min(std::max(t.op_leaf_rows[d], 2 * w), pr);
+    scr += (size_t)odd_ld(r) * w;
+    pr = r;
+    pw = w;
+  }
+  return (size_t)odd_ld(rows) * bk + scr;
+}
+
+constexpr size_t kOpSmemCap = 227 * 1024 - 1024;
+
 }  // namespace
+
+bool op_params_ok(const ca_tree_t &t) {
+  if (t.op_depth < 1 || t.op_depth > 2) return false;
+  for (int d = 0; d < t.op_depth; ++d)
+    if (t.op_b[d] < 1 || t.op_b[d] > kBMaxB || t.op_leaf_rows[d] < t.op_b[d] || t.op_leaf_rows[d] > kBMaxRows)
+      return false;
+  return true;
+}
+
+bool op_node_feasible(int rows, int bk, const ca_tree_t &t) {
+  if (rows > kBMaxRows || bk > kBMaxB || !op_params_ok(t)) return false;
+  return fixed_bytes(CA_DTYPE_F64) + op_node_elems(rows, bk, t) * 8 <= kOpSmemCap;
+}
+
+size_t op_ws_bytes(int nodes, const ca_tree_t &t) {
+  if (t.op_depth < 1) return 0;
+  return align256((size_t)nodes * kOpCand * t.op_depth * 4);
+}
+
+cudaError_t tslu_panel_op(int mk, int bk, double *P, int lda, const ca_tree_t &tree, const Plan &plan,
+                          const LuPanelWs &ws, int *opws, int *ipiv_k, int ipiv_base, int *dev_info,
+                          cudaStream_t st, const int *skip) {
+  static std::atomic<unsigned long long> init{0};
+  cudaError_t e = once_per_device(init, [] {
+    return cudaFuncSetAttribute(op_node_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOpSmemCap);
+  });
+  if (e != cudaSuccess) return e;
+  OpNodeArgs a = {};
+  a.P = P;
+  a.lda = lda;
+  a.mk = mk;
+  a.bk = bk;
+  a.leaf_rows = tree.leaf_rows;
+  a.cand_ld = bk;
+  a.lu11 = ws.lu11;
+  a.ldl = bk;
+  a.perm_src = ws.perm_src;
+  a.perm_dst = ws.perm_dst;
+  a.perm_cnt = ws.perm_cnt;
+  a.ipiv_k = ipiv_k;
+  a.ipiv_base = ipiv_base;
+  a.dev_info = dev_info;
+  a.skip = skip;
+  a.tree = tree;
+  a.opws = opws;
+  a.opws_stride = (long long)kOpCand * tree.op_depth;
+  auto launch = [&](int nodes, int rows) -> cudaError_t {
+    const size_t smem = fixed_bytes(CA_DTYPE_F64) + op_node_elems(rows, bk, tree) * 8;
+    if (smem > kOpSmemCap) return cudaErrorInvalidValue;
+    ProfScope ps(kClsTsluNode, st, 0.0);
+    op_node_kernel<<<nodes, kBT, smem, st>>>(a);
+    return cudaGetLastError();
+  };
+  a.is_leaf = 1;
+  a.is_root = plan.nrounds == 0;
+  a.cand_in = nullptr;
+  a.ncand_in = nullptr;
+  a.cand_out = ws.cand[0];
+  a.ncand_out = ws.ncand[0];
+  if ((e = launch(plan.nleaves, std::min(tree.leaf_rows, mk))) != cudaSuccess) return e;
+  int buf = 0;
+  for (int r = 0; r < plan.nrounds; ++r) {
+    a.is_leaf = 0;
+    a.is_root = (r == plan.nrounds - 1);
+    a.rd = plan.r[r];
+    a.cand_in = ws.cand[buf];
+    a.ncand_in = ws.ncand[buf];
+    a.cand_out = ws.cand[buf ^ 1];
+    a.ncand_out = ws.ncand[buf ^ 1];
+    if ((e = launch(plan.r[r].n_out, plan.r[r].max_cnt * bk)) != cudaSuccess) return e;
+    buf ^= 1;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace cagb
 
 using namespace cagb;

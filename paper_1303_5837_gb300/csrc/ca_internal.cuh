@@ -224,6 +224,14 @@ cudaError_t tslu_panel(int mk, int bk, double *P, int lda, int leaf_rows, const 
                        cudaStream_t st, const int *skip = nullptr);
 cudaError_t laswp_apply(int ncols, double *A, int lda, int row0, const LuPanelWs &ws, int bk,
                         cudaStream_t st, const int *skip = nullptr);
+// the tournament with the 2D multilevel operator (batched.cu): one CTA per
+// node, the node factored in shared memory by CALU of the levels below
+bool op_params_ok(const ca_tree_t &t);
+bool op_node_feasible(int rows, int bk, const ca_tree_t &t);
+size_t op_ws_bytes(int nodes, const ca_tree_t &t);
+cudaError_t tslu_panel_op(int mk, int bk, double *P, int lda, const ca_tree_t &tree, const Plan &plan,
+                          const LuPanelWs &ws, int *opws, int *ipiv_k, int ipiv_base, int *dev_info,
+                          cudaStream_t st, const int *skip = nullptr);
 cudaError_t lu_panel_finish(int mk, int bk, double *P, int lda, const LuPanelWs &ws,
                             cudaStream_t st, const int *skip = nullptr);
 cudaError_t trsm_u12(int bk, int nt, const double *L11, int ldl, double *A12, int lda,

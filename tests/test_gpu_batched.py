@@ -270,10 +270,10 @@ def test_batched_2d_operator_matches_oracle(ca):
     assert not torch.equal(plain.ipiv(0), bf.ipiv(2))
 
 
-def test_batched_2d_operator_rejected_elsewhere(ca):
+def test_batched_2d_operator_rejected_for_qr(ca):
     t = ca.make_tree(64, op=[(8, 16)])
     A = to_dev(inputs.gaussian(128, 128, 1))
     with pytest.raises(ca.CaError):
-        ca.calu_factor(A, 32, t)
+        ca.caqr_factor(A, 32, t)
     with pytest.raises(ca.CaError):
         ca.BatchedFactor([A], ["qr"], [32], [t])

@@ -91,6 +91,36 @@ def test_calu_parity(ca, m, n, b, L, tname):
     check(lu_err(to_host(Ad), LU_o), TOL)
 
 
+# (m, n, b, leaf_rows, levels, operator): the 2D multilevel operator in the
+# single-matrix path (one CTA per tournament node), matrices far larger than
+# one CTA, several panels, ragged sizes
+OP_SINGLE = [
+    (1024, 1024, 64, 256, [(0, 0)], [(32, 64)]),
+    (1500, 1200, 64, 256, [(4, 1), (0, 0)], [(32, 64), (8, 16)]),
+    (3000, 200, 64, 128, [(0, 0)], [(16, 32)]),
+    (2048, 2048, 64, 256, [(0, 0)], [(32, 64), (8, 16)]),
+]
+
+
+@pytest.mark.parametrize("m,n,b,L,lv,op", OP_SINGLE)
+def test_calu_2d_operator_single_matrix(ca, m, n, b, L, lv, op):
+    """calu_factor with the 2D multilevel reduction operator (Algorithm
+    2D-ML-CALU, depth 1 and 2) against the oracle's node_factor: pivots
+    exactly, every factor element within 1e-12 of its rounding scale; the
+    operator changes the pivots of plain CALU on the same tree."""
+    A = inputs.gaussian(m, n, 31 * m + n)
+    LU_o, ipiv_o, info_o, nt = oracle.calu(A, b, oracle.make_tree(L, lv, op))
+    assert nt == 0
+    Ad = to_dev(A)
+    ipiv, info = ca.calu_factor(Ad, b, ca.make_tree(L, lv, op))
+    torch.cuda.synchronize()
+    assert info.cpu().tolist() == [info_o, 0]
+    assert np.array_equal(ipiv.cpu().numpy(), ipiv_o)
+    check(lu_err(to_host(Ad), LU_o), TOL, (m, n, b, op))
+    _, ipiv_plain, _, _ = oracle.calu(A, b, oracle.make_tree(L, lv))
+    assert not np.array_equal(ipiv_plain, ipiv_o)
+
+
 def test_calu_zero_column_info(ca):
     A = inputs.gaussian(256, 256, 3)
     A[:, 70] = 0.0
