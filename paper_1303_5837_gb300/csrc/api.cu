@@ -190,18 +190,21 @@ int calu_run(int m, int n, double *A, int lda, int b, const ca_tree_t *tree, int
     const int nt = n - kb - bk;
     if (nt > 0) {
       double *A12 = A + kb + (size_t)(kb + bk) * lda;
-      // 4. U12 = L11^-1 A12
-      if (trsm_u12(bk, nt, ws.lu11, bk, A12, lda, stream, skip) != cudaSuccess) return CA_ERR_LAUNCH;
-      // 5. A22 -= L21 U12: first the next panel's columns, then the rest
-      //    (the next tournament starts in between)
+      // 4. U12 = L11^-1 A12 and 5. A22 -= L21 U12: first the next panel's
+      //    columns (the next tournament starts as soon as they are done),
+      //    then the rest; every column's result is the same either way.  L11
+      //    is read from its place in A: the workspace copy belongs to the
+      //    next panel's tournament once it has started.
       const int nnext = (kb + bk < K) ? ((K - kb - bk < b) ? K - kb - bk : b) : 0;
       if (la && nnext > 0 && nnext < nt) {
+        if (trsm_u12(bk, nnext, P, lda, A12, lda, stream, skip) != cudaSuccess) return CA_ERR_LAUNCH;
         if (update(mk - bk, nnext, bk, P + bk, A12, A12 + bk) != cudaSuccess) return CA_ERR_LAUNCH;
         if (cudaEventRecord(la->ev_next, stream) != cudaSuccess) return CA_ERR_LAUNCH;
-        if (update(mk - bk, nt - nnext, bk, P + bk, A12 + (size_t)nnext * lda, A12 + bk + (size_t)nnext * lda) !=
-            cudaSuccess)
-          return CA_ERR_LAUNCH;
+        double *A12r = A12 + (size_t)nnext * lda;
+        if (trsm_u12(bk, nt - nnext, P, lda, A12r, lda, stream, skip) != cudaSuccess) return CA_ERR_LAUNCH;
+        if (update(mk - bk, nt - nnext, bk, P + bk, A12r, A12r + bk) != cudaSuccess) return CA_ERR_LAUNCH;
       } else {
+        if (trsm_u12(bk, nt, P, lda, A12, lda, stream, skip) != cudaSuccess) return CA_ERR_LAUNCH;
         if (update(mk - bk, nt, bk, P + bk, A12, A12 + bk) != cudaSuccess) return CA_ERR_LAUNCH;
         if (la && cudaEventRecord(la->ev_next, stream) != cudaSuccess) return CA_ERR_LAUNCH;
       }

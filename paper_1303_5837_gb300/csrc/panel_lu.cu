@@ -54,11 +54,17 @@ struct TsluSmem {
   double *scal;     // [0] = 1 / pivot
   int *iscal;       // [0] pivot pos, [1] pivot label, [2] label at j, [3] zero column
   int *work;        // 4 * bk ints (root permutation bookkeeping)
+  // published for the peers of the cluster, double-buffered by step parity:
+  ArgMax *pkey;     // [2] this CTA's best position of the next column
+  double *prow_pub; // [2][bk] that row (every column, as after the step's update)
+  double *jrow_pub; // [2][bk] the row at the next diagonal position (its owner only)
+  int *plab;        // [2] label of the published best row; [2 + q] label of the published diagonal row
 };
 
 __host__ __device__ inline size_t tslu_smem_bytes(int rloc, int bk) {
   size_t s = (size_t)(rloc | 1) * bk * 8 + 2 * (size_t)bk * 8;
   s += (size_t)rloc * 4 + 16 * (kNodeWarps + 1) + 16 * 8 + 16 + 16 + 4 * (size_t)bk * 4 + 64;
+  s += 2 * 16 + 4 * (size_t)bk * 8 + 16 + 64;  // published keys, rows and labels
   return s;
 }
 
@@ -83,8 +89,23 @@ __device__ inline TsluSmem tslu_carve(char *base, int rloc, int bk) {
   s.lab = (int *)base;
   base += (size_t)rloc * 4;
   s.work = (int *)base;
+  base += 4 * (size_t)bk * 4;
+  base = (char *)(((uintptr_t)base + 15) & ~(uintptr_t)15);
+  s.pkey = (ArgMax *)base;
+  base += 2 * 16;
+  s.prow_pub = (double *)base;
+  base += 2 * (size_t)bk * 8;
+  s.jrow_pub = (double *)base;
+  base += 2 * (size_t)bk * 8;
+  s.plab = (int *)base;
   return s;
 }
+
+// Split cluster barrier: arrive (release: this CTA's shared-memory writes
+// become visible to the peers' reads after their wait), then wait (acquire).
+// Every thread of every CTA of the cluster executes both, in the same order.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 // Cluster-wide barrier (a plain CTA barrier when the cluster has one CTA).
 __device__ __forceinline__ void node_sync(cg::cluster_group &cl, int G) {
@@ -163,81 +184,118 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
   __syncthreads();
 
   // ---- GEPP on the distributed tile ------------------------------------
+  // One cluster barrier per column.  At the end of step j-1 every CTA has
+  // published its best position of column j with that row's values (its
+  // columns beyond j computed on the fly exactly as the step's update
+  // computes them), and the owner of position j has published the row there;
+  // step j reads the G keys, takes the pivot row (and, at the pivot's owner,
+  // the row at j) from the peers' published copies, swaps locally, scales
+  // column j, updates column j + 1, finds and publishes column j + 1's best
+  // row, arrives at the barrier, and only then updates columns j + 2.. while
+  // the peers catch up.  The published copies of step j are overwritten two
+  // steps later, after a barrier every reader has passed.
   const int kmax = min(R, bk);
-  for (int j = 0; j < kmax; ++j) {
-    // (a) local argmax over positions >= j of column j
+  // local best of column c over positions >= c (valid rows of this CTA);
+  // publishes it (and, at the owner, the row at position c) into buffer q
+  auto find_and_publish = [&](int c, int q, bool upd, int jprev) {
     ArgMax best{0ull, INT_MAX};
-    const int i0 = max(j - p0, 0);
-    const double *colj = s.tile + (size_t)j * ldt;
+    const int i0 = max(c - p0, 0);
+    const double *colc = s.tile + (size_t)c * ldt;
     for (int i = i0 + tid; i < myrows; i += kNodeThreads)
-      best = argmax_better(best, ArgMax{absbits(colj[i]), p0 + i});
+      best = argmax_better(best, ArgMax{absbits(colc[i]), p0 + i});
     best = warp_argmax(best);
     if (lane == 0) s.wbest[warp] = best;
     __syncthreads();
-    if (tid == 0) {
-      ArgMax b = s.wbest[0];
-      for (int w = 1; w < kNodeWarps; ++w) b = argmax_better(b, s.wbest[w]);
-      *s.slot = b;
+    ArgMax b = s.wbest[0];
+    for (int w = 1; w < kNodeWarps; ++w) b = argmax_better(b, s.wbest[w]);
+    // row values as after step jprev's update: columns > jprev + 1 on the fly
+    const double *cjp = upd ? s.tile + (size_t)jprev * ldt : nullptr;
+    auto value = [&](int li, int k) -> double {
+      const double v = s.tile[li + (size_t)k * ldt];
+      return (upd && k > jprev + 1) ? fma(-cjp[li], s.prow[k], v) : v;
+    };
+    if (b.pos != INT_MAX) {
+      const int li = b.pos - p0;
+      for (int k = tid; k < bk; k += kNodeThreads) s.prow_pub[q * bk + k] = value(li, k);
+      if (tid == 0) s.plab[q] = s.lab[li];
     }
-    node_sync(cl, G);
-    // (b) cluster argmax (the G partial maxima read in parallel through
-    //     DSMEM); read the pivot row and (owner of the pivot position) the
-    //     row at position j
-    if (tid < G) s.gslot[tid] = (tid == rank) ? *s.slot : *cl.map_shared_rank(s.slot, tid);
+    if (tid == 0) s.pkey[q] = b;
+    if (c / rloc == rank) {
+      const int lc = c - p0;
+      for (int k = tid; k < bk; k += kNodeThreads) s.jrow_pub[q * bk + k] = value(lc, k);
+      if (tid == 0) s.plab[2 + q] = s.lab[lc];
+    }
+    // every read of the tile above is done before any thread updates it
+    // (the arrive that follows does not wait)
     __syncthreads();
-    // every thread combines the G partial maxima (same order, same result)
+  };
+  if (kmax > 0) find_and_publish(0, 0, false, 0);
+  cluster_arrive();
+  cluster_wait();
+  for (int j = 0; j < kmax; ++j) {
+    const int q = j & 1;
+    // (a) the cluster's best position of column j
+    if (tid < G) s.gslot[tid] = (tid == rank) ? s.pkey[q] : *cl.map_shared_rank(s.pkey + q, tid);
+    __syncthreads();
     ArgMax gb = s.gslot[0];
-    for (int q = 1; q < G; ++q) gb = argmax_better(gb, s.gslot[q]);
+    for (int r = 1; r < G; ++r) gb = argmax_better(gb, s.gslot[r]);
     const int zero = (gb.key == 0ull);
     const int p = gb.pos;
+    const int i1 = max(j + 1 - p0, 0);
+    double *cj = s.tile + (size_t)j * ldt;
     if (!zero) {
+      // (b) the pivot row, and at the pivot's owner the row at position j
       const int op = p / rloc, lp = p - op * rloc;
       const int oj = j / rloc, lj = j - oj * rloc;
-      const double *tp = (op == rank) ? s.tile : cl.map_shared_rank(s.tile, op);
+      const double *pr = (op == rank) ? s.prow_pub + q * bk : cl.map_shared_rank(s.prow_pub + q * bk, op);
       for (int k = tid; k < bk; k += kNodeThreads) {
-        const double v = tp[lp + (size_t)k * ldt];
+        const double v = pr[k];
         s.prow[k] = v;
-        if (k == j) s.scal[0] = 1.0 / v;  // the pivot's reciprocal, read after the barrier below
+        if (k == j) s.scal[0] = 1.0 / v;
       }
-      if (tid == 0) s.iscal[1] = (op == rank) ? s.lab[lp] : *cl.map_shared_rank(s.lab + lp, op);
+      if (tid == 0) s.iscal[1] = (op == rank) ? s.plab[q] : *cl.map_shared_rank(s.plab + q, op);
       if (p != j && op == rank) {
-        const double *tj = (oj == rank) ? s.tile : cl.map_shared_rank(s.tile, oj);
-        for (int k = tid; k < bk; k += kNodeThreads) s.trow[k] = tj[lj + (size_t)k * ldt];
-        if (tid == 0) s.iscal[2] = (oj == rank) ? s.lab[lj] : *cl.map_shared_rank(s.lab + lj, oj);
+        const double *jr = (oj == rank) ? s.jrow_pub + q * bk : cl.map_shared_rank(s.jrow_pub + q * bk, oj);
+        for (int k = tid; k < bk; k += kNodeThreads) s.trow[k] = jr[k];
+        if (tid == 0) s.iscal[2] = (oj == rank) ? s.plab[2 + q] : *cl.map_shared_rank(s.plab + 2 + q, oj);
       }
-    } else if (a.is_root && rank == 0 && tid == 0 && a.dev_info) {
-      atomicCAS(a.dev_info, 0, a.ipiv_base + j + 1);
-    }
-    node_sync(cl, G);  // every read of this step is complete
-    if (zero) continue;
-    // (c) swap rows j and p (full width), labels with them
-    if (p != j) {
-      const int op = p / rloc, lp = p - op * rloc;
-      const int oj = j / rloc, lj = j - oj * rloc;
+      __syncthreads();
+      // (c) swap rows j and p (full width), labels with them
       if (oj == rank) {
         for (int k = tid; k < bk; k += kNodeThreads) s.tile[lj + (size_t)k * ldt] = s.prow[k];
         if (tid == 0) s.lab[lj] = s.iscal[1];
       }
-      if (op == rank) {
+      if (p != j && op == rank) {
         for (int k = tid; k < bk; k += kNodeThreads) s.tile[lp + (size_t)k * ldt] = s.trow[k];
         if (tid == 0) s.lab[lp] = s.iscal[2];
       }
+      __syncthreads();
+      // (d) multipliers l_i = a_ij / a_jj for positions > j
+      const double rinv = s.scal[0];
+      for (int i = i1 + tid; i < myrows; i += kNodeThreads) cj[i] *= rinv;
+      __syncthreads();
+      // (e) column j + 1 first
+      if (j + 1 < bk) {
+        const double u = s.prow[j + 1];
+        double *ck = s.tile + (size_t)(j + 1) * ldt;
+        for (int i = i1 + tid; i < myrows; i += kNodeThreads) ck[i] = fma(-cj[i], u, ck[i]);
+      }
+      __syncthreads();
+    } else if (a.is_root && rank == 0 && tid == 0 && a.dev_info) {
+      atomicCAS(a.dev_info, 0, a.ipiv_base + j + 1);
     }
-    // (d) multipliers l_i = a_ij / a_jj for positions > j (the swap's writes
-    //     are visible after the barrier; without a swap there is nothing to wait for)
-    if (p != j) __syncthreads();
-    const double rinv = s.scal[0];
-    const int i1 = max(j + 1 - p0, 0);
-    double *cj = s.tile + (size_t)j * ldt;
-    for (int i = i1 + tid; i < myrows; i += kNodeThreads) cj[i] *= rinv;
-    __syncthreads();
-    // (e) rank-1 update of the trailing columns
-    for (int k = j + 1 + warp; k < bk; k += kNodeWarps) {
-      const double u = s.prow[k];
-      double *ck = s.tile + (size_t)k * ldt;
-      for (int i = i1 + lane; i < myrows; i += 32) ck[i] = fma(-cj[i], u, ck[i]);
+    // (f) column j + 1's best row, published for the next step
+    if (j + 1 < kmax) find_and_publish(j + 1, q ^ 1, !zero, j);
+    cluster_arrive();
+    // (g) the rest of the rank-1 update while the peers reach the barrier
+    if (!zero) {
+      for (int k = j + 2 + warp; k < bk; k += kNodeWarps) {
+        const double u = s.prow[k];
+        double *ck = s.tile + (size_t)k * ldt;
+        for (int i = i1 + lane; i < myrows; i += 32) ck[i] = fma(-cj[i], u, ck[i]);
+      }
     }
-    __syncthreads();
+    cluster_wait();
   }
 
   // ---- outputs: candidates in selection order --------------------------
