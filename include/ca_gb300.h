@@ -326,7 +326,8 @@ int caqr_factor_mixed(int m, int n, double *A, int lda, int b, const ca_tree_t *
  * conditioned for the classic correction with the same digits; CA_REFINE_AUTO
  * three phases, each started only if the one before stopped above tol:
  * classic corrections while every step reduces the backward error at least
- * tenfold (up to max_iter); then up to 3 GMRES corrections; then, when the
+ * tenfold (up to max_iter); then up to 3 GMRES corrections, again while each
+ * gains tenfold; then, when the
  * reduced-precision factors are too far from A for either to converge
  * (roughly cond(A) 2^(-8 slices) >= 1), A factored again with 7 exact digits
  * (FP64-accurate factors), X from those and up to 3 classic corrections, with

@@ -662,8 +662,10 @@ int calu_gesv_mixed(int n, int nrhs, const double *A, int lda, int b, const ca_t
   // AUTO: classic corrections while each gains 10x or more
   if (ir_begin(ph[0], kSlowAuto, stream) != cudaSuccess) return CA_ERR_LAUNCH;
   if ((rc = run_phase(ph[0], false, max_iter)) != CA_OK) return rc;
-  // then GMRES corrections, if the classic phase stopped above tol
-  if (ir_begin_next(ph[0].ctl, ph[1], kNever, stream) != cudaSuccess) return CA_ERR_LAUNCH;
+  // then GMRES corrections, if the classic phase stopped above tol, while
+  // each gains 10x (a GMRES correction that does not is a sign that the
+  // factors are too far from A: the refactorization follows at once)
+  if (ir_begin_next(ph[0].ctl, ph[1], kSlowAuto, stream) != cudaSuccess) return CA_ERR_LAUNCH;
   if ((rc = run_phase(ph[1], true, kAutoGmresSteps)) != CA_OK) return rc;
   // then, if GMRES stopped above tol too (the reduced-precision factors are
   // too far from A), A factored again with 7 exact digits (FP64-accurate

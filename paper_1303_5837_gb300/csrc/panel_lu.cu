@@ -184,118 +184,197 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
   __syncthreads();
 
   // ---- GEPP on the distributed tile ------------------------------------
-  // One cluster barrier per column.  At the end of step j-1 every CTA has
-  // published its best position of column j with that row's values (its
-  // columns beyond j computed on the fly exactly as the step's update
-  // computes them), and the owner of position j has published the row there;
-  // step j reads the G keys, takes the pivot row (and, at the pivot's owner,
-  // the row at j) from the peers' published copies, swaps locally, scales
-  // column j, updates column j + 1, finds and publishes column j + 1's best
-  // row, arrives at the barrier, and only then updates columns j + 2.. while
-  // the peers catch up.  The published copies of step j are overwritten two
-  // steps later, after a barrier every reader has passed.
   const int kmax = min(R, bk);
-  // local best of column c over positions >= c (valid rows of this CTA);
-  // publishes it (and, at the owner, the row at position c) into buffer q
-  auto find_and_publish = [&](int c, int q, bool upd, int jprev) {
-    ArgMax best{0ull, INT_MAX};
-    const int i0 = max(c - p0, 0);
-    const double *colc = s.tile + (size_t)c * ldt;
-    for (int i = i0 + tid; i < myrows; i += kNodeThreads)
-      best = argmax_better(best, ArgMax{absbits(colc[i]), p0 + i});
-    best = warp_argmax(best);
-    if (lane == 0) s.wbest[warp] = best;
-    __syncthreads();
-    ArgMax b = s.wbest[0];
-    for (int w = 1; w < kNodeWarps; ++w) b = argmax_better(b, s.wbest[w]);
-    // row values as after step jprev's update: columns > jprev + 1 on the fly
-    const double *cjp = upd ? s.tile + (size_t)jprev * ldt : nullptr;
-    auto value = [&](int li, int k) -> double {
-      const double v = s.tile[li + (size_t)k * ldt];
-      return (upd && k > jprev + 1) ? fma(-cjp[li], s.prow[k], v) : v;
-    };
-    if (b.pos != INT_MAX) {
-      const int li = b.pos - p0;
-      for (int k = tid; k < bk; k += kNodeThreads) s.prow_pub[q * bk + k] = value(li, k);
-      if (tid == 0) s.plab[q] = s.lab[li];
-    }
-    if (tid == 0) s.pkey[q] = b;
-    if (c / rloc == rank) {
-      const int lc = c - p0;
-      for (int k = tid; k < bk; k += kNodeThreads) s.jrow_pub[q * bk + k] = value(lc, k);
-      if (tid == 0) s.plab[2 + q] = s.lab[lc];
-    }
-    // every read of the tile above is done before any thread updates it
-    // (the arrive that follows does not wait)
-    __syncthreads();
-  };
-  if (kmax > 0) find_and_publish(0, 0, false, 0);
-  cluster_arrive();
-  cluster_wait();
-  for (int j = 0; j < kmax; ++j) {
-    const int q = j & 1;
-    // (a) the cluster's best position of column j
-    if (tid < G) s.gslot[tid] = (tid == rank) ? s.pkey[q] : *cl.map_shared_rank(s.pkey + q, tid);
-    __syncthreads();
-    ArgMax gb = s.gslot[0];
-    for (int r = 1; r < G; ++r) gb = argmax_better(gb, s.gslot[r]);
-    const int zero = (gb.key == 0ull);
-    const int p = gb.pos;
-    const int i1 = max(j + 1 - p0, 0);
-    double *cj = s.tile + (size_t)j * ldt;
-    if (!zero) {
-      // (b) the pivot row, and at the pivot's owner the row at position j
-      const int op = p / rloc, lp = p - op * rloc;
-      const int oj = j / rloc, lj = j - oj * rloc;
-      const double *pr = (op == rank) ? s.prow_pub + q * bk : cl.map_shared_rank(s.prow_pub + q * bk, op);
-      for (int k = tid; k < bk; k += kNodeThreads) {
-        const double v = pr[k];
-        s.prow[k] = v;
-        if (k == j) s.scal[0] = 1.0 / v;
-      }
-      if (tid == 0) s.iscal[1] = (op == rank) ? s.plab[q] : *cl.map_shared_rank(s.plab + q, op);
-      if (p != j && op == rank) {
-        const double *jr = (oj == rank) ? s.jrow_pub + q * bk : cl.map_shared_rank(s.jrow_pub + q * bk, oj);
-        for (int k = tid; k < bk; k += kNodeThreads) s.trow[k] = jr[k];
-        if (tid == 0) s.iscal[2] = (oj == rank) ? s.plab[2 + q] : *cl.map_shared_rank(s.plab + 2 + q, oj);
-      }
+  // A node held by one CTA: plain barriers, every row local.
+  if (G == 1) {
+    for (int j = 0; j < kmax; ++j) {
+      // (a) local argmax over positions >= j of column j
+      ArgMax best{0ull, INT_MAX};
+      const int i0 = max(j - p0, 0);
+      const double *colj = s.tile + (size_t)j * ldt;
+      for (int i = i0 + tid; i < myrows; i += kNodeThreads)
+        best = argmax_better(best, ArgMax{absbits(colj[i]), p0 + i});
+      best = warp_argmax(best);
+      if (lane == 0) s.wbest[warp] = best;
       __syncthreads();
+      if (tid == 0) {
+        ArgMax b = s.wbest[0];
+        for (int w = 1; w < kNodeWarps; ++w) b = argmax_better(b, s.wbest[w]);
+        *s.slot = b;
+      }
+      node_sync(cl, G);
+      // (b) cluster argmax (the G partial maxima read in parallel through
+      //     DSMEM); read the pivot row and (owner of the pivot position) the
+      //     row at position j
+      if (tid < G) s.gslot[tid] = (tid == rank) ? *s.slot : *cl.map_shared_rank(s.slot, tid);
+      __syncthreads();
+      // every thread combines the G partial maxima (same order, same result)
+      ArgMax gb = s.gslot[0];
+      for (int q = 1; q < G; ++q) gb = argmax_better(gb, s.gslot[q]);
+      const int zero = (gb.key == 0ull);
+      const int p = gb.pos;
+      if (!zero) {
+        const int op = p / rloc, lp = p - op * rloc;
+        const int oj = j / rloc, lj = j - oj * rloc;
+        const double *tp = (op == rank) ? s.tile : cl.map_shared_rank(s.tile, op);
+        for (int k = tid; k < bk; k += kNodeThreads) {
+          const double v = tp[lp + (size_t)k * ldt];
+          s.prow[k] = v;
+          if (k == j) s.scal[0] = 1.0 / v;  // the pivot's reciprocal, read after the barrier below
+        }
+        if (tid == 0) s.iscal[1] = (op == rank) ? s.lab[lp] : *cl.map_shared_rank(s.lab + lp, op);
+        if (p != j && op == rank) {
+          const double *tj = (oj == rank) ? s.tile : cl.map_shared_rank(s.tile, oj);
+          for (int k = tid; k < bk; k += kNodeThreads) s.trow[k] = tj[lj + (size_t)k * ldt];
+          if (tid == 0) s.iscal[2] = (oj == rank) ? s.lab[lj] : *cl.map_shared_rank(s.lab + lj, oj);
+        }
+      } else if (a.is_root && rank == 0 && tid == 0 && a.dev_info) {
+        atomicCAS(a.dev_info, 0, a.ipiv_base + j + 1);
+      }
+      node_sync(cl, G);  // every read of this step is complete
+      if (zero) continue;
       // (c) swap rows j and p (full width), labels with them
-      if (oj == rank) {
-        for (int k = tid; k < bk; k += kNodeThreads) s.tile[lj + (size_t)k * ldt] = s.prow[k];
-        if (tid == 0) s.lab[lj] = s.iscal[1];
+      if (p != j) {
+        const int op = p / rloc, lp = p - op * rloc;
+        const int oj = j / rloc, lj = j - oj * rloc;
+        if (oj == rank) {
+          for (int k = tid; k < bk; k += kNodeThreads) s.tile[lj + (size_t)k * ldt] = s.prow[k];
+          if (tid == 0) s.lab[lj] = s.iscal[1];
+        }
+        if (op == rank) {
+          for (int k = tid; k < bk; k += kNodeThreads) s.tile[lp + (size_t)k * ldt] = s.trow[k];
+          if (tid == 0) s.lab[lp] = s.iscal[2];
+        }
       }
-      if (p != j && op == rank) {
-        for (int k = tid; k < bk; k += kNodeThreads) s.tile[lp + (size_t)k * ldt] = s.trow[k];
-        if (tid == 0) s.lab[lp] = s.iscal[2];
-      }
-      __syncthreads();
-      // (d) multipliers l_i = a_ij / a_jj for positions > j
+      // (d) multipliers l_i = a_ij / a_jj for positions > j (the swap's writes
+      //     are visible after the barrier; without a swap there is nothing to wait for)
+      if (p != j) __syncthreads();
       const double rinv = s.scal[0];
+      const int i1 = max(j + 1 - p0, 0);
+      double *cj = s.tile + (size_t)j * ldt;
       for (int i = i1 + tid; i < myrows; i += kNodeThreads) cj[i] *= rinv;
       __syncthreads();
-      // (e) column j + 1 first
-      if (j + 1 < bk) {
-        const double u = s.prow[j + 1];
-        double *ck = s.tile + (size_t)(j + 1) * ldt;
-        for (int i = i1 + tid; i < myrows; i += kNodeThreads) ck[i] = fma(-cj[i], u, ck[i]);
-      }
-      __syncthreads();
-    } else if (a.is_root && rank == 0 && tid == 0 && a.dev_info) {
-      atomicCAS(a.dev_info, 0, a.ipiv_base + j + 1);
-    }
-    // (f) column j + 1's best row, published for the next step
-    if (j + 1 < kmax) find_and_publish(j + 1, q ^ 1, !zero, j);
-    cluster_arrive();
-    // (g) the rest of the rank-1 update while the peers reach the barrier
-    if (!zero) {
-      for (int k = j + 2 + warp; k < bk; k += kNodeWarps) {
+      // (e) rank-1 update of the trailing columns
+      for (int k = j + 1 + warp; k < bk; k += kNodeWarps) {
         const double u = s.prow[k];
         double *ck = s.tile + (size_t)k * ldt;
         for (int i = i1 + lane; i < myrows; i += 32) ck[i] = fma(-cj[i], u, ck[i]);
       }
+      __syncthreads();
     }
+  } else {
+    // One cluster barrier per column.  At the end of step j-1 every CTA has
+    // published its best position of column j with that row's values (its
+    // columns beyond j computed on the fly exactly as the step's update
+    // computes them), and the owner of position j has published the row there;
+    // step j reads the G keys, takes the pivot row (and, at the pivot's owner,
+    // the row at j) from the peers' published copies, swaps locally, scales
+    // column j, updates column j + 1, finds and publishes column j + 1's best
+    // row, arrives at the barrier, and only then updates columns j + 2.. while
+    // the peers catch up.  The published copies of step j are overwritten two
+    // steps later, after a barrier every reader has passed.
+    // local best of column c over positions >= c (valid rows of this CTA);
+    // publishes it (and, at the owner, the row at position c) into buffer q
+    auto find_and_publish = [&](int c, int q, bool upd, int jprev) {
+      ArgMax best{0ull, INT_MAX};
+      const int i0 = max(c - p0, 0);
+      const double *colc = s.tile + (size_t)c * ldt;
+      for (int i = i0 + tid; i < myrows; i += kNodeThreads)
+        best = argmax_better(best, ArgMax{absbits(colc[i]), p0 + i});
+      best = warp_argmax(best);
+      if (lane == 0) s.wbest[warp] = best;
+      __syncthreads();
+      ArgMax b = s.wbest[0];
+      for (int w = 1; w < kNodeWarps; ++w) b = argmax_better(b, s.wbest[w]);
+      // row values as after step jprev's update: columns > jprev + 1 on the fly
+      const double *cjp = upd ? s.tile + (size_t)jprev * ldt : nullptr;
+      auto value = [&](int li, int k) -> double {
+        const double v = s.tile[li + (size_t)k * ldt];
+        return (upd && k > jprev + 1) ? fma(-cjp[li], s.prow[k], v) : v;
+      };
+      if (b.pos != INT_MAX) {
+        const int li = b.pos - p0;
+        for (int k = tid; k < bk; k += kNodeThreads) s.prow_pub[q * bk + k] = value(li, k);
+        if (tid == 0) s.plab[q] = s.lab[li];
+      }
+      if (tid == 0) s.pkey[q] = b;
+      if (c / rloc == rank) {
+        const int lc = c - p0;
+        for (int k = tid; k < bk; k += kNodeThreads) s.jrow_pub[q * bk + k] = value(lc, k);
+        if (tid == 0) s.plab[2 + q] = s.lab[lc];
+      }
+      // every read of the tile above is done before any thread updates it
+      // (the arrive that follows does not wait)
+      __syncthreads();
+    };
+    if (kmax > 0) find_and_publish(0, 0, false, 0);
+    cluster_arrive();
     cluster_wait();
+    for (int j = 0; j < kmax; ++j) {
+      const int q = j & 1;
+      // (a) the cluster's best position of column j
+      if (tid < G) s.gslot[tid] = (tid == rank) ? s.pkey[q] : *cl.map_shared_rank(s.pkey + q, tid);
+      __syncthreads();
+      ArgMax gb = s.gslot[0];
+      for (int r = 1; r < G; ++r) gb = argmax_better(gb, s.gslot[r]);
+      const int zero = (gb.key == 0ull);
+      const int p = gb.pos;
+      const int i1 = max(j + 1 - p0, 0);
+      double *cj = s.tile + (size_t)j * ldt;
+      if (!zero) {
+        // (b) the pivot row, and at the pivot's owner the row at position j
+        const int op = p / rloc, lp = p - op * rloc;
+        const int oj = j / rloc, lj = j - oj * rloc;
+        const double *pr = (op == rank) ? s.prow_pub + q * bk : cl.map_shared_rank(s.prow_pub + q * bk, op);
+        for (int k = tid; k < bk; k += kNodeThreads) {
+          const double v = pr[k];
+          s.prow[k] = v;
+          if (k == j) s.scal[0] = 1.0 / v;
+        }
+        if (tid == 0) s.iscal[1] = (op == rank) ? s.plab[q] : *cl.map_shared_rank(s.plab + q, op);
+        if (p != j && op == rank) {
+          const double *jr = (oj == rank) ? s.jrow_pub + q * bk : cl.map_shared_rank(s.jrow_pub + q * bk, oj);
+          for (int k = tid; k < bk; k += kNodeThreads) s.trow[k] = jr[k];
+          if (tid == 0) s.iscal[2] = (oj == rank) ? s.plab[2 + q] : *cl.map_shared_rank(s.plab + 2 + q, oj);
+        }
+        __syncthreads();
+        // (c) swap rows j and p (full width), labels with them
+        if (oj == rank) {
+          for (int k = tid; k < bk; k += kNodeThreads) s.tile[lj + (size_t)k * ldt] = s.prow[k];
+          if (tid == 0) s.lab[lj] = s.iscal[1];
+        }
+        if (p != j && op == rank) {
+          for (int k = tid; k < bk; k += kNodeThreads) s.tile[lp + (size_t)k * ldt] = s.trow[k];
+          if (tid == 0) s.lab[lp] = s.iscal[2];
+        }
+        __syncthreads();
+        // (d) multipliers l_i = a_ij / a_jj for positions > j
+        const double rinv = s.scal[0];
+        for (int i = i1 + tid; i < myrows; i += kNodeThreads) cj[i] *= rinv;
+        __syncthreads();
+        // (e) column j + 1 first
+        if (j + 1 < bk) {
+          const double u = s.prow[j + 1];
+          double *ck = s.tile + (size_t)(j + 1) * ldt;
+          for (int i = i1 + tid; i < myrows; i += kNodeThreads) ck[i] = fma(-cj[i], u, ck[i]);
+        }
+        __syncthreads();
+      } else if (a.is_root && rank == 0 && tid == 0 && a.dev_info) {
+        atomicCAS(a.dev_info, 0, a.ipiv_base + j + 1);
+      }
+      // (f) column j + 1's best row, published for the next step
+      if (j + 1 < kmax) find_and_publish(j + 1, q ^ 1, !zero, j);
+      cluster_arrive();
+      // (g) the rest of the rank-1 update while the peers reach the barrier
+      if (!zero) {
+        for (int k = j + 2 + warp; k < bk; k += kNodeWarps) {
+          const double u = s.prow[k];
+          double *ck = s.tile + (size_t)k * ldt;
+          for (int i = i1 + lane; i < myrows; i += 32) ck[i] = fma(-cj[i], u, ck[i]);
+        }
+      }
+      cluster_wait();
+    }
   }
 
   // ---- outputs: candidates in selection order --------------------------
