@@ -78,6 +78,9 @@ def parse():
     p.add_argument("--c3-conds", default="1e2,1e6,1e10")
     p.add_argument("--no-c3", action="store_true")
     p.add_argument("--only-c3", action="store_true", help="diagnostic: run only the n x cond grid")
+    p.add_argument("--only-tslu-panel", default="",
+                   help="diagnostic for profiling: M,B -- tslu of a seeded M x B panel with the benchmark's "
+                        "leaves and tree, twice (the second call is the one to capture)")
     p.add_argument("--aux-steps", type=int, default=2,
                    help="timed runs of each secondary measurement (LU forms, C3 grid), after one warm-up")
     p.add_argument("--cpu-n", type=int, default=2048,
@@ -661,6 +664,17 @@ def run_ours(a, rank: int, world: int, local: int):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     ca.load()
+    if a.only_tslu_panel:
+        m, bw = (int(x) for x in a.only_tslu_panel.split(","))
+        t = ca.make_tree(a.leaf, parse_tree(a.tree))
+        P0 = torch.randn(bw, m, dtype=torch.float64, device=dev,
+                         generator=torch.Generator(device=dev).manual_seed(3)).t()
+        for _ in range(2):
+            P = P0.t().contiguous().t()
+            _, info = ca.tslu(P, t)
+        torch.cuda.synchronize()
+        print(json.dumps({"tslu_panel": [m, bw], "info": info.cpu().tolist()}), flush=True)
+        return
     peaks = measure_fma_peaks(ca, torch, dev)
     if a.only_c3:
         res = c3_grid(a, ca, torch, dev, world)
