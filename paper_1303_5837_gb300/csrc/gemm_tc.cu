@@ -133,13 +133,11 @@ __device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, uint32_t (&r)[32])
 }
 
 // 32 TMEM lanes x 16 consecutive 32-bit columns.
-__device__ __forceinline__ void tmem_ld_32x16(uint32_t taddr, uint32_t (&r)[16]) {
+__device__ __forceinline__ void tmem_ld_32x8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-        "=r"(r[15])
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -221,6 +219,7 @@ constexpr int kTcBM = 128;
 constexpr int kTcKpad = 64;                      // K is padded to a multiple of 64
 constexpr long long kWaitLimit = 4000000000ll;   // ~2 s of SM clock
 constexpr size_t kTcSmemBudget = 224 * 1024;
+constexpr size_t kTcSmemHalf = 110 * 1024;  // per CTA when two share an SM
 
 struct TcArgs {
   int kblocks, S, mpad, npad, bn;
@@ -249,7 +248,7 @@ __host__ __device__ inline size_t tc_stage_bytes(int S, int bn, int bk) {
   return (size_t)S * (kTcBM + bn) * bk * 2;
 }
 
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, 2)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -366,7 +365,7 @@ __global__ void __launch_bounds__(256, 1)
     // and turn each into a double with integer instructions (the FP64 pipe
     // is left with the two subtractions from C).
     const int dmax = a.exact ? a.S - 1 : 0;
-    constexpr int kEp = 16;  // columns per epilogue step
+    constexpr int kEp = 8;  // columns per epilogue step
     for (int c0 = half * kEp; c0 < a.bn; c0 += 2 * kEp) {
       long long thi[kEp], tlo[kEp];
 #pragma unroll
@@ -374,7 +373,7 @@ __global__ void __launch_bounds__(256, 1)
       float vf[kEp];
       for (int d = 0; d < nacc; ++d) {
         uint32_t r[kEp];
-        tmem_ld_32x16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(d * a.bn + c0), r);
+        tmem_ld_32x8(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(d * a.bn + c0), r);
         if (!a.exact) {
 #pragma unroll
           for (int j = 0; j < kEp; ++j) vf[j] = __uint_as_float(r[j]);
@@ -565,12 +564,34 @@ struct TcCfg {
   size_t smem;
 };
 
-// Tile width, K block and stages: one CTA of 8 warps per SM; the widest
-// tile whose accumulators fit in the 512 tensor-memory columns, then the
-// deepest K-block pipeline that fits in shared memory (two stages overlap the
-// loads of one K block with the MMAs of the previous one).
+// Tile width, K block and stages.  First choice: two CTAs of 8 warps per
+// SM (each with at most 256 tensor-memory columns and half the shared
+// memory), so that one CTA's epilogue -- the FP64 read-modify-write of its C
+// tile -- overlaps the other's loads and MMAs; tiles at least 64 wide.
+// Otherwise one CTA per SM: the widest tile whose accumulators fit in the
+// 512 columns.  Then the deepest K-block pipeline that fits in shared memory
+// (two stages overlap the loads of one K block with the MMAs of the
+// previous one).
 static bool tc_config(int S, int exact, int kpad, TcCfg &c) {
   const int nacc = tc_nacc(S, exact, kpad);
+  {
+    int bn2 = 128;
+    while (bn2 > 64 && nacc * bn2 > 256) bn2 /= 2;
+    if (nacc * bn2 <= 256) {
+      const int opts2[3][2] = {{64, 2}, {32, 2}, {32, 1}};
+      for (auto &o : opts2) {
+        const int bk = o[0];
+        int ns = o[1];
+        const int kblocks = kpad / bk;
+        if (ns > kblocks) ns = kblocks;
+        const size_t smem = ns * tc_stage_bytes(S, bn2, bk) + 1024 + 256;
+        if (smem <= kTcSmemHalf) {
+          c = {bn2, bk, bk == 64 ? 2 : 4, ns, pow2_at_least(nacc * bn2), smem};
+          return true;
+        }
+      }
+    }
+  }
   int bn = 128;
   while (bn > 32 && nacc * bn > 512) bn /= 2;
   if (nacc * bn > 512) return false;
@@ -670,7 +691,10 @@ cudaError_t gemm_tc(const TcGemm &g, void *ws, int *status, cudaStream_t st) {
   const size_t smem = cfg.smem;
   static std::atomic<unsigned long long> init{0};
   e = once_per_device(init, [] {
-    return cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBudget);
+    cudaError_t r = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmemBudget);
+    if (r != cudaSuccess) return r;
+    return cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   });
   if (e != cudaSuccess) return e;
   dim3 grid(mp / kTcBM, np / bn, g.nbatch);
