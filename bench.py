@@ -60,6 +60,21 @@ def _hbm_peak() -> float:
 HBM_GBS = _hbm_peak()
 
 
+def _bf16_peaks():
+    """Measured cuBLAS bf16 GEMM throughput of this machine's GB300
+    (MEASURED_PEAKS.json: burst, sustained), else the profiling recipe's
+    fallback 1900 / 1700 TFLOP/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, 1700.0, "fallback"
+
+
+BF16_TFLOPS, BF16_TFLOPS_SUSTAINED, BF16_SOURCE = _bf16_peaks()
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -978,11 +993,29 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
 
     ms, (it, be) = timed(mixed, "mixed_ir")
     it, be = int(it.item()), float(be.item())
+    mixed_ms = ms
     out["mixed_ir"] = {"ms": ms, "gflops": lu_flops / ms / 1e6, "iters": it, "berr": be, "refine": "auto",
                        "berr_check": berr_of(X), "slices": S, "exact": ex,
                        "x_rel_err": float(torch.linalg.norm(X - x_true) / torch.linalg.norm(x_true)),
                        "speedup_vs_fp64": out["fp64"]["ms"] / ms,
-                       "form": f"calu_gesv_mixed: {S}-digit bf16 tensor-core update + FP64 refinement"}
+                       "form": f"calu_gesv_mixed: {S}-digit bf16 tensor-core update + FP64 refinement",
+                       "kernels_note": ("launch records of every kernel enqueued, including the phases that the "
+                                        "device skips once refinement has converged (the GMRES and the 7-digit "
+                                        "refactorization phases of refine=auto): those launches return at once, "
+                                        "and their flop figures were not executed; mixed_factor below holds the "
+                                        "factorization alone")}
+    wfac = torch.empty((ca.ca_calu_mixed_workspace(n, n, b, tree, S, ex) + 7) // 8, dtype=torch.float64,
+                       device=A0.device)
+
+    def mixed_factor():
+        A.copy_(A0)
+        ca.calu_factor_mixed(A, b, tree, slices=S, exact=ex, ipiv=ipiv, work=wfac, dev_info=info)
+
+    ms, _ = timed(mixed_factor, "mixed_factor")
+    out["mixed_factor"] = {"ms": ms, "gflops": 2.0 * n ** 3 / 3.0 / ms / 1e6,
+                           "share_of_mixed_ir": ms / mixed_ms,
+                           "form": f"calu_factor_mixed({S} digits), the factorization of mixed_ir alone"}
+    del wfac
     wemu = torch.empty((ca.ca_calu_mixed_workspace(n, n, b, tree, 7, True) + 7) // 8, dtype=torch.float64,
                        device=A0.device)
 
@@ -1047,6 +1080,17 @@ def lu_form_timings(a, ca, torch, A0, B0, x_true, tree, st, world):
     del qtg, wgl
     for k, v in kernels_of.items():
         out[k]["kernels"] = v
+    tc = kernels_of.get("mixed_factor", {}).get("gemm_tc")
+    if tc and tc["ms"] > 0:
+        # bf16 flops issued by the tensor-core update (2 M N K per digit
+        # product, padded tile sizes) over its summed CUDA-event time
+        ach = tc["gflop"] / tc["ms"]  # GFLOP per ms = TFLOP/s
+        out["mixed_factor"]["roofline"] = {
+            "kernel": "gemm_tc", "bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
+            "peak": BF16_TFLOPS, "frac": ach / BF16_TFLOPS,
+            "peak_sustained": BF16_TFLOPS_SUSTAINED, "frac_of_sustained": ach / BF16_TFLOPS_SUSTAINED,
+            "peak_source": f"cuBLAS bf16 GEMM, {BF16_SOURCE} (MEASURED_PEAKS.json: burst and sustained)",
+            "work": "2 M N K x S (S + 1) / 2 bf16 flop per launch (exact digit products)"}
     return out
 
 

@@ -132,7 +132,7 @@ __device__ __forceinline__ void tmem_ld_32x32(uint32_t taddr, uint32_t (&r)[32])
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// 32 TMEM lanes x 16 consecutive 32-bit columns.
+// 32 TMEM lanes x 8 consecutive 32-bit columns.
 __device__ __forceinline__ void tmem_ld_32x8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 "
@@ -189,7 +189,17 @@ __device__ __forceinline__ double i64_scaled_to_double(long long v, int e2) {
     }
   }
   const long long E = 52 + sh + e2 + 1023;  // m in [2^52, 2^53)
-  if (E <= 0 || E >= 2047) return (double)v * pow2i(e2);  // outside the normal range: rare path
+  if (E >= 2047) return __longlong_as_double((long long)(sign | (0x7ffull << 52)));  // overflow: infinity
+  if (E <= 0) {
+    // subnormal or zero: m 2^(E - 1075) = (m >> (1 - E)) 2^-1074, rounded to
+    // nearest even (a carry into bit 52 gives the smallest normal number)
+    const int s2 = 1 - (int)E;
+    if (s2 > 53) return __longlong_as_double((long long)sign);
+    unsigned long long q = m >> s2;
+    const unsigned long long rem = m & ((1ull << s2) - 1), half = 1ull << (s2 - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;
+    return __longlong_as_double((long long)(sign | q));
+  }
   return __longlong_as_double((long long)(sign | ((unsigned long long)E << 52) | (m & ((1ull << 52) - 1))));
 }
 
@@ -409,9 +419,8 @@ __global__ void __launch_bounds__(256, 2)
         if (a.exact) {
           // value = T_hi 2^(8 (4 - dmax)) ... written relative to diagonal dmax:
           // sum_D acc_D 2^(-8 D) = T_hi 2^(-32) + T_lo 2^(-48)
-          const long long sh = a.sign;
-          c -= i64_scaled_to_double(sh * thi[j], sc - 32);
-          if (dmax > 4) c -= i64_scaled_to_double(sh * tlo[j], sc - 48);
+          c -= i64_scaled_to_double(a.sign > 0 ? thi[j] : -thi[j], sc - 32);
+          if (dmax > 4) c -= i64_scaled_to_double(a.sign > 0 ? tlo[j] : -tlo[j], sc - 48);
         } else {
           c = fma((double)(-a.sign * vf[j]), pow2i(sc), c);
         }
