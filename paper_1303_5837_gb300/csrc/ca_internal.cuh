@@ -251,6 +251,25 @@ struct QrPanelWs {
 size_t qr_panel_ws_bytes(int nleaves_max);
 void qr_panel_ws_carve(void *work, int nleaves_max, QrPanelWs &ws);
 
+// One round of TSQR nodes (leaves, or the merges of one tree round).
+struct TsqrNodeArgs {
+  double *P;  // panel, ld lda
+  int lda, mk, bk, b;
+  int leaf_rows;
+  int is_leaf;
+  RoundDesc rd;
+  const int *top_in, *c_in;
+  int *top_out, *c_out;
+  double *Tp;     // the panel's T blocks (b x b each)
+  int nleaves;
+  int rloc, ld;   // tile rows per CTA, tile leading dimension (odd)
+  int *dev_info;
+};
+// Register-resident TSQR nodes (panel_qr_reg.cu) for nodes of at most 256
+// rows and 64 columns held by one CTA; *done = false when the shape is not
+// covered (the shared-memory node kernel then runs).
+bool tsqr_reg_fits(int rows, int bk);
+cudaError_t launch_tsqr_reg(const TsqrNodeArgs &a, int nodes, int rows, cudaStream_t st, bool *done);
 cudaError_t tsqr_panel(int mk, int bk, int b, double *P, int lda, int leaf_rows,
                        const Plan &plan, double *Tp, const QrPanelWs &ws, int *dev_info,
                        cudaStream_t st);

@@ -19,20 +19,6 @@ constexpr int kQrWarps = kQrThreads / 32;
 constexpr size_t kQrSmemBudget = 220 * 1024;
 constexpr int kQrGroups = 4;  // row groups of the dot-product mapping
 
-struct TsqrNodeArgs {
-  double *P;  // panel, ld lda
-  int lda, mk, bk, b;
-  int leaf_rows;
-  int is_leaf;
-  RoundDesc rd;
-  const int *top_in, *c_in;
-  int *top_out, *c_out;
-  double *Tp;     // the panel's T blocks (b x b each)
-  int nleaves;
-  int rloc, ld;   // tile rows per CTA, tile leading dimension (odd)
-  int *dev_info;
-};
-
 __host__ __device__ inline size_t tsqr_smem_bytes(int rloc, int ld, int bk) {
   size_t s = (size_t)ld * bk * 8;          // tile
   s += (size_t)kQrGroups * bk * 8;         // dot partials per row group
@@ -912,6 +898,11 @@ static cudaError_t launch_tsqr_node(const TsqrNodeArgs &args, int nodes, int G, 
   const double c = args.bk;
   // Householder QR (2 r c^2 - 2 c^3 / 3) plus T (r c^2 / ... about r c^2)
   ProfScope ps(kClsTsqrNode, st, nodes * (2.0 * r * c * c - 2.0 * c * c * c / 3.0 + r * c * c));
+  if (G == 0) {  // the node fits the registers of one CTA
+    bool done = false;
+    e = launch_tsqr_reg(args, nodes, (int)r, st, &done);
+    return (e == cudaSuccess && !done) ? cudaErrorInvalidValue : e;
+  }
   cfg.gridDim = dim3(nodes * G);
   cfg.blockDim = dim3(kQrThreads);
   cfg.dynamicSmemBytes = tsqr_smem_bytes(args.rloc, args.ld, args.bk);
@@ -939,8 +930,9 @@ cudaError_t tsqr_panel(int mk, int bk, int b, double *P, int lda, int leaf_rows,
   a.nleaves = plan.nleaves;
   a.dev_info = dev_info;
   int R = leaf_rows < mk ? leaf_rows : mk;
-  int rloc, ld;
-  int G = pick_qr_cluster(R, bk, plan.nleaves, &rloc, &ld);
+  int rloc = 0, ld = 0;
+  // G = 0: the register-resident node kernel; else a cluster of G CTAs
+  int G = tsqr_reg_fits(R, bk) ? 0 : pick_qr_cluster(R, bk, plan.nleaves, &rloc, &ld);
   if (G < 0) return cudaErrorInvalidValue;
   a.is_leaf = 1;
   a.rloc = rloc;
@@ -952,7 +944,7 @@ cudaError_t tsqr_panel(int mk, int bk, int b, double *P, int lda, int leaf_rows,
   int buf = 0;
   for (int r = 0; r < plan.nrounds; ++r) {
     const RoundDesc &rd = plan.r[r];
-    G = pick_qr_cluster(rd.max_cnt * bk, bk, rd.n_out, &rloc, &ld);
+    G = tsqr_reg_fits(rd.max_cnt * bk, bk) ? 0 : pick_qr_cluster(rd.max_cnt * bk, bk, rd.n_out, &rloc, &ld);
     if (G < 0) return cudaErrorInvalidValue;
     a.is_leaf = 0;
     a.rd = rd;
