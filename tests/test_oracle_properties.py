@@ -1,11 +1,11 @@
-"""Property-based pins of the oracle (CPU; needs hypothesis, skipped where it
-is not installed): on random small shapes and random reduction trees, the
-oracle's tournament pivots and CALU factors equal an exact rational brute
-force of the same algorithm (Sec. 3.2: GEPP on every leaf, GEPP on the
-stacked candidate rows of every merge, in the tree's order), the tournament
-over a single leaf is GEPP, and CAQR over any tree is a QR factorization
-whose least-squares solve matches LAPACK's.  The examples are derandomized
-(the same on every run)."""
+"""Property-based pins of the oracle (CPU; with hypothesis, or, where it is
+not installed, the same strategies on seeded draws): on random small shapes
+and random reduction trees, the oracle's tournament pivots and CALU factors
+equal an exact rational brute force of the same algorithm (Sec. 3.2: GEPP on
+every leaf, GEPP on the stacked candidate rows of every merge, in the tree's
+order), the tournament over a single leaf is GEPP, and CAQR over any tree is
+a QR factorization whose least-squares solve matches LAPACK's.  The examples
+are derandomized (the same on every run)."""
 import numpy as np
 import pytest
 
@@ -13,9 +13,12 @@ import oracle
 from paper_1303_5837_gb300 import inputs
 from tests import bruteforce as bf
 
-hyp = pytest.importorskip("hypothesis")
-st = pytest.importorskip("hypothesis.strategies")
-given, settings, HealthCheck, event = hyp.given, hyp.settings, hyp.HealthCheck, hyp.event
+try:
+    import hypothesis as hyp
+    from hypothesis import strategies as st
+    given, settings, HealthCheck, event = hyp.given, hyp.settings, hyp.HealthCheck, hyp.event
+except ImportError:  # the same pins on seeded draws where hypothesis is not installed
+    from tests._seeded_cases import HealthCheck, event, given, settings, st
 
 
 def tie_free(m, n, seed, chk, span):
