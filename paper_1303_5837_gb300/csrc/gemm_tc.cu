@@ -203,6 +203,17 @@ __device__ __forceinline__ double i64_scaled_to_double(long long v, int e2) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)E << 52) | (m & ((1ull << 52) - 1))));
 }
 
+// v * 2^e2 as a double, rounded to nearest even: CUDA's correctly rounded
+// conversion of v, then the scale added to its exponent field (exact while
+// the result stays normal); zero and results outside the normal range take
+// the integer path above.
+__device__ __forceinline__ double scaled_rn(long long v, int e2) {
+  const long long bits = __double_as_longlong(__ll2double_rn(v));
+  const int E = (int)((bits >> 52) & 0x7ff) + e2;
+  if (v != 0 && E > 0 && E < 2047) return __longlong_as_double(bits + ((long long)e2 << 52));
+  return i64_scaled_to_double(v, e2);
+}
+
 // Digits of x for the split: F = round(|x| 2^(8S - e)) (|x| < 2^e), as a
 // signed integer with at most 8 S + 1 bits, from the FP64 bit pattern.
 __device__ __forceinline__ long long fixed_point_digits(double x, int e, int S) {
@@ -372,8 +383,8 @@ __global__ void __launch_bounds__(256, 2)
     // exact mode: the digit diagonals D = 0 .. S-1 (weights 2^(-8 D)) are
     // integers below 2^24; combine them in integer arithmetic,
     //   T_hi = sum_{D <= 4} acc_D 2^(8 (4 - D)),  T_lo = sum_{D > 4} acc_D 2^(8 (6 - D)),
-    // and turn each into a double with integer instructions (the FP64 pipe
-    // is left with the two subtractions from C).
+    // and turn each into a double by one correctly rounded conversion and an
+    // exponent add (FP64 pipe: the conversion and the subtraction from C).
     const int dmax = a.exact ? a.S - 1 : 0;
     constexpr int kEp = 8;  // columns per epilogue step
     for (int c0 = half * kEp; c0 < a.bn; c0 += 2 * kEp) {
@@ -381,7 +392,10 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
       for (int j = 0; j < kEp; ++j) thi[j] = tlo[j] = 0;
       float vf[kEp];
-      for (int d = 0; d < nacc; ++d) {
+      // unrolled over the at most 8 accumulators: constant shifts
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        if (d >= nacc) break;
         uint32_t r[kEp];
         tmem_ld_32x8(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(d * a.bn + c0), r);
         if (!a.exact) {
@@ -419,8 +433,8 @@ __global__ void __launch_bounds__(256, 2)
         if (a.exact) {
           // value = T_hi 2^(8 (4 - dmax)) ... written relative to diagonal dmax:
           // sum_D acc_D 2^(-8 D) = T_hi 2^(-32) + T_lo 2^(-48)
-          c -= i64_scaled_to_double(a.sign > 0 ? thi[j] : -thi[j], sc - 32);
-          if (dmax > 4) c -= i64_scaled_to_double(a.sign > 0 ? tlo[j] : -tlo[j], sc - 48);
+          c -= scaled_rn(a.sign > 0 ? thi[j] : -thi[j], sc - 32);
+          if (dmax > 4) c -= scaled_rn(a.sign > 0 ? tlo[j] : -tlo[j], sc - 48);
         } else {
           c = fma((double)(-a.sign * vf[j]), pow2i(sc), c);
         }
