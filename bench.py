@@ -556,8 +556,8 @@ def c3_grid(a, ca, torch, dev, world):
     calu_getrs) against the mixed form (calu_gesv_mixed: a.mixed_slices
     digits on the tensor cores, refinement "auto" to backward error 1e-14);
     each one warm-up and a.aux_steps timed runs.  A = U diag(s) V^T with
-    s_i = cond^(-i/(n-1)); U, V Haar (QR of a Gaussian) for n <= 8192, the
-    Kronecker Haar factors of the main step at n = 16384."""
+    s_i = cond^(-i/(n-1)); U, V Haar (QR of a seeded Gaussian), drawn once
+    per n."""
     from paper_1303_5837_gb300 import inputs
     st = torch.cuda.current_stream()
     b, S = a.b, a.mixed_slices
@@ -582,12 +582,8 @@ def c3_grid(a, ca, torch, dev, world):
 
     for n in sizes:
         lu_flops = 2.0 * n ** 3 / 3.0 + 2.0 * n * n
-        if n <= 8192:
-            U, V = haar_device(n, 31 + n, dev), haar_device(n, 37 + n, dev)
-            family = "Haar U, V (QR of a Gaussian)"
-        else:
-            U = V = None
-            family = "Kronecker products of Haar factors (as the main step)"
+        U, V = haar_device(n, 31 + n, dev), haar_device(n, 37 + n, dev)
+        family = "Haar U, V (QR of a Gaussian)"
         A = torch.empty((n, n), dtype=torch.float64, device=dev).t()
         LU = torch.empty_like(A)
         X = torch.empty((n, 1), dtype=torch.float64, device=dev)
@@ -598,11 +594,8 @@ def c3_grid(a, ca, torch, dev, world):
         wmix = torch.empty((ca.ca_gesv_mixed_workspace(n, 1, b, tree, S, True, "auto") + 7) // 8,
                            dtype=torch.float64, device=dev)
         for cond in conds:
-            if U is not None:
-                s_ = torch.from_numpy(inputs.singular_values(n, cond)).to(dev)
-                A0 = ((U * s_) @ V.t()).t().contiguous().t()
-            else:
-                A0 = conditioned_device(n, cond, 2026, dev)
+            s_ = torch.from_numpy(inputs.singular_values(n, cond)).to(dev)
+            A0 = ((U * s_) @ V.t()).t().contiguous().t()
             x_true = torch.randn(n, 1, dtype=torch.float64, device=dev,
                                  generator=torch.Generator(device=dev).manual_seed(5))
             B0 = A0 @ x_true
@@ -1446,26 +1439,17 @@ def serving_run(a):
 
 
 def conditioned_device(n, cond, seed, dev):
-    """A = U diag(s) V^T in FP64 on the device; U and V are Kronecker products
-    of two seeded Haar-orthogonal factors (exactly orthogonal up to rounding,
-    cheap to draw at n = 16384), s log-spaced from 1 to 1/cond."""
+    """A = U diag(s) V^T in FP64 on the device, s log-spaced from 1 to 1/cond
+    in a seeded order; U and V Haar orthogonal (QR of a seeded Gaussian on
+    the device, signs of R folded in; input generation, untimed)."""
     import torch
     from paper_1303_5837_gb300 import inputs
-    n1 = 1 << (int(np.log2(n)) // 2)
-    if n1 * (n // n1) != n or n < 4096:
+    if n < 4096:
         return torch.from_numpy(np.ascontiguousarray(inputs.conditioned(n, cond, seed).T)).to(dev).t()
-    n2 = n // n1
-    g = np.random.Generator(np.random.PCG64(seed))
-
-    def haar(k):
-        z = g.standard_normal((k, k))
-        q, r = np.linalg.qr(z)
-        return q * np.sign(np.diag(r))
-
-    U = torch.kron(torch.from_numpy(haar(n1)).to(dev), torch.from_numpy(haar(n2)).to(dev))
-    V = torch.kron(torch.from_numpy(haar(n1)).to(dev), torch.from_numpy(haar(n2)).to(dev))
+    U = haar_device(n, 7 * seed + 1, dev)
+    V = haar_device(n, 7 * seed + 2, dev)
     s = torch.from_numpy(inputs.singular_values(n, cond)).to(dev)
-    perm = torch.from_numpy(g.permutation(n)).to(dev)
+    perm = torch.from_numpy(np.random.Generator(np.random.PCG64(seed)).permutation(n)).to(dev)
     A = (U * s[perm]) @ V.t()
     del U, V
     return A.t().contiguous().t()
