@@ -497,9 +497,11 @@ __global__ void __launch_bounds__(kFinThreads) lu_finish_kernel(int mk, int bk, 
                                                                 int rt, const int *skip) {
   extern __shared__ __align__(16) double fsm[];
   if (skip && *skip) return;
-  double *U = fsm;                       // bk x bk (ld bk), upper part used
-  double *rd = U + (size_t)bk * bk;      // reciprocals of U's diagonal
-  double *T = rd + bk;                   // rt x bk tile (ld rt)
+  // U's upper triangle packed by rows: row j (columns j .. bk-1) at uoff(j)
+  double *U = fsm;
+  double *rd = U + (size_t)bk * (bk + 1) / 2;  // reciprocals of U's diagonal
+  double *T = rd + bk;                         // rt x bk tile (ld rt)
+  auto uoff = [bk](int j) { return j * bk - j * (j - 1) / 2; };
   const int tid = threadIdx.x;
   if (blockIdx.x == 0) {
     for (int k = 0; k < bk; ++k)
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__(kFinThreads) lu_finish_kernel(int mk, int bk, 
   const int r0 = bk + (blockIdx.x - 1) * rt;
   const int rows = min(rt, mk - r0);
   for (int k = 0; k < bk; ++k)
-    for (int i = tid; i <= k; i += kFinThreads) U[i + (size_t)k * bk] = lu11[i + (size_t)k * ldl];
+    for (int i = tid; i <= k; i += kFinThreads) U[uoff(i) + (k - i)] = lu11[i + (size_t)k * ldl];
   for (int i = tid; i < bk; i += kFinThreads) rd[i] = 1.0 / lu11[i + (size_t)i * ldl];
   for (int k = 0; k < bk; ++k)
     for (int i = tid; i < rows; i += kFinThreads) T[i + (size_t)k * rt] = P[r0 + i + (size_t)k * lda];
@@ -522,8 +524,8 @@ __global__ void __launch_bounds__(kFinThreads) lu_finish_kernel(int mk, int bk, 
     __syncthreads();
     if (g < ng && r < rows) {
       const double x = T[r + (size_t)j * rt];
-      for (int k = j + 1 + g; k < bk; k += ng)
-        T[r + (size_t)k * rt] = fma(-x, U[j + (size_t)k * bk], T[r + (size_t)k * rt]);
+      const double *uj = U + uoff(j) - j;  // uj[k] = U(j, k)
+      for (int k = j + 1 + g; k < bk; k += ng) T[r + (size_t)k * rt] = fma(-x, uj[k], T[r + (size_t)k * rt]);
     }
     __syncthreads();
   }
@@ -704,10 +706,19 @@ cudaError_t lu_panel_finish(int mk, int bk, double *P, int lda, const LuPanelWs 
     return cudaFuncSetAttribute(lu_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   });
   if (e != cudaSuccess) return e;
-  int rt = 8192 / bk;  // 64 KiB row tile
-  if (rt > 256) rt = 256;
-  size_t smem = ((size_t)bk * bk + bk + (size_t)rt * bk) * 8;
-  int below = mk - bk;
+  // row tiles sized so that the rows below the panel's top fill one wave
+  // of one CTA per SM where they can (shared memory: packed U plus the tile)
+  int sms = 0;
+  if ((e = device_sm_count(&sms)) != cudaSuccess) return e;
+  const int below = mk - bk;
+  const size_t ubytes = ((size_t)bk * (bk + 1) / 2 + bk) * 8;
+  int rtmax = (int)((200 * 1024 - ubytes) / ((size_t)bk * 8));
+  if (rtmax > kFinThreads) rtmax = kFinThreads;
+  int rt = below > 0 ? (below + sms - 1) / sms : 1;
+  rt = (rt + 7) / 8 * 8;
+  if (rt < 32) rt = 32;
+  if (rt > rtmax) rt = rtmax;
+  size_t smem = ubytes + (size_t)rt * bk * 8;
   int nblk = 1 + (below > 0 ? (below + rt - 1) / rt : 0);
   ProfScope ps(kClsLuFinish, st, (double)(below > 0 ? below : 0) * bk * bk);
   lu_finish_kernel<<<nblk, kFinThreads, smem, st>>>(mk, bk, P, lda, ws.lu11, bk, rt, skip);
@@ -722,8 +733,15 @@ cudaError_t trsm_u12(int bk, int nt, const double *L11, int ldl, double *A12, in
   });
   if (e != cudaSuccess) return e;
   if (nt <= 0 || bk <= 1) return cudaSuccess;
-  int ct = 8192 / bk;
-  if (ct > 128) ct = 128;
+  // column tiles: as many CTAs as SMs where the columns allow (the look-ahead
+  // solve of the next panel's b columns is on the panel chain), at most
+  // 8192 / bk columns each
+  int sms = 0;
+  if ((e = device_sm_count(&sms)) != cudaSuccess) return e;
+  int ct = (nt + sms - 1) / sms;
+  const int ctmax = 8192 / bk < 128 ? 8192 / bk : 128;
+  if (ct > ctmax) ct = ctmax;
+  if (ct < 1) ct = 1;
   size_t smem = ((size_t)bk * bk + (size_t)bk * ct) * 8;
   ProfScope ps(kClsTrsmU12, st, (double)bk * bk * nt);
   trsm_u12_kernel<<<(nt + ct - 1) / ct, 256, smem, st>>>(bk, nt, L11, ldl, A12, lda, ct, skip);
