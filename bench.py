@@ -538,11 +538,23 @@ def traffic_for(kernel: str, plan: str):
     return None
 
 
+def _load_torch_linalg():
+    """torch loads its CUDA linear-algebra library by name on the first QR;
+    under a profiler that intercepts dlopen the name is not found, so load it
+    by its path first (a no-op once loaded)."""
+    import ctypes
+    import torch
+    path = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+    if os.path.exists(path):
+        ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL)
+
+
 def haar_device(n, seed, dev):
     """A Haar-distributed orthogonal n x n matrix on the device: Q of the QR
     of a seeded N(0, 1) matrix with the signs of R's diagonal folded in
     (input generation, untimed; torch's QR)."""
     import torch
+    _load_torch_linalg()
     g = torch.Generator(device=dev).manual_seed(seed)
     Z = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
     Q, R = torch.linalg.qr(Z)
@@ -1354,6 +1366,8 @@ def conditioned_rect_device(m, n, cond, seed, dev):
     import torch
     from paper_1303_5837_gb300 import inputs
     g = torch.Generator(device=dev).manual_seed(seed)
+
+    _load_torch_linalg()
 
     def q_of(r, c):
         Q, R = torch.linalg.qr(torch.randn(r, c, dtype=torch.float64, device=dev, generator=g))

@@ -59,12 +59,14 @@ struct TsluSmem {
   double *prow_pub; // [2][bk] that row (every column, as after the step's update)
   double *jrow_pub; // [2][bk] the row at the next diagonal position (its owner only)
   int *plab;        // [2] label of the published best row; [2 + q] label of the published diagonal row
+  double *lv;       // rloc multipliers of the current column (nodes held by one CTA)
 };
 
 __host__ __device__ inline size_t tslu_smem_bytes(int rloc, int bk) {
   size_t s = (size_t)(rloc | 1) * bk * 8 + 2 * (size_t)bk * 8;
   s += (size_t)rloc * 4 + 16 * (kNodeWarps + 1) + 16 * 8 + 16 + 16 + 4 * (size_t)bk * 4 + 64;
   s += 2 * 16 + 4 * (size_t)bk * 8 + 16 + 64;  // published keys, rows and labels
+  s += (size_t)rloc * 8 + 16;                   // multipliers
   return s;
 }
 
@@ -98,6 +100,9 @@ __device__ inline TsluSmem tslu_carve(char *base, int rloc, int bk) {
   s.jrow_pub = (double *)base;
   base += 2 * (size_t)bk * 8;
   s.plab = (int *)base;
+  base += 16;
+  base = (char *)(((uintptr_t)base + 15) & ~(uintptr_t)15);
+  s.lv = (double *)base;
   return s;
 }
 
@@ -185,83 +190,85 @@ __global__ void __launch_bounds__(kNodeThreads, 1) tslu_node_kernel(TsluNodeArgs
 
   // ---- GEPP on the distributed tile ------------------------------------
   const int kmax = min(R, bk);
-  // A node held by one CTA: plain barriers, every row local.
+  // A node held by one CTA: two barriers per column, every row local.
+  // Step j reads the pivot p of column j and 1 / a_pj that the previous
+  // step left in pkey[j & 1] / scal[j & 1]; phase 1 keeps the old rows p and
+  // j (prow, trow) and the multipliers l_i = a_ij / a_pj at their positions
+  // after the interchange (lv); phase 2 writes the interchanged rows, the
+  // multipliers and the rank-1 update, each element by one thread from those
+  // copies, and the warp that updates column j + 1 also finds that column's
+  // pivot and its reciprocal.  The arithmetic per element is that of the
+  // cluster loop below: the same reciprocal, the same fused multiply-add.
   if (G == 1) {
+    double *lv = s.lv;
+    // pivot of column c over positions >= c (by warp 0, from the tile), its
+    // reciprocal, published into buffer q
+    auto publish_pivot = [&](int c, int q, ArgMax b) {
+      b = warp_argmax(b);
+      __syncwarp();  // the warp's writes of column c are visible to lane 0
+      if (lane == 0) {
+        s.pkey[q] = b;
+        s.scal[q] = (b.key != 0ull) ? 1.0 / s.tile[(b.pos - p0) + (size_t)c * ldt] : 0.0;
+      }
+    };
+    if (kmax > 0 && warp == 0) {
+      ArgMax b{0ull, INT_MAX};
+      for (int i = lane; i < myrows; i += 32) b = argmax_better(b, ArgMax{absbits(s.tile[i]), i});
+      publish_pivot(0, 0, b);
+    }
     for (int j = 0; j < kmax; ++j) {
-      // (a) local argmax over positions >= j of column j
-      ArgMax best{0ull, INT_MAX};
-      const int i0 = max(j - p0, 0);
-      const double *colj = s.tile + (size_t)j * ldt;
-      for (int i = i0 + tid; i < myrows; i += kNodeThreads)
-        best = argmax_better(best, ArgMax{absbits(colj[i]), p0 + i});
-      best = warp_argmax(best);
-      if (lane == 0) s.wbest[warp] = best;
-      __syncthreads();
-      if (tid == 0) {
-        ArgMax b = s.wbest[0];
-        for (int w = 1; w < kNodeWarps; ++w) b = argmax_better(b, s.wbest[w]);
-        *s.slot = b;
+      const int q = j & 1;
+      __syncthreads();  // column j's pivot is published; step j - 1 is complete
+      const ArgMax gb = s.pkey[q];
+      const bool zero = gb.key == 0ull;
+      const int p = gb.pos;  // p0 = 0: positions are local rows
+      if (zero) {
+        if (a.is_root && tid == 0 && a.dev_info) atomicCAS(a.dev_info, 0, a.ipiv_base + j + 1);
+        if (j + 1 < kmax && warp == 0) {  // nothing changes: column j + 1 as it stands
+          ArgMax b{0ull, INT_MAX};
+          const double *c1 = s.tile + (size_t)(j + 1) * ldt;
+          for (int i = j + 1 + lane; i < myrows; i += 32) b = argmax_better(b, ArgMax{absbits(c1[i]), i});
+          publish_pivot(j + 1, q ^ 1, b);
+        }
+        continue;
       }
-      node_sync(cl, G);
-      // (b) cluster argmax (the G partial maxima read in parallel through
-      //     DSMEM); read the pivot row and (owner of the pivot position) the
-      //     row at position j
-      if (tid < G) s.gslot[tid] = (tid == rank) ? *s.slot : *cl.map_shared_rank(s.slot, tid);
-      __syncthreads();
-      // every thread combines the G partial maxima (same order, same result)
-      ArgMax gb = s.gslot[0];
-      for (int q = 1; q < G; ++q) gb = argmax_better(gb, s.gslot[q]);
-      const int zero = (gb.key == 0ull);
-      const int p = gb.pos;
-      if (!zero) {
-        const int op = p / rloc, lp = p - op * rloc;
-        const int oj = j / rloc, lj = j - oj * rloc;
-        const double *tp = (op == rank) ? s.tile : cl.map_shared_rank(s.tile, op);
-        for (int k = tid; k < bk; k += kNodeThreads) {
-          const double v = tp[lp + (size_t)k * ldt];
-          s.prow[k] = v;
-          if (k == j) s.scal[0] = 1.0 / v;  // the pivot's reciprocal, read after the barrier below
-        }
-        if (tid == 0) s.iscal[1] = (op == rank) ? s.lab[lp] : *cl.map_shared_rank(s.lab + lp, op);
-        if (p != j && op == rank) {
-          const double *tj = (oj == rank) ? s.tile : cl.map_shared_rank(s.tile, oj);
-          for (int k = tid; k < bk; k += kNodeThreads) s.trow[k] = tj[lj + (size_t)k * ldt];
-          if (tid == 0) s.iscal[2] = (oj == rank) ? s.lab[lj] : *cl.map_shared_rank(s.lab + lj, oj);
-        }
-      } else if (a.is_root && rank == 0 && tid == 0 && a.dev_info) {
-        atomicCAS(a.dev_info, 0, a.ipiv_base + j + 1);
+      const double rinv = s.scal[q];
+      // phase 1: the old rows p and j, the multipliers, the labels
+      for (int k = tid; k < bk; k += kNodeThreads) {
+        s.prow[k] = s.tile[p + (size_t)k * ldt];
+        s.trow[k] = s.tile[j + (size_t)k * ldt];
       }
-      node_sync(cl, G);  // every read of this step is complete
-      if (zero) continue;
-      // (c) swap rows j and p (full width), labels with them
-      if (p != j) {
-        const int op = p / rloc, lp = p - op * rloc;
-        const int oj = j / rloc, lj = j - oj * rloc;
-        if (oj == rank) {
-          for (int k = tid; k < bk; k += kNodeThreads) s.tile[lj + (size_t)k * ldt] = s.prow[k];
-          if (tid == 0) s.lab[lj] = s.iscal[1];
-        }
-        if (op == rank) {
-          for (int k = tid; k < bk; k += kNodeThreads) s.tile[lp + (size_t)k * ldt] = s.trow[k];
-          if (tid == 0) s.lab[lp] = s.iscal[2];
-        }
+      {
+        const double *cj = s.tile + (size_t)j * ldt;
+        for (int i = j + 1 + tid; i < myrows; i += kNodeThreads) lv[i] = ((i == p) ? cj[j] : cj[i]) * rinv;
       }
-      // (d) multipliers l_i = a_ij / a_jj for positions > j (the swap's writes
-      //     are visible after the barrier; without a swap there is nothing to wait for)
-      if (p != j) __syncthreads();
-      const double rinv = s.scal[0];
-      const int i1 = max(j + 1 - p0, 0);
-      double *cj = s.tile + (size_t)j * ldt;
-      for (int i = i1 + tid; i < myrows; i += kNodeThreads) cj[i] *= rinv;
+      if (tid == 0 && p != j) {
+        const int t = s.lab[j];
+        s.lab[j] = s.lab[p];
+        s.lab[p] = t;
+      }
       __syncthreads();
-      // (e) rank-1 update of the trailing columns
+      // phase 2: rows j and p interchanged, the multipliers into column j,
+      // the update of columns j + 1 .. from the copies
+      for (int k = tid; k < bk; k += kNodeThreads) {
+        s.tile[j + (size_t)k * ldt] = s.prow[k];
+        if (p != j && k < j) s.tile[p + (size_t)k * ldt] = s.trow[k];
+      }
+      for (int i = j + 1 + tid; i < myrows; i += kNodeThreads) s.tile[i + (size_t)j * ldt] = lv[i];
       for (int k = j + 1 + warp; k < bk; k += kNodeWarps) {
         const double u = s.prow[k];
         double *ck = s.tile + (size_t)k * ldt;
-        for (int i = i1 + lane; i < myrows; i += 32) ck[i] = fma(-cj[i], u, ck[i]);
+        const double tk = s.trow[k];
+        ArgMax b{0ull, INT_MAX};
+        for (int i = j + 1 + lane; i < myrows; i += 32) {
+          const double v = fma(-lv[i], u, (i == p) ? tk : ck[i]);
+          ck[i] = v;
+          if (k == j + 1) b = argmax_better(b, ArgMax{absbits(v), i});
+        }
+        if (k == j + 1 && j + 1 < kmax) publish_pivot(j + 1, q ^ 1, b);
       }
-      __syncthreads();
     }
+    __syncthreads();
   } else {
     // One cluster barrier per column.  At the end of step j-1 every CTA has
     // published its best position of column j with that row's values (its
@@ -713,7 +720,7 @@ cudaError_t lu_panel_finish(int mk, int bk, double *P, int lda, const LuPanelWs 
   const int below = mk - bk;
   const size_t ubytes = ((size_t)bk * (bk + 1) / 2 + bk) * 8;
   int rtmax = (int)((200 * 1024 - ubytes) / ((size_t)bk * 8));
-  if (rtmax > kFinThreads) rtmax = kFinThreads;
+  if (rtmax > kFinThreads / 2) rtmax = kFinThreads / 2;  // at least two threads per row
   int rt = below > 0 ? (below + sms - 1) / sms : 1;
   rt = (rt + 7) / 8 * 8;
   if (rt < 32) rt = 32;

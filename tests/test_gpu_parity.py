@@ -183,7 +183,9 @@ def test_getrs(ca):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("m,n,L", [(2048, 64, 256), (3001, 32, 256), (1000, 16, 64), (256, 64, 256),
-                                   (4100, 128, 256)])
+                                   (4100, 128, 256),
+                                   # last leaves of 20 and 12 rows: merges of R factors of unequal height
+                                   (2068, 64, 256), (2060, 64, 128)])
 @pytest.mark.parametrize("tname", sorted(TREES))
 def test_tsqr_parity(ca, m, n, L, tname):
     A = inputs.gaussian(m, n, 5 * m + n)
