@@ -88,7 +88,7 @@ typedef struct {
 /* return codes (negative small values -i name a bad argument i) */
 #define CA_OK 0
 #define CA_ERR_WORKSPACE -1001   /* workspace pointer null or too small      */
-#define CA_ERR_UNSUPPORTED -1002 /* valid shape this build cannot run        */
+#define CA_ERR_UNSUPPORTED -1002 /* valid shape the library cannot run       */
 #define CA_ERR_LAUNCH -1003      /* a kernel launch failed (CUDA error)      */
 #define CA_ERR_TREE -1004        /* malformed tree                           */
 #define CA_ERR_BATCH_ITEM -1005  /* an item of a batch is invalid            */

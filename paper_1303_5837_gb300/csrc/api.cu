@@ -301,7 +301,7 @@ const char *ca_strerror(int code) {
     case CA_ERR_WORKSPACE:
       return "workspace pointer is null or smaller than the workspace query";
     case CA_ERR_UNSUPPORTED:
-      return "shape not supported by this build (panel width > 128 or a tree node too large)";
+      return "shape not supported by the library (panel width > 128 or a tree node too large)";
     case CA_ERR_LAUNCH:
       return "a CUDA kernel launch failed";
     case CA_ERR_TREE:
