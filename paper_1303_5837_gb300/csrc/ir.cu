@@ -15,34 +15,38 @@ constexpr int kResRows = 256;    // rows per CTA (one thread per row)
 constexpr int kResCols = 1024;   // columns of A per CTA
 constexpr int kResMaxRhs = 16;
 
-// partial[cb][j][i] = sum_{c in block cb} A(i, c) X(c, j)
+// partial[cb][j][i] = sum_{c in block cb} A(i, c) X(c, j); NJ right-hand
+// sides per pass (1 for a single one, else 4, the last pass padded)
+template <int NJ>
 __global__ void __launch_bounds__(kResRows) resid_partial_kernel(int n, int ncols, int nrhs, const double *A,
                                                                  int lda, const double *X, int ldx,
                                                                  double *partial, const int *skip) {
-  __shared__ double xs[kResCols * 4];
+  __shared__ double xs[kResCols * NJ];
   if (*skip) return;
   const int i = blockIdx.x * kResRows + threadIdx.x;
   const int c0 = blockIdx.y * kResCols;
   const int nc = min(kResCols, ncols - c0);
-  for (int j0 = 0; j0 < nrhs; j0 += 4) {  // right-hand sides four at a time
-    const int nj = min(4, nrhs - j0);
+  for (int j0 = 0; j0 < nrhs; j0 += NJ) {
+    const int nj = min(NJ, nrhs - j0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nc * 4; idx += kResRows) {
+    for (int idx = threadIdx.x; idx < nc * NJ; idx += kResRows) {
       int c = idx % nc, j = idx / nc;
       xs[j * kResCols + c] = (j < nj) ? X[(c0 + c) + (size_t)(j0 + j) * ldx] : 0.0;
     }
     __syncthreads();
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double acc[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[j] = 0.0;
     if (i < n) {
       const double *a = A + i + (size_t)c0 * lda;
 #pragma unroll 4
       for (int c = 0; c < nc; ++c) {
         const double v = a[(size_t)c * lda];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[j] = fma(v, xs[j * kResCols + c], acc[j]);
+        for (int j = 0; j < NJ; ++j) acc[j] = fma(v, xs[j * kResCols + c], acc[j]);
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < NJ; ++j)
         if (j < nj) partial[((size_t)blockIdx.y * nrhs + j0 + j) * n + i] = acc[j];
     }
   }
@@ -279,9 +283,11 @@ cudaError_t ir_residual(int n, int nrhs, const double *A, int lda, const double 
   const int ncb = (n + kResCols - 1) / kResCols;
   {
     ProfScope ps(kClsRefine, st, 2.0 * n * (double)n * nrhs);
-    resid_partial_kernel<<<dim3((n + kResRows - 1) / kResRows, ncb), kResRows, 0, st>>>(n, n, nrhs, A, lda, X,
-                                                                                         ldx, w.partial,
-                                                                                         &w.ctl->done);
+    const dim3 grid((n + kResRows - 1) / kResRows, ncb);
+    if (nrhs == 1)
+      resid_partial_kernel<1><<<grid, kResRows, 0, st>>>(n, n, nrhs, A, lda, X, ldx, w.partial, &w.ctl->done);
+    else
+      resid_partial_kernel<4><<<grid, kResRows, 0, st>>>(n, n, nrhs, A, lda, X, ldx, w.partial, &w.ctl->done);
   }
   ProfScope ps(kClsRefine, st, 0.0);
   const long long tot = (long long)n * nrhs;
@@ -350,33 +356,37 @@ __device__ __forceinline__ DD dd_add(DD a, DD b) {
   return DD{s.hi, __dadd_rn(__dadd_rn(a.lo, b.lo), s.lo)};
 }
 
-// partial[(cb * nrhs + j) * m + i] = (hi, lo) of sum_{c in block cb} A(i, c) X(c, j)
+// partial[(cb * nrhs + j) * m + i] = (hi, lo) of sum_{c in block cb} A(i, c) X(c, j);
+// NJ right-hand sides per pass (1 for a single one, else 4)
+template <int NJ>
 __global__ void __launch_bounds__(kResRows) resid_partial_dd_kernel(int m, int ncols, int nrhs, const double *A,
                                                                     int lda, const double *X, int ldx, DD *partial,
                                                                     const int *skip) {
-  __shared__ double xs[kResCols * 4];
+  __shared__ double xs[kResCols * NJ];
   if (*skip) return;
   const int i = blockIdx.x * kResRows + threadIdx.x;
   const int c0 = blockIdx.y * kResCols;
   const int nc = min(kResCols, ncols - c0);
-  for (int j0 = 0; j0 < nrhs; j0 += 4) {
-    const int nj = min(4, nrhs - j0);
+  for (int j0 = 0; j0 < nrhs; j0 += NJ) {
+    const int nj = min(NJ, nrhs - j0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nc * 4; idx += kResRows) {
+    for (int idx = threadIdx.x; idx < nc * NJ; idx += kResRows) {
       int c = idx % nc, j = idx / nc;
       xs[j * kResCols + c] = (j < nj) ? X[(c0 + c) + (size_t)(j0 + j) * ldx] : 0.0;
     }
     __syncthreads();
-    DD acc[4] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+    DD acc[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[j] = DD{0.0, 0.0};
     if (i < m) {
       const double *a = A + i + (size_t)c0 * lda;
       for (int c = 0; c < nc; ++c) {
         const double v = a[(size_t)c * lda];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[j] = dd_add_prod(acc[j], v, xs[j * kResCols + c]);
+        for (int j = 0; j < NJ; ++j) acc[j] = dd_add_prod(acc[j], v, xs[j * kResCols + c]);
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < NJ; ++j)
         if (j < nj) partial[((size_t)blockIdx.y * nrhs + j0 + j) * m + i] = acc[j];
     }
   }
@@ -418,6 +428,7 @@ __global__ void rowsum_abs_rect_kernel(int m, int n, const double *A, int lda, d
 // S(j, c) = sum_i A(i, j) R(i, c): one warp per column j of A, lanes down the
 // rows (coalesced), every right-hand side accumulated per lane, then summed
 // across the warp in a fixed order
+template <int NC>  // right-hand sides per pass: 1 for a single one, else kResMaxRhs
 __global__ void __launch_bounds__(kAtrWarps * 32) atr_kernel(int m, int n, int nrhs, const double *A, int lda,
                                                              const double *R, int ldr, double *S, int lds,
                                                              const int *skip) {
@@ -425,19 +436,19 @@ __global__ void __launch_bounds__(kAtrWarps * 32) atr_kernel(int m, int n, int n
   const int j = blockIdx.x * kAtrWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (j >= n) return;
   const double *a = A + (size_t)j * lda;
-  for (int c0 = 0; c0 < nrhs; c0 += kResMaxRhs) {
-    const int nc = min(kResMaxRhs, nrhs - c0);
-    double acc[kResMaxRhs];
+  for (int c0 = 0; c0 < nrhs; c0 += NC) {
+    const int nc = min(NC, nrhs - c0);
+    double acc[NC];
 #pragma unroll
-    for (int c = 0; c < kResMaxRhs; ++c) acc[c] = 0.0;
+    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
     for (int i = lane; i < m; i += 32) {
       const double v = a[i];
 #pragma unroll
-      for (int c = 0; c < kResMaxRhs; ++c)
+      for (int c = 0; c < NC; ++c)
         if (c < nc) acc[c] = fma(v, R[i + (size_t)(c0 + c) * ldr], acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < kResMaxRhs; ++c) {
+    for (int c = 0; c < NC; ++c) {
       double v = acc[c];
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -588,8 +599,11 @@ cudaError_t ls_residual(int m, int n, int nrhs, const double *A, int lda, const 
   DD *part = (DD *)w.partial;
   {
     ProfScope ps(kClsRefine, st, 2.0 * m * (double)n * nrhs);
-    resid_partial_dd_kernel<<<dim3((m + kResRows - 1) / kResRows, ncb), kResRows, 0, st>>>(m, n, nrhs, A, lda, X,
-                                                                                            ldx, part, skip);
+    const dim3 grid((m + kResRows - 1) / kResRows, ncb);
+    if (nrhs == 1)
+      resid_partial_dd_kernel<1><<<grid, kResRows, 0, st>>>(m, n, nrhs, A, lda, X, ldx, part, skip);
+    else
+      resid_partial_dd_kernel<4><<<grid, kResRows, 0, st>>>(m, n, nrhs, A, lda, X, ldx, part, skip);
   }
   ProfScope ps(kClsRefine, st, 0.0);
   const long long tot = (long long)m * nrhs;
@@ -600,8 +614,11 @@ cudaError_t ls_residual(int m, int n, int nrhs, const double *A, int lda, const 
 cudaError_t ls_normal_residual(int m, int n, int nrhs, const double *A, int lda, const double *X, int ldx,
                                const double *B, int ldb, const LsWs &w, cudaStream_t st) {
   ProfScope ps(kClsRefine, st, 2.0 * m * (double)n * nrhs);
-  atr_kernel<<<(n + kAtrWarps - 1) / kAtrWarps, kAtrWarps * 32, 0, st>>>(m, n, nrhs, A, lda, w.R, m, w.S, n,
-                                                                         &w.ctl->done);
+  const unsigned g = (n + kAtrWarps - 1) / kAtrWarps;
+  if (nrhs == 1)
+    atr_kernel<1><<<g, kAtrWarps * 32, 0, st>>>(m, n, nrhs, A, lda, w.R, m, w.S, n, &w.ctl->done);
+  else
+    atr_kernel<kResMaxRhs><<<g, kAtrWarps * 32, 0, st>>>(m, n, nrhs, A, lda, w.R, m, w.S, n, &w.ctl->done);
   ls_berr_kernel<<<nrhs, 256, 0, st>>>(m, n, w.S, n, X, ldx, B, ldb, w.anorm, w.a1, w.berr, &w.ctl->done);
   return cudaGetLastError();
 }
@@ -860,8 +877,8 @@ cudaError_t ir_gmres_correction(int n, const double *A, int lda, const double *L
     double *vs = g.V + (size_t)s * n;
     {  // w = A v_s
       ProfScope ps(kClsRefine, st, 2.0 * n * (double)n);
-      resid_partial_kernel<<<dim3((n + kResRows - 1) / kResRows, ncb), kResRows, 0, st>>>(n, n, 1, A, lda, vs,
-                                                                                           n, g.mv, stop);
+      resid_partial_kernel<1><<<dim3((n + kResRows - 1) / kResRows, ncb), kResRows, 0, st>>>(n, n, 1, A, lda, vs,
+                                                                                              n, g.mv, stop);
       gm_gemv_reduce_kernel<<<nb, 256, 0, st>>>(n, ncb, g.mv, g.w, g.ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
