@@ -106,7 +106,7 @@ def parse():
     p.add_argument("--mixed-slices", type=int, default=4)
     p.add_argument("--mixed-exact", type=int, default=1)
     p.add_argument("--no-mixed", action="store_true")
-    p.add_argument("--serve-rates", default="100,1000,10000", help="arrival rates of the sweep (requests/s)")
+    p.add_argument("--serve-rates", default="100,1000,10000,100000", help="arrival rates of the sweep (requests/s)")
     p.add_argument("--serve-count", type=int, default=24, help="requests per rate (the same shapes at every rate)")
     p.add_argument("--serve-nmax", type=int, default=8192)
     p.add_argument("--serve-cond-max", type=float, default=1e8)
