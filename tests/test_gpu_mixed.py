@@ -100,12 +100,13 @@ def test_calu_mixed_fused_backward_error(ca):
     assert info.cpu().tolist() == [0, 0]
 
 
-@pytest.mark.parametrize("n,cond,slices,exact", [(1024, 1e2, 3, False), (1024, 1e6, 3, True),
-                                                 (2048, 1e6, 4, True), (1024, 1e10, 5, True),
-                                                 (1536, 1e10, 6, True)])
-def test_gesv_mixed_refinement(ca, n, cond, slices, exact):
+@pytest.mark.parametrize("n,cond,slices,exact,nrhs", [(1024, 1e2, 3, False, 2), (1024, 1e6, 3, True, 2),
+                                                      (2048, 1e6, 4, True, 2), (1024, 1e10, 5, True, 2),
+                                                      (1536, 1e10, 6, True, 2), (2048, 1e6, 4, True, 1),
+                                                      (1024, 1e6, 4, True, 6)])
+def test_gesv_mixed_refinement(ca, n, cond, slices, exact, nrhs):
     A = inputs.conditioned(n, cond, 7)
-    x_true = inputs.rhs(n, 2, 8)
+    x_true = inputs.rhs(n, nrhs, 8)
     B = A @ x_true
     b, L = 128, 256
     LU_o, ipiv_o, _, _ = oracle.calu(A, b, oracle.make_tree(L))
@@ -267,9 +268,10 @@ def test_caqr_mixed_geqrs(ca):
     check(solve_err(to_host(Bd)[:n], x_o), 1e-12)
 
 
-@pytest.mark.parametrize("m,n,cond,slices,noise", [(2048, 512, 1e4, 4, 0.0), (2048, 512, 1e4, 4, 1e-3),
-                                                   (3000, 700, 1e6, 4, 1e-6), (1500, 400, 1e2, 3, 1e-2)])
-def test_gels_mixed_refinement(ca, m, n, cond, slices, noise):
+@pytest.mark.parametrize("m,n,cond,slices,noise,nrhs", [(2048, 512, 1e4, 4, 0.0, 2), (2048, 512, 1e4, 4, 1e-3, 2),
+                                                        (3000, 700, 1e6, 4, 1e-6, 2), (1500, 400, 1e2, 3, 1e-2, 2),
+                                                        (2048, 512, 1e6, 4, 1e-3, 1), (1700, 600, 1e4, 4, 0.0, 5)])
+def test_gels_mixed_refinement(ca, m, n, cond, slices, noise, nrhs):
     """Least squares after a reduced-digit CAQR, refined on the corrected
     semi-normal equations: the stop measure (||A^T r|| over its scale)
     reaches 1e-14 and the solution is the oracle's FP64 CAQR least-squares
@@ -280,8 +282,8 @@ def test_gels_mixed_refinement(ca, m, n, cond, slices, noise):
     V, _ = np.linalg.qr(g.standard_normal((n, n)))
     s = cond ** (-np.arange(n) / (n - 1))
     A = np.asfortranarray((U * s) @ V.T)
-    x_true = g.standard_normal((n, 2))
-    e = g.standard_normal((m, 2))
+    x_true = g.standard_normal((n, nrhs))
+    e = g.standard_normal((m, nrhs))
     e -= U @ (U.T @ e)                             # orthogonal to range(A)
     B = A @ x_true + noise * e / np.linalg.norm(e, axis=0) * np.linalg.norm(A @ x_true, axis=0)
     b, L = 64, 256
