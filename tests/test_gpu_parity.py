@@ -133,6 +133,21 @@ def test_calu_zero_column_info(ca):
     assert np.array_equal(ipiv.cpu().numpy()[:64], ipiv_o[:64])
 
 
+def test_tslu_zero_column_single_cta_nodes(ca):
+    """A column that is exactly zero in every node, on a panel whose 128
+    leaves are each held by one CTA: no interchange and no update at that
+    column, the same selections as the oracle, info at the first zero pivot."""
+    A = inputs.gaussian(8192, 32, 5)
+    A[:, 5] = 0.0
+    tree = [(2, 0), (0, 0)]
+    _, ipiv_o, info_o, nt = oracle.calu(A, 32, oracle.make_tree(64, tree))
+    assert nt == 0 and info_o == 6
+    ipiv, info = ca.tslu(to_dev(A), ca.make_tree(64, tree))
+    torch.cuda.synchronize()
+    assert info.cpu().tolist()[0] == 6
+    assert np.array_equal(ipiv.cpu().numpy(), ipiv_o)
+
+
 def test_calu_nonfinite_status(ca):
     A = inputs.gaussian(128, 128, 4)
     A[5, 3] = np.nan
