@@ -269,6 +269,10 @@ struct TsqrNodeArgs {
 // rows and 64 columns held by one CTA; *done = false when the shape is not
 // covered (the shared-memory node kernel then runs).
 bool tsqr_reg_fits(int rows, int bk);
+// Cluster form of the register-resident node (64 < bk <= 128, 129 .. 1024
+// rows): its cluster size, 0 when the shape is not covered.
+int tsqr_creg_cluster(int rows, int bk);
+cudaError_t launch_tsqr_creg(const TsqrNodeArgs &a, int nodes, int rows, cudaStream_t st);
 cudaError_t launch_tsqr_reg(const TsqrNodeArgs &a, int nodes, int rows, cudaStream_t st, bool *done);
 cudaError_t tsqr_panel(int mk, int bk, int b, double *P, int lda, int leaf_rows,
                        const Plan &plan, double *Tp, const QrPanelWs &ws, int *dev_info,

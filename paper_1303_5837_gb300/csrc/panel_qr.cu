@@ -903,6 +903,7 @@ static cudaError_t launch_tsqr_node(const TsqrNodeArgs &args, int nodes, int G, 
     e = launch_tsqr_reg(args, nodes, (int)r, st, &done);
     return (e == cudaSuccess && !done) ? cudaErrorInvalidValue : e;
   }
+  if (G < 0) return launch_tsqr_creg(args, nodes, (int)r, st);  // registers of a cluster
   cfg.gridDim = dim3(nodes * G);
   cfg.blockDim = dim3(kQrThreads);
   cfg.dynamicSmemBytes = tsqr_smem_bytes(args.rloc, args.ld, args.bk);
@@ -931,9 +932,16 @@ cudaError_t tsqr_panel(int mk, int bk, int b, double *P, int lda, int leaf_rows,
   a.dev_info = dev_info;
   int R = leaf_rows < mk ? leaf_rows : mk;
   int rloc = 0, ld = 0;
-  // G = 0: the register-resident node kernel; else a cluster of G CTAs
-  int G = tsqr_reg_fits(R, bk) ? 0 : pick_qr_cluster(R, bk, plan.nleaves, &rloc, &ld);
-  if (G < 0) return cudaErrorInvalidValue;
+  // G = 0: the register-resident node kernel; -1: its cluster form; else
+  // the shared-memory node kernel on a cluster of G CTAs
+  auto pick = [&](int rows, int nodes) {
+    if (tsqr_reg_fits(rows, bk)) return 0;
+    if (tsqr_creg_cluster(rows, bk) >= 2) return -1;
+    const int g = pick_qr_cluster(rows, bk, nodes, &rloc, &ld);
+    return g > 0 ? g : -2;
+  };
+  int G = pick(R, plan.nleaves);
+  if (G == -2) return cudaErrorInvalidValue;
   a.is_leaf = 1;
   a.rloc = rloc;
   a.ld = ld;
@@ -944,8 +952,8 @@ cudaError_t tsqr_panel(int mk, int bk, int b, double *P, int lda, int leaf_rows,
   int buf = 0;
   for (int r = 0; r < plan.nrounds; ++r) {
     const RoundDesc &rd = plan.r[r];
-    G = tsqr_reg_fits(rd.max_cnt * bk, bk) ? 0 : pick_qr_cluster(rd.max_cnt * bk, bk, rd.n_out, &rloc, &ld);
-    if (G < 0) return cudaErrorInvalidValue;
+    G = pick(rd.max_cnt * bk, rd.n_out);
+    if (G == -2) return cudaErrorInvalidValue;
     a.is_leaf = 0;
     a.rd = rd;
     a.rloc = rloc;
