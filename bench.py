@@ -856,21 +856,29 @@ def run_ours(a, rank: int, world: int, local: int):
     # ---- end to end through the public API with host buffers --------------
     e2e = None
     if a.e2e_steps > 0:
-        A_h = A0.cpu().pin_memory()
-        B_h = B0.cpu().pin_memory()
-        X_h = torch.empty(B0.shape, dtype=torch.float64).pin_memory()
+        # pinned host copies in the device tensors' own column-major layout;
+        # every transfer goes through the transposed (contiguous) views, so it
+        # is one contiguous copy of the whole buffer
+        A_h = torch.empty(A0.shape[::-1], dtype=torch.float64).pin_memory().t()
+        A_h.t().copy_(A0.t().cpu())
+        B_h = torch.empty(B0.shape[::-1], dtype=torch.float64).pin_memory().t()
+        B_h.t().copy_(B0.t().cpu())
+        X_h = torch.empty(B0.shape[::-1], dtype=torch.float64).pin_memory().t()
+
+        def xfer(dst, src):
+            dst.t().copy_(src.t(), non_blocking=True)
 
         def e2e_step():
-            A.copy_(A_h, non_blocking=True)      # H2D: the matrix
-            X.copy_(B_h, non_blocking=True)      # H2D: the right-hand side
+            xfer(A, A_h)                         # H2D: the matrix
+            xfer(X, B_h)                         # H2D: the right-hand side
             ca.calu_factor(A, b, tree, ipiv=ipiv, work=work, dev_info=info)
             ca.calu_getrs(A, ipiv, X, work=swork)
-            X_h.copy_(X, non_blocking=True)      # D2H: the LU solution
-            A.copy_(A_h, non_blocking=True)
-            X.copy_(B_h, non_blocking=True)
+            xfer(X_h, X)                         # D2H: the LU solution
+            xfer(A, A_h)
+            xfer(X, B_h)
             ca.caqr_factor(A, b, tree, qtree=qtree, work=qwork, dev_info=info)
             ca.caqr_geqrs(A, b, tree, qtree, X, work=qwork)
-            X_h.copy_(X, non_blocking=True)      # D2H: the least-squares solution
+            xfer(X_h, X)                         # D2H: the least-squares solution
 
         e2e_step()
         torch.cuda.synchronize()
